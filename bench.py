@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Device-resident decode benchmark (one JSON line on stdout).
+
+Workload (default): the chr1-shaped synthetic genome of 253,935,557 B
+(seed 0; 15,499 blocks of 16 KiB), encoded by the library encoder with the
+4-entry distance history; one step = one full device-resident decode
+(rANS of the four streams + parse + match copy) from the archive in HBM to
+the output in HBM, through aceapex_decode_all.
+
+Metric: decoded GB/s (decompressed bytes / device time), with the roofline of
+the dominant kernel, the whole-path HBM fraction, an end-to-end number
+through aceapex_decode_host (host archive -> host output, copies inside the
+timed region), and the CPU oracle timed on the host as the baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--corpus dna|text] [--encoding history|no_rep] [--variant fast|plain]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+GENOME = synth.GENOME_CHR1_SIZE
+TEXT = 200 * 1024 * 1024
+L2_FLUSH = 256 << 20
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--corpus", default="dna", choices=["dna", "text"])
+    p.add_argument("--size", type=int, default=0)
+    p.add_argument("--encoding", default="history", choices=["history", "no_rep"])
+    p.add_argument("--variant", default="fast", choices=["fast", "plain"])
+    p.add_argument("--lanes", type=int, default=32)
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cache-dir", default=os.environ.get("ACEAPEX_CACHE", "/tmp/aceapex_bench_cache"))
+    return p.parse_args()
+
+
+def workload(args):
+    size = args.size or (GENOME if args.corpus == "dna" else TEXT)
+    name = (f"chr1-shaped synthetic genome {size:,} B" if args.corpus == "dna" and size == GENOME
+            else f"synthetic {args.corpus} {size:,} B")
+    return size, name
+
+
+def encoder_key():
+    h = hashlib.sha256()
+    for f in ("encode.cpp", "internal.h", "plan.h"):
+        h.update(open(os.path.join(ROOT, "paper_2608_10188_gb300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(ROOT, "synth", "synth.c"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def get_archive(args, acx):
+    """Generate the corpus and encode it with the library encoder (cached on
+    the local disk between runs of the same source version)."""
+    size, _ = workload(args)
+    data = synth.corpus(args.corpus, size, 0)
+    key = f"{args.corpus}-{size}-s0-{args.encoding}-k{args.lanes}-{encoder_key()}.acx"
+    path = os.path.join(args.cache_dir, key)
+    arc = None
+    if os.path.exists(path):
+        arc = open(path, "rb").read()
+    if arc is None:
+        arc = acx.encode(data, no_rep=args.encoding == "no_rep", max_lanes=args.lanes)
+        try:
+            os.makedirs(args.cache_dir, exist_ok=True)
+            tmp = path + f".{os.getpid()}"
+            with open(tmp, "wb") as f:
+                f.write(arc)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    return data, arc
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_oracle_baseline(arc, data, repeats=3):
+    import oracle
+    times = []
+    for _ in range(repeats):
+        t = time.perf_counter()
+        out = oracle.decode(arc, verify=False)
+        times.append(time.perf_counter() - t)
+    if not np.array_equal(out, data):
+        raise RuntimeError("oracle decode mismatch")
+    med = statistics.median(times)
+    return {"value": round(data.size / med / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"whole archive ({data.size:,} B decoded), single-threaded C oracle, median of {repeats}"}
+
+
+def run_reference(args, dist):
+    """The oracle timed on the host cores (bench --impl reference)."""
+    rank = dist["rank"]
+    if rank != 0:
+        return
+    import oracle
+    import paper_2608_10188_gb300 as acx
+    acx.build.build()
+    data, arc = get_archive(args, acx)
+    size, wname = workload(args)
+    for _ in range(args.warmup):
+        oracle.decode(arc, verify=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = oracle.decode(arc, verify=False)
+    el = time.perf_counter() - t0
+    if not np.array_equal(out, data):
+        raise RuntimeError("oracle decode mismatch")
+    value = size * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": "device-resident decode GB/s", "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": wname, "encoding": args.encoding, "block_size": 16384},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"whole archive per step ({size:,} B), single-threaded C oracle"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def init_dist(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    d = {"rank": rank, "world": world, "local": local, "pg": None}
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        d["pg"] = tdist
+    return d
+
+
+def main():
+    args = parse_args()
+    dist = init_dist(args)
+    if args.impl == "reference":
+        run_reference(args, dist)
+        if dist["pg"]:
+            dist["pg"].barrier()
+        return
+    import torch
+
+    import paper_2608_10188_gb300 as acx
+    acx.build.build()
+    dev = dist["local"]
+    torch.cuda.set_device(dev)
+    size, wname = workload(args)
+    data, arc = get_archive(args, acx)
+    variant = acx.lib.VARIANT_PLAIN if args.variant == "plain" else acx.lib.VARIANT_FAST
+    ctx = acx.Context(dev, variant=variant)
+    h_arc = np.frombuffer(arc, dtype=np.uint8).copy()
+    d_arc = torch.from_numpy(h_arc).to(f"cuda:{dev}")
+    A = acx.Archive(ctx, d_arc.data_ptr(), h_arc, h_arc.size)
+    info = A.info
+    out = torch.empty(size, dtype=torch.uint8, device=f"cuda:{dev}")
+    flush = torch.empty(L2_FLUSH, dtype=torch.uint8, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    # correctness gate: the timed configuration must reproduce the input exactly
+    rc = acx.decode_all(ctx, A, out.data_ptr(), size, sh)
+    if rc != 0:
+        raise RuntimeError(f"decode failed: {rc} {ctx.last_error()}")
+    if not torch.equal(out, torch.from_numpy(data).to(out.device)):
+        raise RuntimeError("GPU decode differs from the input")
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        acx.decode_all(ctx, A, out.data_ptr(), size, sh)
+    torch.cuda.synchronize()
+    if dist["pg"]:
+        dist["pg"].barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ms_total, ms_ans, ms_asm = [], [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)  # write 256 MiB > L2 between steps
+        r, st = acx.decode_all(ctx, A, out.data_ptr(), size, sh, stats=True)
+        if r != 0:
+            raise RuntimeError(f"decode failed: {r} {ctx.last_error()}")
+        ms_total.append(st["ms_total"])
+        ms_ans.append(st["ms_ans"])
+        ms_asm.append(st["ms_parse"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist["pg"]:
+        dist["pg"].barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    dev_ms = sum(ms_total)
+    if dist["pg"]:
+        t = torch.tensor([dev_ms], device=out.device, dtype=torch.float64)
+        dist["pg"].all_reduce(t, op=dist["pg"].ReduceOp.MAX)
+        dev_ms = float(t.item())
+    world = dist["world"]
+    value = world * size * args.steps / (dev_ms / 1e3) / 1e9
+    ms_step = dev_ms / args.steps
+
+    # roofline of the dominant kernel and of the whole path
+    peak, peak_kind = measured_peaks()
+    plan_bytes = stream_bytes(arc)
+    a_ms = statistics.mean(ms_ans)
+    s_ms = statistics.mean(ms_asm)
+    k_rans_bytes = plan_bytes["payload"] + plan_bytes["decoded"]
+    k_asm_bytes = plan_bytes["decoded"] + size
+    if a_ms >= s_ms:
+        dom, dom_ms, dom_bytes = "k_rans", a_ms, k_rans_bytes
+    else:
+        dom, dom_ms, dom_bytes = "k_assemble", s_ms, k_asm_bytes
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    path_bytes = len(arc) + size
+    path_gbs = path_bytes / (ms_step / 1e3) / 1e9
+
+    # end to end through the C ABI from pinned host memory
+    e2e = None
+    if args.e2e_steps > 0:
+        h_in = torch.from_numpy(h_arc).pin_memory()
+        h_out = torch.empty(size, dtype=torch.uint8).pin_memory()
+        hin_np, hout_np = h_in.numpy(), h_out.numpy()
+        for _ in range(2):
+            acx.decode_host(ctx, A, hin_np, hout_np, sh)
+        e_ms = []
+        for _ in range(args.e2e_steps):
+            r, st = acx.decode_host(ctx, A, hin_np, hout_np, sh, stats=True)
+            if r != 0:
+                raise RuntimeError(f"decode_host failed: {r} {ctx.last_error()}")
+            e_ms.append(st["ms_total"])
+        if not np.array_equal(hout_np, data):
+            raise RuntimeError("decode_host output differs from the input")
+        e_mean = statistics.mean(e_ms)
+        e2e = {"value": round(world * size / (e_mean / 1e3) / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": len(arc), "d2h_bytes_per_step": size}
+
+    cpu = None
+    if dist["rank"] == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_baseline(arc, data)
+
+    if dist["rank"] == 0:
+        line = {
+            "metric": "device-resident decode GB/s", "value": round(value, 3), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded generator; stands in for chr1 hg38)",
+            "config": {"workload": wname, "encoding": args.encoding, "variant": args.variant,
+                       "rans_lanes": args.lanes, "block_size": 16384, "blocks": info["n_blocks"],
+                       "tokens": info["tokens"], "archive_bytes": len(arc),
+                       "ratio": round(size / len(arc), 4),
+                       "l2": "256 MiB buffer written between steps; per-step CUDA events exclude it"},
+            "stage_ms": {"ans": round(a_ms, 4), "parse_copy": round(s_ms, 4)},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_kind": peak_kind,
+                         "algorithmic_bytes": int(dom_bytes)},
+            "path_roofline": {"bytes": path_bytes, "achieved": round(path_gbs, 1), "peak": peak,
+                              "frac": round(path_gbs / peak, 4), "frac_nominal_8tbs": round(path_gbs / 8000, 4)},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk,
+            "wall_s": round(wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    A.close()
+    ctx.close()
+    if dist["pg"]:
+        dist["pg"].barrier()
+        dist["pg"].destroy_process_group()
+
+
+def stream_bytes(arc: bytes) -> dict:
+    """Payload bytes and decoded stream bytes of an archive (from its index
+    and block descriptors)."""
+    import struct
+    nb = struct.unpack_from("<I", arc, 24)[0]
+    off_idx = struct.unpack_from("<Q", arc, 40)[0]
+    payload = 0
+    decoded = 0
+    for b in range(nb):
+        poff, plen = struct.unpack_from("<QI", arc, off_idx + 40 * b)
+        payload += plen
+        for s in range(4):
+            decoded += struct.unpack_from("<I", arc, poff + 12 * s)[0]
+    return {"payload": payload, "decoded": decoded}
+
+
+if __name__ == "__main__":
+    main()

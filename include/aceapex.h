@@ -1,0 +1,167 @@
+/*
+ * aceapex.h — C ABI of the GB300 (sm_103a) decoder for the blockwise
+ * absolute-offset LZ77 format studied in "What Actually Serializes GPU LZ77
+ * Decode" (format v1).
+ *
+ * What the paper defines (section names of the paper):
+ *  - Setup: every back-reference is an absolute position in the decompressed
+ *    output; the encoder searches matches globally and cuts the output into
+ *    fixed 16 KiB blocks; a block can be decoded once the blocks holding its
+ *    sources exist; each block stores four streams — literals, lengths,
+ *    absolute offsets, commands — behind an ANS entropy stage (Table 1).
+ *  - "The Last Sequential Element": repeat matches take their distance from
+ *    a four-entry history; lengths are varints; everything else in the parse
+ *    is a prefix sum; an encoder flag drops the history (history-free
+ *    encoding, same format, same decoder).
+ *  - "What Does: Periods, Not Chains": a self-overlapping match is the
+ *    periodic fill out[dst+k] = out[src + (k mod dist)].
+ * The byte layout the paper leaves open is fixed by format v1 (see the
+ * design notes): 64-byte header, four 256-entry frequency tables summing to
+ * 4096, a 40-byte index entry per block, and per-block payloads of four
+ * stream bodies (stored, or interleaved rANS with K <= 128 lanes, 32-bit
+ * states, 16-bit words, 12-bit probabilities).
+ *
+ * Conventions for every function:
+ *  - Return value: ACEAPEX_OK (0) or a negative ACEAPEX_E_* status.  The
+ *    library never prints; aceapex_last_error() gives a message.
+ *  - "device pointer": memory of the context's CUDA device (cudaMalloc or a
+ *    framework allocator); "host pointer": ordinary host memory.
+ *  - "stream": a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Decode calls enqueue work on it; the synchronous variants then
+ *    synchronise that stream and read the device error word.
+ *  - A context is not thread-safe and its scratch is reused by every call:
+ *    use one context per concurrently running stream.
+ *  - Corrupt input never traps or hangs: it returns ACEAPEX_E_CORRUPT (or
+ *    ACEAPEX_E_TIMEOUT if a dependency wait ran out); the output content is
+ *    then undefined.
+ */
+#ifndef ACEAPEX_H
+#define ACEAPEX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ACEAPEX_OK 0
+#define ACEAPEX_E_ARG (-1)      /* bad argument (null pointer, too-small buffer, ...) */
+#define ACEAPEX_E_CORRUPT (-2)  /* archive violates format v1 */
+#define ACEAPEX_E_NOMEM (-3)    /* host or device allocation failed */
+#define ACEAPEX_E_CUDA (-4)     /* a CUDA runtime call failed */
+#define ACEAPEX_E_TIMEOUT (-5)  /* a device-side dependency wait exceeded its limit */
+#define ACEAPEX_E_RANGE (-6)    /* requested range outside the archive */
+#define ACEAPEX_E_BUSY (-7)     /* admission refused (serving) */
+
+#define ACEAPEX_BLOCK_SIZE 16384u
+
+typedef struct aceapex_ctx aceapex_ctx;
+typedef struct aceapex_archive aceapex_archive;
+
+/* Encoder parameters (0 fields select defaults). */
+typedef struct {
+    int no_rep;          /* 1: history-free encoding (no repeat codes; paper's encoder flag) */
+    uint32_t min_match;  /* minimum match length, >= 4 (default 4) */
+    uint32_t max_lanes;  /* rANS lane cap K, power of two <= 128 (default 32) */
+    int threads;         /* encoder threads (default: hardware concurrency) */
+} aceapex_enc_params;
+
+/* Decoder variants. */
+#define ACEAPEX_VARIANT_FAST 0   /* scan parse + periodic fill + dependency dataflow */
+#define ACEAPEX_VARIANT_PLAIN 1  /* serial parse with history, byte-serial copies (comparison) */
+
+typedef struct {
+    uint32_t variant;     /* ACEAPEX_VARIANT_* */
+    uint32_t timeout_us;  /* limit of every device-side dependency wait (default 2,000,000) */
+    uint32_t ctas_per_sm; /* persistent CTAs per SM for the assembly kernel (0 = occupancy maximum) */
+    uint32_t reserved;
+} aceapex_dec_params;
+
+/* Timing of the last call, measured with CUDA events on the call's stream
+ * (filled only when stats is non-NULL; timing adds event records). */
+typedef struct {
+    double ms_total;  /* whole call, device time */
+    double ms_ans;    /* entropy stage (rANS decode of the four streams) */
+    double ms_parse;  /* parse + copy (assembly kernel) */
+    double ms_copy;   /* reserved: the fused assembly kernel reports parse and copy together */
+    uint64_t blocks;  /* blocks decoded */
+    uint64_t bytes;   /* bytes written to the output */
+} aceapex_stats;
+
+typedef struct {
+    uint64_t total_size;    /* decompressed bytes */
+    uint32_t n_blocks;
+    uint32_t flags;         /* bit0: encoded history-free */
+    uint32_t min_match;
+    uint32_t max_tokens;    /* largest token count of a block */
+    uint64_t archive_bytes;
+    uint64_t tokens;        /* total tokens */
+} aceapex_archive_info;
+
+/* Status code -> static message. */
+const char* aceapex_status_string(int status);
+/* Last error message of a context (static storage inside the context). */
+const char* aceapex_last_error(const aceapex_ctx* ctx);
+
+/* Create a context on CUDA device `device`.  params may be NULL (defaults).
+ * The context owns the decode scratch (device memory, grown on demand by
+ * the decode calls, freed by aceapex_ctx_destroy). */
+int aceapex_ctx_create(int device, const aceapex_dec_params* params, aceapex_ctx** out);
+int aceapex_ctx_destroy(aceapex_ctx* ctx);
+int aceapex_ctx_set_params(aceapex_ctx* ctx, const aceapex_dec_params* params);
+
+/*
+ * Encode n bytes (host pointer src) into a format v1 archive.  *out is
+ * allocated by the library (host memory) and must be released with
+ * aceapex_free.  Paper, Setup: global match search, absolute offsets, 16 KiB
+ * blocks; "The Last Sequential Element": no_rep drops the repeat codes.
+ */
+int aceapex_encode(const uint8_t* src, uint64_t n, const aceapex_enc_params* params, uint8_t** out,
+                   uint64_t* out_len);
+void aceapex_free(void* p);
+
+/*
+ * Open an archive for decoding.  d_arc: device pointer to the archive bytes
+ * (caller-owned, must stay valid until aceapex_archive_close).  h_arc: host
+ * pointer to the same bytes (read during this call only; the header, index
+ * and block descriptors are validated here and a device-resident decode plan
+ * is built).  The archive object owns the plan (device memory).
+ */
+int aceapex_archive_open(aceapex_ctx* ctx, const void* d_arc, const void* h_arc, uint64_t arc_len,
+                         aceapex_archive** out);
+int aceapex_archive_close(aceapex_archive* arc);
+/* Host-only structural validation of an archive (header, tables, index,
+ * payload descriptors); no device work.  info may be NULL.  Returns
+ * ACEAPEX_OK or ACEAPEX_E_CORRUPT. */
+int aceapex_archive_check(const void* h_arc, uint64_t arc_len, aceapex_archive_info* info);
+int aceapex_archive_get_info(const aceapex_archive* arc, aceapex_archive_info* info);
+
+/*
+ * Decode the whole archive into d_out (device pointer, out_cap >= total
+ * size) — the paper's full device-resident decode (Table 2: ANS + parse +
+ * copy).  Enqueued on `stream`; the _async variant returns after enqueueing
+ * (errors accumulate in the context until aceapex_sync), the plain variant
+ * synchronises the stream and returns the decode status.
+ */
+int aceapex_decode_all(aceapex_ctx* ctx, aceapex_archive* arc, void* d_out, uint64_t out_cap, void* stream,
+                       aceapex_stats* stats);
+int aceapex_decode_all_async(aceapex_ctx* ctx, aceapex_archive* arc, void* d_out, uint64_t out_cap,
+                             void* stream);
+/* Synchronise `stream` and return (and clear) the context's device error status. */
+int aceapex_sync(aceapex_ctx* ctx, void* stream);
+
+/*
+ * End-to-end decode from host memory: copies the archive (host pointer
+ * h_arc, arc_len bytes, ideally pinned) to the device, decodes it, and copies
+ * the output to h_out (host pointer, out_cap >= total size).  Device buffers
+ * are context scratch.  `arc` must be an archive opened from the same bytes
+ * (its plan is reused); pass NULL to open a temporary one.
+ */
+int aceapex_decode_host(aceapex_ctx* ctx, aceapex_archive* arc, const void* h_arc, uint64_t arc_len,
+                        void* h_out, uint64_t out_cap, void* stream, aceapex_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACEAPEX_H */

@@ -1,0 +1,377 @@
+// C ABI of the GB300 decoder (see include/aceapex.h): contexts, archive
+// plans, and the orchestration of the decode kernels on a caller's stream.
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/aceapex.h"
+#include "internal.h"
+#include "plan.h"
+
+namespace acx {
+cudaError_t launch_prologue(uint32_t* counters, uint32_t n_counters, cudaStream_t st);
+cudaError_t launch_rans(const JobDev& job, int grid, cudaStream_t st);
+cudaError_t launch_assemble(const JobDev& job, int grid, cudaStream_t st);
+cudaError_t launch_plain(const JobDev& job, int grid, cudaStream_t st);
+size_t rans_smem_bytes();
+size_t asm_smem_bytes(uint32_t T, uint32_t LB);
+size_t plain_smem_bytes(uint32_t T);
+int occupancy(int which, size_t smem);
+}  // namespace acx
+
+using namespace acx;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t n) {
+        if (n <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max(n, cap + cap / 4);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            e = cudaMalloc(&p, n);
+            if (e != cudaSuccess) { p = nullptr; return e; }
+            want = n;
+        }
+        cap = want;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+constexpr uint32_t kMaxCounters = 4096 + 2;
+
+}  // namespace
+
+struct aceapex_ctx {
+    int device = 0;
+    aceapex_dec_params params{};
+    std::string err;
+    int n_sms = 0;
+    DevBuf streams, state, pmap, arcs, in_arc, out_buf;
+    uint32_t* counters = nullptr;  // device
+    int* d_err = nullptr;          // device
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    uint32_t state_blocks = 0;     // blocks covered by the zero-initialised state region
+};
+
+struct aceapex_archive {
+    aceapex_ctx* ctx = nullptr;
+    const void* d_arc = nullptr;
+    Plan plan;
+    BlockDev* d_blk = nullptr;
+    uint32_t* d_dtab = nullptr;
+};
+
+static int fail(aceapex_ctx* c, int code, const std::string& m) {
+    if (c) c->err = m;
+    return code;
+}
+static int cuda_fail(aceapex_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, ACEAPEX_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" {
+
+const char* aceapex_status_string(int s) {
+    switch (s) {
+        case ACEAPEX_OK: return "ok";
+        case ACEAPEX_E_ARG: return "invalid argument";
+        case ACEAPEX_E_CORRUPT: return "corrupt archive";
+        case ACEAPEX_E_NOMEM: return "out of memory";
+        case ACEAPEX_E_CUDA: return "CUDA error";
+        case ACEAPEX_E_TIMEOUT: return "device dependency wait timed out";
+        case ACEAPEX_E_RANGE: return "range outside the archive";
+        case ACEAPEX_E_BUSY: return "admission refused";
+        default: return "unknown status";
+    }
+}
+
+const char* aceapex_last_error(const aceapex_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int aceapex_ctx_create(int device, const aceapex_dec_params* params, aceapex_ctx** out) {
+    if (!out) return ACEAPEX_E_ARG;
+    *out = nullptr;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return ACEAPEX_E_CUDA;
+    aceapex_ctx* c = new (std::nothrow) aceapex_ctx();
+    if (!c) return ACEAPEX_E_NOMEM;
+    c->device = device;
+    if (params) c->params = *params;
+    if (!c->params.timeout_us) c->params.timeout_us = 2000000;
+    if (cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&c->counters, kMaxCounters * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->counters, 0, kMaxCounters * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        aceapex_ctx_destroy(c);
+        return ACEAPEX_E_CUDA;
+    }
+    for (auto& ev : c->ev) {
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            aceapex_ctx_destroy(c);
+            return ACEAPEX_E_CUDA;
+        }
+    }
+    *out = c;
+    return ACEAPEX_OK;
+}
+
+int aceapex_ctx_destroy(aceapex_ctx* c) {
+    if (!c) return ACEAPEX_E_ARG;
+    cudaSetDevice(c->device);
+    c->streams.release();
+    c->state.release();
+    c->pmap.release();
+    c->arcs.release();
+    c->in_arc.release();
+    c->out_buf.release();
+    if (c->counters) cudaFree(c->counters);
+    if (c->d_err) cudaFree(c->d_err);
+    for (auto& ev : c->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete c;
+    return ACEAPEX_OK;
+}
+
+int aceapex_ctx_set_params(aceapex_ctx* c, const aceapex_dec_params* p) {
+    if (!c || !p) return ACEAPEX_E_ARG;
+    c->params = *p;
+    if (!c->params.timeout_us) c->params.timeout_us = 2000000;
+    return ACEAPEX_OK;
+}
+
+int aceapex_encode(const uint8_t* src, uint64_t n, const aceapex_enc_params* p, uint8_t** out, uint64_t* out_len) {
+    aceapex_enc_params d{};
+    if (p) d = *p;
+    return encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, out, out_len);
+}
+
+void aceapex_free(void* p) { free(p); }
+
+int aceapex_archive_open(aceapex_ctx* c, const void* d_arc, const void* h_arc, uint64_t len, aceapex_archive** out) {
+    if (!c || !out || !h_arc || !d_arc) return fail(c, ACEAPEX_E_ARG, "archive_open: null argument");
+    *out = nullptr;
+    cudaSetDevice(c->device);
+    aceapex_archive* A = new (std::nothrow) aceapex_archive();
+    if (!A) return fail(c, ACEAPEX_E_NOMEM, "archive_open: host allocation");
+    std::string why;
+    if (build_plan((const uint8_t*)h_arc, len, &A->plan, &why) != 0) {
+        delete A;
+        return fail(c, ACEAPEX_E_CORRUPT, "archive_open: " + why);
+    }
+    A->ctx = c;
+    A->d_arc = d_arc;
+    const size_t nb = A->plan.blk.size();
+    cudaError_t e = cudaMalloc(&A->d_blk, std::max<size_t>(nb, 1) * sizeof(BlockDev));
+    if (e == cudaSuccess) e = cudaMalloc(&A->d_dtab, 4 * kM * sizeof(uint32_t));
+    if (e == cudaSuccess && nb) e = cudaMemcpy(A->d_blk, A->plan.blk.data(), nb * sizeof(BlockDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(A->d_dtab, A->plan.dtab.data(), 4 * kM * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        aceapex_archive_close(A);
+        return cuda_fail(c, e, "archive_open");
+    }
+    *out = A;
+    return ACEAPEX_OK;
+}
+
+int aceapex_archive_close(aceapex_archive* A) {
+    if (!A) return ACEAPEX_E_ARG;
+    if (A->ctx) cudaSetDevice(A->ctx->device);
+    if (A->d_blk) cudaFree(A->d_blk);
+    if (A->d_dtab) cudaFree(A->d_dtab);
+    delete A;
+    return ACEAPEX_OK;
+}
+
+int aceapex_archive_check(const void* h_arc, uint64_t len, aceapex_archive_info* info) {
+    if (!h_arc) return ACEAPEX_E_ARG;
+    Plan P;
+    std::string why;
+    if (build_plan((const uint8_t*)h_arc, len, &P, &why) != 0) return ACEAPEX_E_CORRUPT;
+    if (info) {
+        info->total_size = P.total;
+        info->n_blocks = P.n_blocks;
+        info->flags = P.flags;
+        info->min_match = P.min_match;
+        info->max_tokens = P.max_tok;
+        info->archive_bytes = P.archive_bytes;
+        info->tokens = P.tokens;
+    }
+    return ACEAPEX_OK;
+}
+
+int aceapex_archive_get_info(const aceapex_archive* A, aceapex_archive_info* info) {
+    if (!A || !info) return ACEAPEX_E_ARG;
+    info->total_size = A->plan.total;
+    info->n_blocks = A->plan.n_blocks;
+    info->flags = A->plan.flags;
+    info->min_match = A->plan.min_match;
+    info->max_tokens = A->plan.max_tok;
+    info->archive_bytes = A->plan.archive_bytes;
+    info->tokens = A->plan.tokens;
+    return ACEAPEX_OK;
+}
+
+}  // extern "C"
+
+// Enqueue the whole decode of one archive.  ev (optional) receives three
+// event records: start, after the entropy stage, after assembly.
+static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc, void* d_out, cudaStream_t st,
+                          bool timed) {
+    const Plan& P = A->plan;
+    cudaError_t e;
+    if ((e = c->streams.ensure(P.scratch_bytes)) != cudaSuccess) return cuda_fail(c, e, "scratch allocation");
+    const size_t nb = std::max<size_t>(P.n_blocks, 1);
+    if (c->state_blocks < nb) {
+        if ((e = c->state.ensure(nb * 4)) != cudaSuccess) return cuda_fail(c, e, "state allocation");
+        if ((e = cudaMemsetAsync(c->state.p, 0, nb * 4, st)) != cudaSuccess) return cuda_fail(c, e, "state init");
+        c->state_blocks = (uint32_t)nb;
+    }
+    if ((e = c->pmap.ensure(nb * (kBlock / 8))) != cudaSuccess) return cuda_fail(c, e, "bitmap allocation");
+    JobDev job{};
+    ArcJob& J = job.one;
+    J.arc = (const uint8_t*)d_arc;
+    J.blk = A->d_blk;
+    J.dtab = A->d_dtab;
+    J.scratch = (uint8_t*)c->streams.p;
+    J.out = (uint8_t*)d_out;
+    J.state = (uint32_t*)c->state.p;
+    J.pmap = (uint32_t*)c->pmap.p;
+    J.total = P.total;
+    J.n_blocks = P.n_blocks;
+    J.lo = 0;
+    J.hi = P.n_blocks;
+    J.min_match = P.min_match;
+    J.item_base = 0;
+    job.arcs = nullptr;
+    job.n_arcs = 1;
+    job.n_items = P.n_blocks;
+    job.counters = c->counters;
+    job.err = c->d_err;
+    job.timeout_ns = (uint64_t)c->params.timeout_us * 1000ull;
+    job.max_tok = P.max_tok;
+    job.max_lenb = P.max_lenb;
+    if (P.n_blocks == 0) return ACEAPEX_OK;
+    if (timed && (e = cudaEventRecord(c->ev[0], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    if ((e = launch_prologue(c->counters, 2 + 1, st)) != cudaSuccess) return cuda_fail(c, e, "prologue launch");
+    const int occ_r = std::max(1, occupancy(0, rans_smem_bytes()));
+    if ((e = launch_rans(job, occ_r * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "rANS launch");
+    if (timed && (e = cudaEventRecord(c->ev[1], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    if (c->params.variant == ACEAPEX_VARIANT_PLAIN) {
+        const int occ = std::max(1, occupancy(2, plain_smem_bytes(P.max_tok)));
+        if ((e = launch_plain(job, occ * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "plain launch");
+    } else {
+        const size_t sm = asm_smem_bytes(P.max_tok, P.max_lenb);
+        if (sm > 227 * 1024) return fail(c, ACEAPEX_E_CORRUPT, "block too large for the assembly kernel");
+        int occ = std::max(1, occupancy(1, sm));
+        if (c->params.ctas_per_sm) occ = std::min<int>(occ, (int)c->params.ctas_per_sm);
+        if ((e = launch_assemble(job, occ * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "assembly launch");
+    }
+    if (timed && (e = cudaEventRecord(c->ev[2], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    return ACEAPEX_OK;
+}
+
+static int read_status(aceapex_ctx* c, cudaStream_t st) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    int h = 0;
+    if ((e = cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(c, e, "error word");
+    if (h) {
+        cudaMemset(c->d_err, 0, sizeof(int));
+        return fail(c, h, std::string("device reported: ") + aceapex_status_string(h));
+    }
+    return ACEAPEX_OK;
+}
+
+static void fill_stats(aceapex_ctx* c, const Plan& P, aceapex_stats* s) {
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+    s->ms_ans = a;
+    s->ms_parse = b;
+    s->ms_copy = 0;
+    s->ms_total = a + b;
+    s->blocks = P.n_blocks;
+    s->bytes = P.total;
+}
+
+extern "C" {
+
+int aceapex_decode_all_async(aceapex_ctx* c, aceapex_archive* A, void* d_out, uint64_t out_cap, void* stream) {
+    if (!c || !A || (!d_out && A->plan.total)) return fail(c, ACEAPEX_E_ARG, "decode_all: null argument");
+    if (out_cap < A->plan.total) return fail(c, ACEAPEX_E_ARG, "decode_all: output buffer too small");
+    cudaSetDevice(c->device);
+    return enqueue_decode(c, A, A->d_arc, d_out, (cudaStream_t)stream, false);
+}
+
+int aceapex_sync(aceapex_ctx* c, void* stream) {
+    if (!c) return ACEAPEX_E_ARG;
+    cudaSetDevice(c->device);
+    return read_status(c, (cudaStream_t)stream);
+}
+
+int aceapex_decode_all(aceapex_ctx* c, aceapex_archive* A, void* d_out, uint64_t out_cap, void* stream,
+                       aceapex_stats* stats) {
+    if (!c || !A || (!d_out && A->plan.total)) return fail(c, ACEAPEX_E_ARG, "decode_all: null argument");
+    if (out_cap < A->plan.total) return fail(c, ACEAPEX_E_ARG, "decode_all: output buffer too small");
+    cudaSetDevice(c->device);
+    int rc = enqueue_decode(c, A, A->d_arc, d_out, (cudaStream_t)stream, stats != nullptr);
+    if (rc) return rc;
+    rc = read_status(c, (cudaStream_t)stream);
+    if (rc == ACEAPEX_OK && stats) fill_stats(c, A->plan, stats);
+    return rc;
+}
+
+int aceapex_decode_host(aceapex_ctx* c, aceapex_archive* A, const void* h_arc, uint64_t arc_len, void* h_out,
+                        uint64_t out_cap, void* stream, aceapex_stats* stats) {
+    if (!c || !h_arc || !h_out) return fail(c, ACEAPEX_E_ARG, "decode_host: null argument");
+    cudaSetDevice(c->device);
+    aceapex_archive* tmp = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = c->in_arc.ensure(arc_len + 16)) != cudaSuccess) return cuda_fail(c, e, "archive buffer");
+    if (!A) {
+        int rc = aceapex_archive_open(c, c->in_arc.p, h_arc, arc_len, &tmp);
+        if (rc) return rc;
+        A = tmp;
+    }
+    int rc = ACEAPEX_OK;
+    if (out_cap < A->plan.total) rc = fail(c, ACEAPEX_E_ARG, "decode_host: output buffer too small");
+    else if ((e = c->out_buf.ensure(A->plan.total + 16)) != cudaSuccess) rc = cuda_fail(c, e, "output buffer");
+    if (rc == ACEAPEX_OK && stats && (e = cudaEventRecord(c->ev[0], st)) != cudaSuccess) rc = cuda_fail(c, e, "event");
+    if (rc == ACEAPEX_OK && (e = cudaMemcpyAsync(c->in_arc.p, h_arc, arc_len, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        rc = cuda_fail(c, e, "archive upload");
+    if (rc == ACEAPEX_OK) rc = enqueue_decode(c, A, c->in_arc.p, c->out_buf.p, st, false);
+    if (rc == ACEAPEX_OK &&
+        (e = cudaMemcpyAsync(h_out, c->out_buf.p, A->plan.total, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        rc = cuda_fail(c, e, "output download");
+    if (rc == ACEAPEX_OK && stats && (e = cudaEventRecord(c->ev[2], st)) != cudaSuccess) rc = cuda_fail(c, e, "event");
+    if (rc == ACEAPEX_OK) rc = read_status(c, st);
+    if (rc == ACEAPEX_OK && stats) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[2]);
+        memset(stats, 0, sizeof *stats);
+        stats->ms_total = ms;
+        stats->blocks = A->plan.n_blocks;
+        stats->bytes = A->plan.total;
+    }
+    if (tmp) aceapex_archive_close(tmp);
+    return rc;
+}
+
+}  // extern "C"

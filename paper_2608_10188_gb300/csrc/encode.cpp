@@ -1,0 +1,391 @@
+// Library encoder for format v1 (host, C++).
+//
+// Paper, Setup: the encoder performs a global match search and stores every
+// back-reference as an absolute position in the output, cut into 16 KiB
+// blocks.  "The Last Sequential Element": with no_rep the repeat codes are
+// suppressed and every match goes out with an explicit offset, keeping the
+// same matches (so the history-free archive differs only in coding).
+//
+// Match search: a long-window hash (16 bytes, any distance, most recent
+// position) finds copies anywhere earlier; a short-window hash (6 bytes,
+// recent positions) finds local repeats; the four history distances and
+// distances 1..4 are always tried.  A match is taken when its estimated
+// saving in bits (length x literal cost - token cost) is positive, which
+// keeps chance k-mer hits out of the token stream.  The parse is sequential;
+// stream construction, frequency counting and rANS coding run on threads.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+#include "plan.h"
+
+namespace acx {
+
+uint64_t fnv1a64(const uint8_t* p, uint64_t n) {
+    uint64_t h = 0xcbf29ce484222325ULL;
+    for (uint64_t i = 0; i < n; i++) h = (h ^ p[i]) * 0x100000001b3ULL;
+    return h;
+}
+
+namespace {
+
+struct BlockStreams {
+    std::vector<uint8_t> s[4];
+};
+
+inline uint64_t load64(const uint8_t* p) {
+    uint64_t v;
+    memcpy(&v, p, 8);
+    return v;
+}
+
+inline uint32_t common_len(const uint8_t* a, const uint8_t* b, uint64_t limit) {
+    uint64_t L = 0;
+    while (L + 8 <= limit) {
+        uint64_t x = load64(a + L) ^ load64(b + L);
+        if (x) return (uint32_t)(L + (__builtin_ctzll(x) >> 3));
+        L += 8;
+    }
+    while (L < limit && a[L] == b[L]) L++;
+    return (uint32_t)L;
+}
+
+// Byte-serial match length allowing overlap (source may run into the destination).
+inline uint32_t overlap_len(const uint8_t* s, uint64_t pos, uint64_t src, uint64_t limit) {
+    if (pos - src >= 8) return common_len(s + pos, s + src, limit);
+    uint64_t L = 0;
+    while (L < limit && s[src + L] == s[pos + L]) L++;
+    return (uint32_t)L;
+}
+
+void put_varint(std::vector<uint8_t>& v, uint32_t x) {
+    while (x >= 0x80) {
+        v.push_back((uint8_t)(x | 0x80));
+        x >>= 7;
+    }
+    v.push_back((uint8_t)x);
+}
+
+// Largest-remainder normalisation of counts to 4096 with every present symbol >= 1.
+void normalise(const uint64_t cnt[256], uint16_t f[256]) {
+    uint64_t tot = 0;
+    for (int s = 0; s < 256; s++) tot += cnt[s];
+    memset(f, 0, 512);
+    if (!tot) return;
+    double rem[256];
+    int sum = 0;
+    for (int s = 0; s < 256; s++) {
+        if (!cnt[s]) { rem[s] = -1; continue; }
+        double ideal = (double)cnt[s] * kM / (double)tot;
+        int v = (int)ideal;
+        if (v < 1) v = 1;
+        f[s] = (uint16_t)v;
+        rem[s] = ideal - v;
+        sum += v;
+    }
+    while (sum < (int)kM) {  // hand out the remainder by largest fractional part
+        int best = -1;
+        for (int s = 0; s < 256; s++)
+            if (cnt[s] && (best < 0 || rem[s] > rem[best])) best = s;
+        f[best]++;
+        rem[best] -= 1.0;
+        sum++;
+    }
+    while (sum > (int)kM) {  // too many forced ones: take from the largest entries
+        int best = -1;
+        for (int s = 0; s < 256; s++)
+            if (f[s] > 1 && (best < 0 || f[s] > f[best])) best = s;
+        f[best]--;
+        sum--;
+    }
+}
+
+// Interleaved rANS encoder, K lanes; returns body bytes (states padded to 16, then words).
+std::vector<uint8_t> rans_encode(const uint8_t* sym, uint32_t n, uint32_t K, const uint16_t f[256]) {
+    uint32_t c[256], acc = 0;
+    for (int s = 0; s < 256; s++) { c[s] = acc; acc += f[s]; }
+    std::vector<uint32_t> x(K, kL);
+    std::vector<uint16_t> w;
+    w.reserve(n / 2 + 16);
+    for (uint32_t i = n; i-- > 0;) {
+        uint32_t& st = x[i & (K - 1)];
+        const uint32_t fs = f[sym[i]];
+        if (st >= (fs << 20)) {
+            w.push_back((uint16_t)st);
+            st >>= 16;
+        }
+        st = (st / fs) * kM + st % fs + c[sym[i]];
+    }
+    const uint32_t hdr = (4 * K + 15) & ~15u;
+    std::vector<uint8_t> body(hdr + 2 * w.size(), 0);
+    for (uint32_t j = 0; j < K; j++) memcpy(&body[4 * j], &x[j], 4);
+    for (size_t k = 0; k < w.size(); k++) memcpy(&body[hdr + 2 * k], &w[w.size() - 1 - k], 2);
+    return body;
+}
+
+struct Parser {
+    const uint8_t* s;
+    uint64_t n;
+    bool no_rep;
+    uint32_t min_match;
+    double lit_bits;
+    int lbits, sbits;
+    std::vector<uint64_t> hl;  // 16-byte window -> most recent position + 1
+    std::vector<uint32_t> hs;  // 6-byte window  -> most recent position + 1 (low 32 bits)
+
+    static inline uint32_t hash_long(const uint8_t* p, int bits) {
+        const uint64_t a = load64(p), b = load64(p + 8);
+        return (uint32_t)(((a * 0x9E3779B97F4A7C15ULL) ^ (b * 0xC2B2AE3D27D4EB4FULL)) >> (64 - bits));
+    }
+    static inline uint32_t hash_short(const uint8_t* p, int bits) {
+        const uint64_t a = load64(p) & 0xFFFFFFFFFFFFULL;
+        return (uint32_t)((a * 0xCF1BBCDCB7A56463ULL) >> (64 - bits));
+    }
+    void insert(uint64_t p) {
+        if (p + 16 <= n) hl[hash_long(s + p, lbits)] = p + 1;
+        if (p + 8 <= n) hs[hash_short(s + p, sbits)] = (uint32_t)(p + 1);
+    }
+    // cost in bits of a NEW token (cmd + two varints + absolute offset)
+    double new_cost(uint64_t src) const {
+        int bits = 1;
+        while (bits < 40 && (src >> bits)) bits++;
+        return 18.0 + bits;
+    }
+
+    void parse_block(uint64_t B, uint64_t E, BlockStreams& out, uint64_t& ins) {
+        std::vector<uint8_t>& cmd = out.s[kCmd];
+        std::vector<uint8_t>& len = out.s[kLen];
+        std::vector<uint8_t>& lit = out.s[kLit];
+        std::vector<uint64_t> srcs;
+        uint64_t hist[4] = {1, 2, 3, 4};
+        uint64_t pos = B, lit0 = B;
+        while (pos < E) {
+            while (ins < pos) insert(ins++);
+            if (pos + 24 <= n) __builtin_prefetch(&hl[hash_long(s + pos + 8, lbits)]);
+            const uint64_t limit = E - pos;
+            uint32_t bestL = 0;
+            uint64_t bestD = 0;
+            int bestRep = -1;
+            double bestGain = 0.0;
+            auto consider = [&](uint64_t d, int rep_idx) {
+                if (d == 0 || d > pos) return;
+                const uint32_t L = overlap_len(s, pos, pos - d, limit);
+                if (L < min_match) return;
+                int ri = rep_idx;
+                if (ri < 0)
+                    for (int j = 0; j < 4; j++)
+                        if (hist[j] == d) { ri = j; break; }
+                // costs in history-mode terms in both modes, so the history-free
+                // archive keeps exactly the same matches
+                const double cost = ri >= 0 ? 14.0 : new_cost(pos - d);
+                const double gain = L * lit_bits - cost;
+                if (gain > bestGain) { bestGain = gain; bestL = L; bestD = d; bestRep = ri; }
+            };
+            for (int j = 0; j < 4; j++) consider(hist[j], j);
+            for (uint64_t d = 1; d <= 4; d++) consider(d, -1);
+            if (pos + 16 <= n) {
+                const uint64_t q = hl[hash_long(s + pos, lbits)];
+                if (q) consider(pos - (q - 1), -1);
+            }
+            if (pos + 8 <= n) {
+                const uint64_t q = hs[hash_short(s + pos, sbits)];
+                if (q && q - 1 < pos && pos - (q - 1) < (1u << 22)) consider(pos - (q - 1), -1);
+            }
+            if (!bestL) { pos++; continue; }
+            const uint32_t LL = (uint32_t)(pos - lit0);
+            const bool rep_code = bestRep >= 0 && !no_rep;
+            cmd.push_back(rep_code ? (uint8_t)(1 + bestRep) : kNew);
+            put_varint(len, LL);
+            put_varint(len, bestL);
+            lit.insert(lit.end(), s + lit0, s + pos);
+            if (!rep_code) srcs.push_back(pos - bestD);
+            // the history follows the history-mode rules in both modes
+            if (bestRep >= 0) {
+                const uint64_t d = hist[bestRep];
+                for (int j = bestRep; j > 0; j--) hist[j] = hist[j - 1];
+                hist[0] = d;
+            } else {
+                hist[3] = hist[2]; hist[2] = hist[1]; hist[1] = hist[0]; hist[0] = bestD;
+            }
+            pos += bestL;
+            lit0 = pos;
+        }
+        if (lit0 < E) {
+            cmd.push_back(kLitOnly);
+            put_varint(len, (uint32_t)(E - lit0));
+            put_varint(len, 0);
+            lit.insert(lit.end(), s + lit0, s + E);
+        }
+        std::vector<uint8_t>& off = out.s[kOff];
+        off.resize(5 * srcs.size());
+        for (int p = 0; p < 5; p++)
+            for (size_t i = 0; i < srcs.size(); i++) off[p * srcs.size() + i] = (uint8_t)(srcs[i] >> (8 * p));
+    }
+};
+
+template <class F>
+void parallel_for(uint32_t n, int threads, F fn) {
+    std::atomic<uint32_t> next(0);
+    auto work = [&]() {
+        for (;;) {
+            uint32_t i = next.fetch_add(1);
+            if (i >= n) break;
+            fn(i);
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < threads; t++) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+}
+
+}  // namespace
+
+int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
+                   uint8_t** out, uint64_t* out_len) {
+    if (!out || !out_len || (n && !src)) return -1;
+    if (min_match == 0) min_match = 4;
+    if (max_lanes == 0) max_lanes = 32;
+    if (min_match < 4 || min_match > kBlock || max_lanes > kMaxLanes || (max_lanes & (max_lanes - 1))) return -1;
+    if (n >= (1ull << 40)) return -1;  // absolute offsets are 40-bit
+    if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+    const uint32_t nb = (uint32_t)((n + kBlock - 1) / kBlock);
+    std::vector<BlockStreams> blocks(nb);
+    try {
+        // order-0 literal cost estimate
+        uint64_t hist[256] = {0};
+        for (uint64_t i = 0; i < n; i++) hist[src[i]]++;
+        double H = 0.0;
+        for (int c = 0; c < 256; c++)
+            if (hist[c]) {
+                const double p = (double)hist[c] / (double)n;
+                H -= p * log2(p);
+            }
+        Parser P;
+        P.s = src;
+        P.n = n;
+        P.no_rep = no_rep != 0;
+        P.min_match = min_match;
+        P.lit_bits = std::max(H, 1.0) + 0.1;
+        P.lbits = 16;
+        while (P.lbits < 27 && (1ull << P.lbits) < n) P.lbits++;
+        P.sbits = std::min(P.lbits, 22);
+        P.hl.assign(1ull << P.lbits, 0);
+        P.hs.assign(1ull << P.sbits, 0);
+        uint64_t ins = 0;
+        for (uint32_t b = 0; b < nb; b++) {
+            const uint64_t B = (uint64_t)b * kBlock, E = std::min<uint64_t>(n, B + kBlock);
+            P.parse_block(B, E, blocks[b], ins);
+        }
+    } catch (...) {
+        return -3;
+    }
+    // global frequency tables
+    uint16_t freq[4][256];
+    {
+        std::vector<std::vector<uint64_t>> part(threads, std::vector<uint64_t>(4 * 256, 0));
+        std::atomic<int> tid(0);
+        const uint32_t per = (nb + threads - 1) / threads;
+        parallel_for((uint32_t)threads, threads, [&](uint32_t t) {
+            std::vector<uint64_t>& c = part[t];
+            for (uint32_t b = t * per; b < std::min(nb, (t + 1) * per); b++)
+                for (int s = 0; s < 4; s++)
+                    for (uint8_t v : blocks[b].s[s]) c[s * 256 + v]++;
+        });
+        (void)tid;
+        for (int s = 0; s < 4; s++) {
+            uint64_t cnt[256] = {0};
+            for (int t = 0; t < threads; t++)
+                for (int k = 0; k < 256; k++) cnt[k] += part[t][s * 256 + k];
+            normalise(cnt, freq[s]);
+        }
+    }
+    // per-block payloads
+    std::vector<std::vector<uint8_t>> pay(nb);
+    parallel_for(nb, threads, [&](uint32_t b) {
+        std::vector<uint8_t>& P = pay[b];
+        P.assign(48, 0);
+        for (int s = 0; s < 4; s++) {
+            const std::vector<uint8_t>& raw = blocks[b].s[s];
+            const uint32_t rn = (uint32_t)raw.size();
+            std::vector<uint8_t> body;
+            uint8_t mode = 0, K = 0;
+            bool table = false;
+            {
+                uint32_t sum = 0;
+                for (int k = 0; k < 256; k++) sum += freq[s][k];
+                table = sum == kM;
+            }
+            if (rn >= 16 && table) {
+                uint32_t k = 1;
+                while (2 * k <= max_lanes && 64 * (2 * k) <= rn) k *= 2;
+                std::vector<uint8_t> enc = rans_encode(raw.data(), rn, k, freq[s]);
+                if (enc.size() < rn) {
+                    body.swap(enc);
+                    mode = 1;
+                    K = (uint8_t)k;
+                }
+            }
+            if (!mode) body = raw;
+            uint8_t* d = &P[12 * s];
+            const uint32_t el = (uint32_t)body.size();
+            memcpy(d, &rn, 4);
+            memcpy(d + 4, &el, 4);
+            d[8] = mode;
+            d[9] = K;
+            P.insert(P.end(), body.begin(), body.end());
+            P.resize((P.size() + 15) & ~(size_t)15, 0);
+        }
+        blocks[b] = BlockStreams();
+    });
+    const uint64_t off_tab = 64, off_idx = 64 + 2048, off_pay = (off_idx + 40ull * nb + 15) & ~15ull;
+    uint64_t total = off_pay;
+    std::vector<uint64_t> poff(nb);
+    for (uint32_t b = 0; b < nb; b++) {
+        poff[b] = total;
+        total += pay[b].size();
+    }
+    uint8_t* a = (uint8_t*)calloc(total ? total : 1, 1);
+    if (!a) return -3;
+    memcpy(a, "ACX1", 4);
+    const uint16_t ver = 1, flags = no_rep ? 1 : 0;
+    const uint32_t bs = kBlock;
+    memcpy(a + 4, &ver, 2);
+    memcpy(a + 6, &flags, 2);
+    memcpy(a + 8, &bs, 4);
+    memcpy(a + 12, &min_match, 4);
+    memcpy(a + 16, &n, 8);
+    memcpy(a + 24, &nb, 4);
+    memcpy(a + 32, &off_tab, 8);
+    memcpy(a + 40, &off_idx, 8);
+    const uint64_t zero = 0;
+    memcpy(a + 48, &zero, 8);
+    memcpy(a + 56, &off_pay, 8);
+    for (int s = 0; s < 4; s++) memcpy(a + off_tab + 512 * s, freq[s], 512);
+    parallel_for(nb, threads, [&](uint32_t b) {
+        uint8_t* e = a + off_idx + 40ull * b;
+        const uint64_t B = (uint64_t)b * kBlock;
+        const uint32_t R = (uint32_t)std::min<uint64_t>(kBlock, n - B);
+        const uint32_t pl = (uint32_t)pay[b].size();
+        uint32_t ntok;
+        memcpy(&ntok, &pay[b][0], 4);  // cmd raw length = token count
+        memcpy(e, &poff[b], 8);
+        memcpy(e + 8, &pl, 4);
+        memcpy(e + 12, &ntok, 4);
+        memcpy(e + 16, &R, 4);
+        const uint64_t h = fnv1a64(src + B, R);
+        memcpy(e + 32, &h, 8);
+        memcpy(a + poff[b], pay[b].data(), pay[b].size());
+    });
+    *out = a;
+    *out_len = total;
+    return 0;
+}
+
+}  // namespace acx

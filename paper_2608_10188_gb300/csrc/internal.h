@@ -1,0 +1,73 @@
+// Internal definitions shared by the host library and the CUDA kernels.
+// Format v1 constants and the device-resident decode plan.
+#pragma once
+#include <stdint.h>
+
+namespace acx {
+
+constexpr uint32_t kBlock = 16384;     // fixed block size (paper, Setup / Reproducibility: 16,384 B)
+constexpr uint32_t kProbBits = 12;     // rANS probability precision
+constexpr uint32_t kM = 1u << kProbBits;
+constexpr uint32_t kL = 1u << 16;      // rANS lower bound of the state interval [L, 2^32)
+constexpr int kCmd = 0, kLen = 1, kOff = 2, kLit = 3;
+constexpr uint32_t kMaxLanes = 128;
+constexpr uint32_t kMaxStreamRaw = 4 * kBlock + 16;
+
+// Command codes of the cmd stream.
+constexpr uint8_t kNew = 0;       // explicit absolute offset
+constexpr uint8_t kRep0 = 1;      // 1..4: distance from history entry 0..3
+constexpr uint8_t kLitOnly = 5;   // final literal run without a match
+
+// Per-block decode plan (device-resident, built by the host at archive open).
+struct BlockDev {
+    uint64_t payload;      // archive offset of the block payload
+    uint64_t scratch;      // offset of the block's decoded streams in the stream scratch
+    uint32_t raw_len;      // decompressed bytes of the block
+    uint32_t n_tok;        // tokens (= cmd stream length)
+    uint32_t n_new;        // NEW tokens (= off stream length / 5)
+    uint32_t rans_mask;    // bit s: stream s is rANS coded
+    uint32_t s_raw[4];     // decoded lengths of cmd, len, off, lit
+    uint32_t s_body[4];    // body offset relative to the payload
+    uint32_t s_enc[4];     // body length in bytes (without padding)
+    uint32_t s_off[4];     // offset of each decoded stream inside the block's scratch region
+    uint8_t s_K[4];        // rANS lanes
+    uint32_t pad[3];
+};
+static_assert(sizeof(BlockDev) % 16 == 0, "BlockDev alignment");
+
+// Publish states of a block during one decode call (low 2 bits), tagged with
+// the call's epoch in the upper 30 bits so no reset is needed between calls.
+constexpr uint32_t kStPublished = 1;   // block written, some bytes still pending (see pending bitmap)
+constexpr uint32_t kStComplete = 2;    // every byte of the block is final
+constexpr uint32_t kStAlways = 0xFFFFFFFFu;  // block final independently of the epoch (cache)
+
+// One archive inside a decode job.
+struct ArcJob {
+    const uint8_t* arc;       // archive bytes (device)
+    const BlockDev* blk;      // plan
+    const uint32_t* dtab;     // 4 x 4096 rANS decode entries: sym | (f-1)<<8 | (slot-c)<<20
+    uint8_t* scratch;         // decoded streams
+    uint8_t* out;             // output: block b at out + b*kBlock
+    uint32_t* state;          // per block publish state
+    uint32_t* pmap;           // per block pending bitmap, 512 words per block
+    uint64_t total;           // decompressed size
+    uint32_t n_blocks;
+    uint32_t lo, hi;          // blocks [lo, hi) are decoded by this job
+    uint32_t min_match;
+    uint32_t item_base;       // first item index of this archive in the job's item space
+    uint32_t pad;
+};
+
+struct JobDev {
+    ArcJob one;               // the archive when arcs == nullptr
+    const ArcJob* arcs;       // device array of archives (batched jobs), or nullptr
+    uint32_t n_arcs;
+    uint32_t n_items;         // total blocks over all archives
+    uint32_t* counters;       // [0] epoch, [1] assembly ticket, [2 + a] rANS ticket of archive a
+    int* err;                 // first error status (0 = ok)
+    uint64_t timeout_ns;
+    uint32_t max_tok;         // shared-memory sizing of the assembly kernel
+    uint32_t max_lenb;
+};
+
+}  // namespace acx

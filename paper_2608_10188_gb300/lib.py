@@ -1,0 +1,216 @@
+"""Thin ctypes binding of libaceapex.so (argument marshalling only).
+
+Names follow the C ABI in include/aceapex.h.  Device buffers are passed as
+raw device pointers (e.g. ``tensor.data_ptr()`` of a torch CUDA tensor) and
+streams as ``cudaStream_t`` handles (``torch.cuda.current_stream().cuda_stream``).
+Every step of the decode runs in the library's CUDA kernels; there is no CPU
+fallback: if the shared library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+OK, E_ARG, E_CORRUPT, E_NOMEM, E_CUDA, E_TIMEOUT, E_RANGE, E_BUSY = 0, -1, -2, -3, -4, -5, -6, -7
+VARIANT_FAST, VARIANT_PLAIN = 0, 1
+BLOCK_SIZE = 16384
+
+EXPORTED = [
+    "aceapex_status_string", "aceapex_last_error", "aceapex_ctx_create", "aceapex_ctx_destroy",
+    "aceapex_ctx_set_params", "aceapex_encode", "aceapex_free", "aceapex_archive_open", "aceapex_archive_close",
+    "aceapex_archive_get_info", "aceapex_decode_all", "aceapex_decode_all_async", "aceapex_sync",
+    "aceapex_decode_host", "aceapex_archive_check",
+]
+
+
+class EncParams(ctypes.Structure):
+    _fields_ = [("no_rep", ctypes.c_int), ("min_match", ctypes.c_uint32), ("max_lanes", ctypes.c_uint32),
+                ("threads", ctypes.c_int)]
+
+
+class DecParams(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_uint32), ("timeout_us", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("ms_ans", ctypes.c_double), ("ms_parse", ctypes.c_double),
+                ("ms_copy", ctypes.c_double), ("blocks", ctypes.c_uint64), ("bytes", ctypes.c_uint64)]
+
+
+class ArchiveInfo(ctypes.Structure):
+    _fields_ = [("total_size", ctypes.c_uint64), ("n_blocks", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("min_match", ctypes.c_uint32), ("max_tokens", ctypes.c_uint32),
+                ("archive_bytes", ctypes.c_uint64), ("tokens", ctypes.c_uint64)]
+
+
+class AceapexError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"aceapex status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libaceapex.so (must have been built with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.SO
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (python -m paper_2608_10188_gb300.build)")
+    L = ctypes.CDLL(path)
+    c = ctypes
+    vp, u64, u32 = c.c_void_p, c.c_uint64, c.c_uint32
+    L.aceapex_status_string.argtypes = [c.c_int]
+    L.aceapex_status_string.restype = c.c_char_p
+    L.aceapex_last_error.argtypes = [vp]
+    L.aceapex_last_error.restype = c.c_char_p
+    L.aceapex_ctx_create.argtypes = [c.c_int, c.POINTER(DecParams), c.POINTER(vp)]
+    L.aceapex_ctx_destroy.argtypes = [vp]
+    L.aceapex_ctx_set_params.argtypes = [vp, c.POINTER(DecParams)]
+    L.aceapex_encode.argtypes = [vp, u64, c.POINTER(EncParams), c.POINTER(vp), c.POINTER(u64)]
+    L.aceapex_free.argtypes = [vp]
+    L.aceapex_free.restype = None
+    L.aceapex_archive_open.argtypes = [vp, vp, vp, u64, c.POINTER(vp)]
+    L.aceapex_archive_close.argtypes = [vp]
+    L.aceapex_archive_get_info.argtypes = [vp, c.POINTER(ArchiveInfo)]
+    L.aceapex_archive_check.argtypes = [vp, u64, c.POINTER(ArchiveInfo)]
+    L.aceapex_decode_all.argtypes = [vp, vp, vp, u64, vp, c.POINTER(Stats)]
+    L.aceapex_decode_all_async.argtypes = [vp, vp, vp, u64, vp]
+    L.aceapex_sync.argtypes = [vp, vp]
+    L.aceapex_decode_host.argtypes = [vp, vp, vp, u64, vp, u64, vp, c.POINTER(Stats)]
+    for name in EXPORTED:
+        if name not in ("aceapex_status_string", "aceapex_last_error", "aceapex_free"):
+            getattr(L, name).restype = c.c_int
+    _lib = L
+    return L
+
+
+def _check(rc, ctx=None, what=""):
+    if rc != OK:
+        L = load()
+        msg = L.aceapex_last_error(ctx).decode() if ctx else L.aceapex_status_string(rc).decode()
+        raise AceapexError(rc, f"{what}: {msg}")
+    return rc
+
+
+def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, threads: int = 0) -> bytes:
+    """aceapex_encode on host bytes (numpy uint8 array or bytes)."""
+    import numpy as np
+    L = load()
+    a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data,
+                             dtype=np.uint8)
+    p = EncParams(int(no_rep), min_match, max_lanes, threads)
+    ptr = ctypes.c_void_p()
+    n = ctypes.c_uint64()
+    _check(L.aceapex_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(p), ctypes.byref(ptr),
+                            ctypes.byref(n)), None, "encode")
+    try:
+        return ctypes.string_at(ptr.value, n.value)
+    finally:
+        L.aceapex_free(ptr)
+
+
+class Context:
+    """aceapex_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0):
+        L = load()
+        self._L = L
+        self.params = DecParams(variant, timeout_us, ctas_per_sm, 0)
+        h = ctypes.c_void_p()
+        _check(L.aceapex_ctx_create(device, ctypes.byref(self.params), ctypes.byref(h)), None, "ctx_create")
+        self.h = h
+
+    def set_params(self, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0):
+        self.params = DecParams(variant, timeout_us, ctas_per_sm, 0)
+        _check(self._L.aceapex_ctx_set_params(self.h, ctypes.byref(self.params)), self.h, "set_params")
+
+    def close(self):
+        if self.h:
+            self._L.aceapex_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return self._L.aceapex_last_error(self.h).decode()
+
+    def sync(self, stream: int = 0) -> int:
+        return self._L.aceapex_sync(self.h, stream)
+
+
+class Archive:
+    """aceapex_archive: a validated archive with its device decode plan."""
+
+    def __init__(self, ctx: Context, d_arc: int, h_arc, arc_len: int):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        self._hbuf = h_arc
+        hp = h_arc.ctypes.data if hasattr(h_arc, "ctypes") else ctypes.cast(ctypes.c_char_p(h_arc), ctypes.c_void_p).value
+        _check(ctx._L.aceapex_archive_open(ctx.h, d_arc, hp, arc_len, ctypes.byref(h)), ctx.h, "archive_open")
+        self.h = h
+        info = ArchiveInfo()
+        _check(ctx._L.aceapex_archive_get_info(self.h, ctypes.byref(info)), ctx.h, "archive_info")
+        self.info = {k: getattr(info, k) for k, _ in ArchiveInfo._fields_}
+        self._hbuf = None
+
+    @property
+    def total(self) -> int:
+        return self.info["total_size"]
+
+    def close(self):
+        if self.h:
+            self.ctx._L.aceapex_archive_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def archive_check(h_arc) -> dict:
+    """aceapex_archive_check: host-only structural validation; returns the info dict."""
+    import numpy as np
+    L = load()
+    a = np.ascontiguousarray(np.frombuffer(h_arc, np.uint8) if isinstance(h_arc, (bytes, bytearray)) else h_arc,
+                             dtype=np.uint8)
+    info = ArchiveInfo()
+    rc = L.aceapex_archive_check(a.ctypes.data, a.size, ctypes.byref(info))
+    if rc != OK:
+        raise AceapexError(rc, "archive_check")
+    return {k: getattr(info, k) for k, _ in ArchiveInfo._fields_}
+
+
+def decode_all(ctx: Context, arc: Archive, d_out: int, out_cap: int, stream: int = 0, stats: bool = False):
+    """aceapex_decode_all: returns the status (and a Stats dict when stats=True)."""
+    st = Stats() if stats else None
+    rc = ctx._L.aceapex_decode_all(ctx.h, arc.h, d_out, out_cap, stream, ctypes.byref(st) if st else None)
+    if stats:
+        return rc, {k: getattr(st, k) for k, _ in Stats._fields_}
+    return rc
+
+
+def decode_all_async(ctx: Context, arc: Archive, d_out: int, out_cap: int, stream: int = 0) -> int:
+    return ctx._L.aceapex_decode_all_async(ctx.h, arc.h, d_out, out_cap, stream)
+
+
+def decode_host(ctx: Context, arc, h_arc, h_out, stream: int = 0, stats: bool = False):
+    """aceapex_decode_host: host archive (numpy uint8) -> host output (numpy uint8)."""
+    st = Stats() if stats else None
+    rc = ctx._L.aceapex_decode_host(ctx.h, arc.h if arc is not None else None, h_arc.ctypes.data, h_arc.size,
+                                    h_out.ctypes.data, h_out.size, stream, ctypes.byref(st) if st else None)
+    if stats:
+        return rc, {k: getattr(st, k) for k, _ in Stats._fields_}
+    return rc

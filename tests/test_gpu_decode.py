@@ -1,0 +1,172 @@
+"""Parity of the CUDA decode path (through the C ABI) with the CPU oracle.
+The bar is bit-exact output.  (-m gpu)"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from fmt_writer import build_archive
+from golden import worked_examples as W
+
+pytestmark = pytest.mark.gpu
+
+FAST, PLAIN = 0, 1
+
+
+@pytest.fixture(scope="module")
+def acx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_10188_gb300 as acx
+    acx.build.build()
+    acx.load()
+    return acx
+
+
+@pytest.fixture(scope="module")
+def ctx(acx):
+    c = acx.Context(0, timeout_us=2_000_000)
+    yield c
+    c.close()
+
+
+def dec(ctx, arc, variant=FAST):
+    from gpu_util import gpu_decode
+    return gpu_decode(ctx, arc, variant)
+
+
+@pytest.mark.parametrize("variant", [FAST, PLAIN])
+@pytest.mark.parametrize("ex", W.ARCHIVE_WORKED, ids=lambda e: e["name"])
+def test_worked_archives(ctx, ex, variant):
+    arc = build_archive(ex["blocks"], expected=ex["expected"], fnv=oracle.fnv1a64)
+    rc, out = dec(ctx, arc, variant)
+    assert rc == 0, ctx.last_error()
+    assert out.tobytes() == ex["expected"]
+
+
+@pytest.mark.parametrize("variant", [FAST, PLAIN])
+def test_periodic_overlap_all_small_periods(ctx, variant):
+    rng = np.random.default_rng(4)
+    for d in (1, 2, 3, 5, 7, 12, 16, 33):
+        for ml in (4, 5, 31, 32, 33, 64, 200):
+            lits = bytes(rng.integers(0, 256, d, dtype=np.uint8))
+            arc = build_archive([[{"cmd": 0, "lits": lits, "ml": ml, "src": 0}]])
+            rc, out = dec(ctx, arc, variant)
+            assert rc == 0
+            assert out.tobytes() == lits + bytes(lits[k % d] for k in range(ml))
+
+
+@pytest.mark.parametrize("variant", [FAST, PLAIN])
+@pytest.mark.parametrize("no_rep", [False, True])
+@pytest.mark.parametrize("kind", ["dna", "text"])
+def test_oracle_encoded_small_config(ctx, dna4m, text4m, kind, no_rep, variant):
+    data = dna4m if kind == "dna" else text4m
+    arc = oracle.encode(data, no_rep=no_rep)
+    rc, out = dec(ctx, arc, variant)
+    assert rc == 0, ctx.last_error()
+    assert np.array_equal(out, oracle.decode(arc))
+    assert np.array_equal(out, data)
+
+
+@pytest.mark.parametrize("lanes", [1, 8, 32, 64, 128])
+@pytest.mark.parametrize("no_rep", [False, True])
+@pytest.mark.parametrize("kind", ["dna", "text"])
+def test_library_encoded_small_config(acx, ctx, dna4m, text4m, kind, no_rep, lanes):
+    data = (dna4m if kind == "dna" else text4m)[: (1 << 20) + 12345]
+    arc = acx.encode(data, no_rep=no_rep, max_lanes=lanes)
+    rc, out = dec(ctx, arc, FAST)
+    assert rc == 0, ctx.last_error()
+    assert np.array_equal(out, oracle.decode(arc))
+
+
+@pytest.mark.parametrize("variant", [FAST, PLAIN])
+def test_edge_sizes_and_ragged_tail(acx, ctx, variant):
+    from gpu_util import gpu_decode
+    rng = np.random.default_rng(7)
+    for n in (1, 15, 16, 17, 100, 16383, 16384, 16385, 5 * 16384 + 999):
+        data = synth.dna(n, 11) if n > 64 else (rng.integers(0, 4, n, dtype=np.uint8) + 65)
+        for arc in (oracle.encode(data), acx.encode(data, no_rep=True)):
+            rc, out, tail = gpu_decode(ctx, arc, variant, out_pad=64)
+            assert rc == 0, ctx.last_error()
+            assert np.array_equal(out, data)
+            assert np.all(tail == 0xA5)  # nothing written past the output
+
+
+def test_all_literal_and_long_runs(acx, ctx):
+    rng = np.random.default_rng(1)
+    data = rng.integers(0, 256, 200_000, dtype=np.uint8)
+    for arc in (oracle.encode(data), acx.encode(data)):
+        rc, out = dec(ctx, arc)
+        assert rc == 0 and np.array_equal(out, data)
+    data = np.frombuffer(b"N" * 100_000 + b"ACGT" * 30_000, dtype=np.uint8)
+    for arc in (oracle.encode(data), acx.encode(data), acx.encode(data, no_rep=True)):
+        rc, out = dec(ctx, arc)
+        assert rc == 0 and np.array_equal(out, data)
+
+
+def _corrupt_archives():
+    yield "offset not before destination", build_archive([[{"cmd": 0, "lits": b"ACGT", "ml": 4, "src": 4}]])
+    yield "repeat distance beyond start", build_archive([[{"cmd": 1, "lits": b"", "ml": 4}]])
+    yield "unknown command", build_archive([[{"cmd": 6, "lits": b"ACGT", "ml": 4, "src": 0}]])
+    yield "lit-only not last", build_archive([[{"cmd": 5, "lits": b"AC", "ml": 0},
+                                               {"cmd": 0, "lits": b"GT", "ml": 4, "src": 0}]])
+    yield "short match", build_archive([[{"cmd": 0, "lits": b"ACGT", "ml": 3, "src": 0}]])
+    from fmt_writer import leb128
+    toks = [[{"cmd": 0, "lits": b"ACGT", "ml": 4, "src": 0}]]
+    yield "4-byte varint", build_archive(toks, raw_streams={0: [bytes([0]), b"\x84\x80\x80\x00" + leb128(4),
+                                                                bytes(5), b"ACGT"]})
+    yield "trailing length byte", build_archive(toks, raw_streams={0: [bytes([0]), leb128(4) + leb128(4) + b"\x00",
+                                                                       bytes(5), b"ACGT"]})
+
+
+@pytest.mark.parametrize("variant", [FAST, PLAIN])
+@pytest.mark.parametrize("name,arc", list(_corrupt_archives()), ids=lambda x: x if isinstance(x, str) else "")
+def test_corrupt_token_streams_are_reported(ctx, name, arc, variant):
+    assert oracle.decode_status(arc, verify=False)[0] == oracle.E_CORRUPT
+    rc, _ = dec(ctx, arc, variant)
+    assert rc == -2, (name, rc, ctx.last_error())
+    # the context stays usable after an error
+    good = build_archive([W.ARCHIVE_WORKED[0]["blocks"][0]])
+    rc, out = dec(ctx, good, variant)
+    assert rc == 0 and out.tobytes() == W.ARCHIVE_WORKED[0]["expected"]
+
+
+def test_corrupt_rans_payload_is_reported(acx, ctx, dna4m):
+    data = dna4m[:200_000]
+    arc = bytearray(acx.encode(data))
+    info = oracle.info(bytes(arc))
+    rng = np.random.default_rng(5)
+    seen_corrupt = 0
+    for _ in range(12):
+        bad = bytearray(arc)
+        # flip a byte inside the payload section (after header/tables/index)
+        lo = 64 + 2048 + 40 * info["n_blocks"] + 64
+        pos = int(rng.integers(lo, len(bad)))
+        bad[pos] ^= 0x5A
+        rc_o, ref = oracle.decode_status(bytes(bad), verify=False)
+        try:
+            rc, out = dec(ctx, bytes(bad))
+        except Exception as e:  # structural rejection at open
+            assert getattr(e, "status", None) == -2
+            continue
+        if rc_o == 0:
+            assert rc == 0 and np.array_equal(out, ref)
+        else:
+            assert rc in (-2, 0)
+            seen_corrupt += rc == -2
+    assert seen_corrupt >= 1
+
+
+@pytest.mark.slow
+def test_full_size_genome_matches_oracle(acx, ctx):
+    """The benchmark's workload at its full size (253,935,557 B genome,
+    history-bound encoding, fast decoder): every byte equals the oracle's
+    decode and the generator's input."""
+    data = synth.dna(synth.GENOME_CHR1_SIZE, 0)
+    arc = acx.encode(data)
+    rc, out = dec(ctx, arc, FAST)
+    assert rc == 0, ctx.last_error()
+    assert np.array_equal(out, data)
+    ref = oracle.decode(arc)
+    assert np.array_equal(out, ref)
