@@ -114,9 +114,9 @@ int aceapex_ctx_create(int device, const aceapex_dec_params* params, aceapex_ctx
     if (!c->params.timeout_us) c->params.timeout_us = 2000000;
     if (cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&c->counters, kMaxCounters * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_err, 4 * sizeof(int)) != cudaSuccess ||
         cudaMemset(c->counters, 0, kMaxCounters * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaMemset(c->d_err, 0, 4 * sizeof(int)) != cudaSuccess) {
         aceapex_ctx_destroy(c);
         return ACEAPEX_E_CUDA;
     }
@@ -288,12 +288,18 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
 static int read_status(aceapex_ctx* c, cudaStream_t st) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
-    int h = 0;
-    if ((e = cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    int h[4] = {0, 0, 0, 0};
+    if ((e = cudaMemcpy(h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(c, e, "error word");
-    if (h) {
-        cudaMemset(c->d_err, 0, sizeof(int));
-        return fail(c, h, std::string("device reported: ") + aceapex_status_string(h));
+    if (h[0]) {
+        cudaMemset(c->d_err, 0, sizeof(h));
+        static const char* stages[] = {"?", "rANS stream", "varint lengths", "token sums/commands",
+                                       "offsets/history", "dependency wait", "plain parse", "block limits"};
+        const int st = (h[1] >> 24) & 7;
+        std::string m = std::string("device reported: ") + aceapex_status_string(h[0]) + " (" + stages[st];
+        if (st == 1) m += " " + std::to_string(h[1] & 0xff);
+        m += ", block " + std::to_string((unsigned)h[2]) + ")";
+        return fail(c, h[0], m);
     }
     return ACEAPEX_OK;
 }

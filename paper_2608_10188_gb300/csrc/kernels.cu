@@ -47,7 +47,15 @@ namespace acx {
 constexpr int kErrCorrupt = -2;
 constexpr int kErrTimeout = -5;
 
-__device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
+// err[0]: first status; err[1]: where it was raised (stage << 24 | detail);
+// err[2]: block index.  Stages: 1 rANS (detail = stream), 2 varints, 3 tokens,
+// 4 offsets/history, 5 dependency wait, 6 plain decoder.
+__device__ __forceinline__ void set_err(int* err, int code, int where = 0, uint32_t block = 0) {
+    if (atomicCAS(err, 0, code) == 0) {
+        err[1] = where;
+        err[2] = (int)block;
+    }
+}
 
 __device__ __forceinline__ uint64_t gtimer() {
     uint64_t t;
@@ -143,6 +151,9 @@ __device__ bool rans_stream(const uint32_t* __restrict__ tab, const uint8_t* __r
     }
     ok = __all_sync(ACX_FULL, ok);
     const uint32_t seq0 = seq;
+    // local chunk c lands in ring slot (seq0 + c) % kSlots, so word w of this
+    // stream sits at ring[(rbase + w) % kRingWords]
+    const uint32_t rbase = (seq0 % kSlots) * kChunkWords;
     uint32_t issued = 0, ready = 0;
     while (issued < nchunks && issued < (uint32_t)kSlots) {
         uint32_t q = seq0 + issued, slot = q % kSlots;
@@ -200,7 +211,7 @@ __device__ bool rans_stream(const uint32_t* __restrict__ tab, const uint8_t* __r
 #pragma unroll
         for (int s = 0; s < S; s++) {
             const uint32_t b = __ballot_sync(ACX_FULL, need[s]);
-            if (need[s]) x[s] = (x[s] << 16) | ring[(base + __popc(b & lt_mask)) & (kRingWords - 1)];
+            if (need[s]) x[s] = (x[s] << 16) | ring[(rbase + base + __popc(b & lt_mask)) & (kRingWords - 1)];
             base += __popc(b);
         }
         if (base > W) { ok = false; break; }
@@ -297,7 +308,9 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
             const uint8_t* pay = J.arc + bd.payload;
             uint8_t* scr = J.scratch + bd.scratch;
             bool ok = true;
+            int fs = 0;
             for (int s = 0; s < 4 && ok; s++) {
+                fs = s;
                 const uint32_t n = bd.s_raw[s];
                 if (n == 0) continue;
                 if (bd.rans_mask & (1u << s)) {
@@ -318,7 +331,7 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
                     copy_stored(pay + bd.s_body[s], scr + bd.s_off[s], n, lane);
                 }
             }
-            if (!ok && lane == 0) set_err(job.err, kErrCorrupt);
+            if (!ok && lane == 0) set_err(job.err, kErrCorrupt, (1 << 24) | fs, b);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -593,6 +606,10 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(JobDev job) {
         const uint8_t* g_lit = scr + bd.s_off[kLit];
         const uint32_t n = C.n, LB = bd.s_raw[kLen], n_lit = bd.s_raw[kLit], n_new = bd.n_new;
         bool bad = (n > job.max_tok) || (LB > job.max_lenb);
+        int stage = bad ? 7 : 0;
+        auto mark = [&](bool cond, int st) {
+            if (cond && !bad) { bad = true; stage = st; }
+        };
 
         // ---- stage cmd + len bytes, clear the pending bitmap ----
         if (!bad) {
@@ -621,7 +638,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(JobDev job) {
             v3[0] = c; v3[1] = 0; v3[2] = 0;
             block_scan3(v3, tot3, scanbuf);
         }
-        if (tot3[0] != 2 * n || (LB > 0 && lenb[LB - 1] >= 0x80) || (LB == 0 && n > 0)) bad = true;
+        mark(tot3[0] != 2 * n || (LB > 0 && lenb[LB - 1] >= 0x80) || (LB == 0 && n > 0), 2);
         if (!bad) {
             uint32_t idx = v3[0];
             for (uint32_t j = j0; j < j1; j++) {
@@ -639,7 +656,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(JobDev job) {
             }
         }
         __syncthreads();
-        bad = bad || misc[1];
+        mark(misc[1] != 0, 2);
 
         // ---- token scans: positions, literal positions, NEW indices ----
         const uint32_t tper = (n + kAsmThreads - 1) / kAsmThreads;
@@ -663,7 +680,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(JobDev job) {
             v3[0] = s_len; v3[1] = s_ll; v3[2] = s_new;
             block_scan3(v3, tot3, scanbuf);
         }
-        if (!bad && (tot3[0] != C.R || tot3[1] != n_lit || tot3[2] != n_new || misc[1])) bad = true;
+        mark(tot3[0] != C.R || tot3[1] != n_lit || tot3[2] != n_new || misc[1], 3);
         if (!bad) {
             uint32_t pos = v3[0], lp = v3[1], ni = v3[2];
             for (uint32_t i = i0; i < i1; i++) {
@@ -683,7 +700,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(JobDev job) {
             }
         }
         any_rep = __syncthreads_or(any_rep && !bad);
-        bad = bad || misc[1];
+        mark(misc[1] != 0, 4);
 
         // ---- 4-entry history as a monoid scan (only if the block has repeat codes) ----
         if (any_rep && !bad) {
@@ -723,7 +740,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(JobDev job) {
                 }
             }
             __syncthreads();
-            bad = bad || misc[1];
+            mark(misc[1] != 0, 4);
         }
 
         if (!bad) {
@@ -824,14 +841,14 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(JobDev job) {
                         if (tid == 0 && gtimer() > deadline) misc[1] = 2;
                         __nanosleep(200);
                         __syncthreads();
-                        if (misc[1] == 2) { bad = true; break; }
+                        if (misc[1] == 2) { mark(true, 5); break; }
                     }
                 }
             }
         }
         __syncthreads();
         if (bad) {
-            if (tid == 0) set_err(job.err, misc[1] == 2 ? kErrTimeout : kErrCorrupt);
+            if (tid == 0) set_err(job.err, stage == 5 ? kErrTimeout : kErrCorrupt, stage << 24, b);
         } else if (!published) {
             uint4* gdst = reinterpret_cast<uint4*>(C.gout);
             const uint4* ssrc = reinterpret_cast<const uint4*>(sout);
@@ -985,7 +1002,7 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain(JobDev job, uint32_t ma
                         __nanosleep(100);
                         if ((++spins & 63) == 0 && gtimer() > deadline) { bad2 = true; break; }
                     }
-                    if (bad2) { set_err(job.err, kErrTimeout); break; }
+                    if (bad2) { set_err(job.err, kErrTimeout, 5 << 24, b); break; }
                     const uint32_t o = ddst[q];
                     for (uint32_t j = 0; j < dml[q]; j++) {
                         const uint8_t by = src_byte(J, C, sout, dsrc[q] + j);
@@ -997,7 +1014,7 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain(JobDev job, uint32_t ma
                     pend_set_smem(pend, o, o + dml[q], false);
                 }
             } else if (bad) {
-                set_err(job.err, kErrCorrupt);
+                set_err(job.err, kErrCorrupt, 6 << 24, b);
             }
             __threadfence();
             st_release_u32(J.state + b, (C.epoch << 2) | kStComplete);
