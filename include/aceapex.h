@@ -83,8 +83,8 @@ typedef struct {
 typedef struct {
     double ms_total;  /* whole call, device time */
     double ms_ans;    /* entropy stage (rANS decode of the four streams) */
-    double ms_parse;  /* parse + copy (assembly kernel) */
-    double ms_copy;   /* reserved: the fused assembly kernel reports parse and copy together */
+    double ms_parse;  /* local pass: parse, literals and in-block matches */
+    double ms_copy;   /* cross-block pass: matches whose source chain leaves their block */
     uint64_t blocks;  /* blocks decoded */
     uint64_t bytes;   /* bytes written to the output */
 } aceapex_stats;

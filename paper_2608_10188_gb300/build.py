@@ -27,11 +27,11 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("kernels.cu", "api.cpp", "plan.cpp", "encode.cpp")]
+    return [os.path.join(CSRC, f) for f in ("rans.cu", "assemble.cu", "plain.cu", "api.cpp", "plan.cpp", "encode.cpp")]
 
 
 def _deps():
-    return sources() + [os.path.join(CSRC, f) for f in ("internal.h", "plan.h")] + [
+    return sources() + [os.path.join(CSRC, f) for f in ("internal.h", "plan.h", "common.cuh")] + [
         os.path.join(os.path.dirname(HERE), "include", "aceapex.h")]
 
 

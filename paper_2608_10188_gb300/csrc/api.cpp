@@ -15,12 +15,14 @@
 namespace acx {
 cudaError_t launch_prologue(uint32_t* counters, uint32_t n_counters, cudaStream_t st);
 cudaError_t launch_rans(const JobDev& job, int grid, cudaStream_t st);
-cudaError_t launch_assemble(const JobDev& job, int grid, cudaStream_t st);
+cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st);
+cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st);
 cudaError_t launch_plain(const JobDev& job, int grid, cudaStream_t st);
-size_t rans_smem_bytes();
-size_t asm_smem_bytes(uint32_t T, uint32_t LB);
-size_t plain_smem_bytes(uint32_t T);
-int occupancy(int which, size_t smem);
+size_t local_smem_bytes(uint32_t T, uint32_t LB);
+int rans_occupancy();
+int local_occupancy(size_t smem);
+int external_occupancy();
+int plain_occupancy();
 }  // namespace acx
 
 using namespace acx;
@@ -61,11 +63,11 @@ struct aceapex_ctx {
     aceapex_dec_params params{};
     std::string err;
     int n_sms = 0;
-    DevBuf streams, state, pmap, arcs, in_arc, out_buf;
+    DevBuf streams, npend, pmap, spans, arcs, in_arc, out_buf;
     uint32_t* counters = nullptr;  // device
     int* d_err = nullptr;          // device
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    uint32_t state_blocks = 0;     // blocks covered by the zero-initialised state region
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int occ_rans = 0, occ_ext = 0, occ_plain = 0;
 };
 
 struct aceapex_archive {
@@ -126,6 +128,9 @@ int aceapex_ctx_create(int device, const aceapex_dec_params* params, aceapex_ctx
             return ACEAPEX_E_CUDA;
         }
     }
+    c->occ_rans = std::max(1, rans_occupancy());
+    c->occ_ext = std::max(1, external_occupancy());
+    c->occ_plain = std::max(1, plain_occupancy());
     *out = c;
     return ACEAPEX_OK;
 }
@@ -134,8 +139,9 @@ int aceapex_ctx_destroy(aceapex_ctx* c) {
     if (!c) return ACEAPEX_E_ARG;
     cudaSetDevice(c->device);
     c->streams.release();
-    c->state.release();
+    c->npend.release();
     c->pmap.release();
+    c->spans.release();
     c->arcs.release();
     c->in_arc.release();
     c->out_buf.release();
@@ -228,20 +234,19 @@ int aceapex_archive_get_info(const aceapex_archive* A, aceapex_archive_info* inf
 
 }  // extern "C"
 
-// Enqueue the whole decode of one archive.  ev (optional) receives three
-// event records: start, after the entropy stage, after assembly.
+// Enqueue the whole decode of one archive: ticket reset, entropy stage,
+// local parse + match pass, cross-block pass.  With `timed`, events bracket
+// the three stages.
 static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc, void* d_out, cudaStream_t st,
                           bool timed) {
     const Plan& P = A->plan;
     cudaError_t e;
-    if ((e = c->streams.ensure(P.scratch_bytes)) != cudaSuccess) return cuda_fail(c, e, "scratch allocation");
     const size_t nb = std::max<size_t>(P.n_blocks, 1);
-    if (c->state_blocks < nb) {
-        if ((e = c->state.ensure(nb * 4)) != cudaSuccess) return cuda_fail(c, e, "state allocation");
-        if ((e = cudaMemsetAsync(c->state.p, 0, nb * 4, st)) != cudaSuccess) return cuda_fail(c, e, "state init");
-        c->state_blocks = (uint32_t)nb;
-    }
+    if ((e = c->streams.ensure(P.scratch_bytes)) != cudaSuccess) return cuda_fail(c, e, "scratch allocation");
+    if ((e = c->npend.ensure(nb * 4)) != cudaSuccess) return cuda_fail(c, e, "pending-count allocation");
     if ((e = c->pmap.ensure(nb * (kBlock / 8))) != cudaSuccess) return cuda_fail(c, e, "bitmap allocation");
+    if ((e = c->spans.ensure(std::max<uint64_t>(P.tokens, 1) * sizeof(SpanRec))) != cudaSuccess)
+        return cuda_fail(c, e, "span allocation");
     JobDev job{};
     ArcJob& J = job.one;
     J.arc = (const uint8_t*)d_arc;
@@ -249,8 +254,9 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     J.dtab = A->d_dtab;
     J.scratch = (uint8_t*)c->streams.p;
     J.out = (uint8_t*)d_out;
-    J.state = (uint32_t*)c->state.p;
+    J.npend = (uint32_t*)c->npend.p;
     J.pmap = (uint32_t*)c->pmap.p;
+    J.spans = (SpanRec*)c->spans.p;
     J.total = P.total;
     J.n_blocks = P.n_blocks;
     J.lo = 0;
@@ -266,22 +272,23 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     job.max_tok = P.max_tok;
     job.max_lenb = P.max_lenb;
     if (P.n_blocks == 0) return ACEAPEX_OK;
+    const size_t lsm = local_smem_bytes(P.max_tok, P.max_lenb);
+    if (c->params.variant != ACEAPEX_VARIANT_PLAIN && lsm > 227 * 1024)
+        return fail(c, ACEAPEX_E_CORRUPT, "block too large for the local pass");
     if (timed && (e = cudaEventRecord(c->ev[0], st)) != cudaSuccess) return cuda_fail(c, e, "event");
-    if ((e = launch_prologue(c->counters, 2 + 1, st)) != cudaSuccess) return cuda_fail(c, e, "prologue launch");
-    const int occ_r = std::max(1, occupancy(0, rans_smem_bytes()));
-    if ((e = launch_rans(job, occ_r * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "rANS launch");
+    if ((e = launch_prologue(c->counters, 3 + 1, st)) != cudaSuccess) return cuda_fail(c, e, "prologue launch");
+    if ((e = launch_rans(job, c->occ_rans * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "rANS launch");
     if (timed && (e = cudaEventRecord(c->ev[1], st)) != cudaSuccess) return cuda_fail(c, e, "event");
     if (c->params.variant == ACEAPEX_VARIANT_PLAIN) {
-        const int occ = std::max(1, occupancy(2, plain_smem_bytes(P.max_tok)));
-        if ((e = launch_plain(job, occ * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "plain launch");
+        if ((e = launch_plain(job, c->occ_plain * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "plain launch");
     } else {
-        const size_t sm = asm_smem_bytes(P.max_tok, P.max_lenb);
-        if (sm > 227 * 1024) return fail(c, ACEAPEX_E_CORRUPT, "block too large for the assembly kernel");
-        int occ = std::max(1, occupancy(1, sm));
+        int occ = std::max(1, local_occupancy(lsm));
         if (c->params.ctas_per_sm) occ = std::min<int>(occ, (int)c->params.ctas_per_sm);
-        if ((e = launch_assemble(job, occ * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "assembly launch");
+        if ((e = launch_local(job, occ * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "local launch");
     }
     if (timed && (e = cudaEventRecord(c->ev[2], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    if ((e = launch_external(job, c->occ_ext * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "external launch");
+    if (timed && (e = cudaEventRecord(c->ev[3], st)) != cudaSuccess) return cuda_fail(c, e, "event");
     return ACEAPEX_OK;
 }
 
@@ -305,13 +312,15 @@ static int read_status(aceapex_ctx* c, cudaStream_t st) {
 }
 
 static void fill_stats(aceapex_ctx* c, const Plan& P, aceapex_stats* s) {
-    float a = 0, b = 0;
+    float a = 0, b = 0, x = 0, t = 0;
     cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&x, c->ev[2], c->ev[3]);
+    cudaEventElapsedTime(&t, c->ev[0], c->ev[3]);
     s->ms_ans = a;
     s->ms_parse = b;
-    s->ms_copy = 0;
-    s->ms_total = a + b;
+    s->ms_copy = x;
+    s->ms_total = t;
     s->blocks = P.n_blocks;
     s->bytes = P.total;
 }
@@ -366,11 +375,11 @@ int aceapex_decode_host(aceapex_ctx* c, aceapex_archive* A, const void* h_arc, u
     if (rc == ACEAPEX_OK &&
         (e = cudaMemcpyAsync(h_out, c->out_buf.p, A->plan.total, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         rc = cuda_fail(c, e, "output download");
-    if (rc == ACEAPEX_OK && stats && (e = cudaEventRecord(c->ev[2], st)) != cudaSuccess) rc = cuda_fail(c, e, "event");
+    if (rc == ACEAPEX_OK && stats && (e = cudaEventRecord(c->ev[3], st)) != cudaSuccess) rc = cuda_fail(c, e, "event");
     if (rc == ACEAPEX_OK) rc = read_status(c, st);
     if (rc == ACEAPEX_OK && stats) {
         float ms = 0;
-        cudaEventElapsedTime(&ms, c->ev[0], c->ev[2]);
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]);
         memset(stats, 0, sizeof *stats);
         stats->ms_total = ms;
         stats->blocks = A->plan.n_blocks;

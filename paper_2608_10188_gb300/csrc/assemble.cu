@@ -1,0 +1,621 @@
+// Parse and match layer of the decode (paper: "parse" and "copy"), in two
+// passes separated by a kernel boundary.
+//
+// k_local (one CTA of 128 threads per block, persistent, any order):
+//   * varint boundaries by compaction: every byte < 0x80 ends a value; a CTA
+//     prefix count gives each value its index (LL_i, ML_i).  The paper finds
+//     varints make 0.61% of commands sequential in a serial parse ("The Last
+//     Sequential Element"); here they are a scan like everything else.
+//   * prefix sums of LL+ML, LL and #NEW give every token's output position,
+//     literal position and offset index (the paper's 93.94% scan share).
+//   * the 4-entry distance history as a monoid scan: each token is a map on
+//     the history (NEW pushes a distance, REPk moves entry k to the front);
+//     maps compose associatively, so the history before every token is a
+//     prefix "sum" too.  Skipped when a block has no repeat code (history-
+//     free encoding, where the parse is a dependency-free prefix scan).
+//   * literals are placed with 4-byte funnel-shifted copies, one warp per run.
+//   * matches whose source lies inside the block are periodic fills
+//     out[dst+k] = out[src + (k mod d)] ("What Does: Periods, Not Chains"),
+//     done in rounds as their sources become final; matches whose source
+//     chain leaves the block become pending spans.
+//   * the block is written with coalesced 16-byte stores; its pending-byte
+//     bitmap and pending spans go beside it.
+// k_external (warps take blocks in ascending order, one lane per span):
+//   after the kernel boundary every literal and every in-block match byte is
+//   final, so a pending span waits only on the spans its source really
+//   depends on, which lie at lower positions and were taken earlier: the
+//   ascending order makes the bounded waits deadlock-free.
+#include "common.cuh"
+
+namespace acx {
+
+constexpr int kLocThreads = 128;
+constexpr int kLocWarps = kLocThreads / 32;
+constexpr uint64_t kRefTag = 1ull << 63;  // history map entry "copy input entry k"
+
+struct LocLayout {
+    uint32_t out, pend, tsrc, tpos, tll, tml, tlit, tcmd, tstat, lenb, scan, misc, total;
+};
+
+__host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB) {
+    LocLayout L;
+    uint32_t o = 0;
+    auto take = [&](uint32_t bytes, uint32_t align) {
+        o = (o + align - 1) & ~(align - 1);
+        const uint32_t r = o;
+        o += bytes;
+        return r;
+    };
+    const uint32_t T16 = (T + 15) & ~15u;
+    L.out = take(kBlock, 16);
+    L.pend = take(kBlock / 8, 16);
+    L.tsrc = take(8 * T, 16);
+    L.tpos = take(2 * T, 16);
+    L.tll = take(2 * T, 16);
+    L.tml = take(2 * T, 16);
+    L.tlit = take(2 * T, 16);
+    L.tcmd = take(T16 + 16, 16);
+    L.tstat = take(T16, 16);
+    L.lenb = take(((LB + 15) & ~15u) + 16, 16);
+    L.scan = take(kLocWarps * 4 * 4 + 64, 16);
+    L.misc = take(64, 16);
+    L.total = (o + 127) & ~127u;
+    return L;
+}
+
+// Block-wide exclusive scan of three u32 values per thread.
+__device__ __forceinline__ void block_scan3(uint32_t v[3], uint32_t tot[3], uint32_t* buf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc[3] = {v[0], v[1], v[2]};
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const uint32_t y = __shfl_up_sync(ACX_FULL, inc[k], o);
+            if (lane >= o) inc[k] += y;
+        }
+    }
+    if (lane == 31)
+        for (int k = 0; k < 3; k++) buf[warp * 3 + k] = inc[k];
+    __syncthreads();
+    uint32_t wpre[3] = {0, 0, 0}, t[3] = {0, 0, 0};
+#pragma unroll
+    for (int w = 0; w < kLocWarps; w++) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const uint32_t s = buf[w * 3 + k];
+            if (w < warp) wpre[k] += s;
+            t[k] += s;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        v[k] = wpre[k] + inc[k] - v[k];
+        tot[k] = t[k];
+    }
+    __syncthreads();
+}
+
+struct HMap {
+    uint64_t e[4];
+};
+__device__ __forceinline__ HMap hmap_identity() {
+    HMap m;
+#pragma unroll
+    for (int k = 0; k < 4; k++) m.e[k] = kRefTag | k;
+    return m;
+}
+// (first f, then g)
+__device__ __forceinline__ HMap hmap_compose(const HMap& f, const HMap& g) {
+    HMap r;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint64_t x = g.e[k];
+        r.e[k] = (x & kRefTag) ? f.e[x & 3] : x;
+    }
+    return r;
+}
+__device__ __forceinline__ HMap hmap_token(uint8_t cmd, uint64_t d_new) {
+    HMap m = hmap_identity();
+    if (cmd == kNew) {
+        m.e[0] = d_new;
+        m.e[1] = kRefTag | 0;
+        m.e[2] = kRefTag | 1;
+        m.e[3] = kRefTag | 2;
+    } else if (cmd >= 1 && cmd <= 4) {
+        const int j = cmd - 1;  // move entry j to the front
+        m.e[0] = kRefTag | j;
+#pragma unroll
+        for (int k = 1; k <= 3; k++) m.e[k] = kRefTag | (k <= j ? k - 1 : k);
+    }
+    return m;
+}
+
+__device__ __forceinline__ bool pend_clear_smem(const uint32_t* pend, uint32_t s, uint32_t e) {
+    if (s >= e) return true;
+    for (uint32_t w = s >> 5; w <= ((e - 1) >> 5); w++)
+        if (((volatile const uint32_t*)pend)[w] & range_mask(w, s, e)) return false;
+    return true;
+}
+__device__ __forceinline__ void pend_update_smem(uint32_t* pend, uint32_t s, uint32_t e, bool set) {
+    if (s >= e) return;
+    for (uint32_t w = s >> 5; w <= ((e - 1) >> 5); w++) {
+        const uint32_t m = range_mask(w, s, e);
+        if (set) atomicOr(&pend[w], m); else atomicAnd(&pend[w], ~m);
+    }
+}
+
+// Literal run: out[b, b+L) = lit[a, a+L), one warp, 4-byte funnel-shifted words.
+__device__ __forceinline__ void copy_run(uint8_t* __restrict__ sout, const uint8_t* __restrict__ lit, uint32_t a,
+                                         uint32_t b, uint32_t L, int lane) {
+    if (!L) return;
+    const uint32_t e = b + L;
+    const uint32_t w0 = (b + 3) >> 2, w1 = e >> 2;  // whole words [w0, w1)
+    if (w0 >= w1) {
+        for (uint32_t x = b + lane; x < e; x += 32) sout[x] = __ldg(lit + a + (x - b));
+        return;
+    }
+    if (lane < (int)(4 * w0 - b)) sout[b + lane] = __ldg(lit + a + lane);
+    if (lane < (int)(e - 4 * w1)) sout[4 * w1 + lane] = __ldg(lit + a + (4 * w1 + lane - b));
+    const uint32_t* lw = reinterpret_cast<const uint32_t*>(lit);
+    for (uint32_t w = w0 + lane; w < w1; w += 32) {
+        const uint32_t src = a + (4 * w - b);
+        const uint32_t lo = __ldg(lw + (src >> 2)), hi = __ldg(lw + (src >> 2) + 1);
+        reinterpret_cast<uint32_t*>(sout)[w] = __funnelshift_r(lo, hi, 8 * (src & 3));
+    }
+}
+
+__global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    const LocLayout L = loc_layout(job.max_tok, job.max_lenb);
+    uint8_t* sout = sm + L.out;
+    uint32_t* pend = reinterpret_cast<uint32_t*>(sm + L.pend);
+    uint64_t* tsrc = reinterpret_cast<uint64_t*>(sm + L.tsrc);
+    uint16_t* tpos = reinterpret_cast<uint16_t*>(sm + L.tpos);
+    uint16_t* tll = reinterpret_cast<uint16_t*>(sm + L.tll);
+    uint16_t* tml = reinterpret_cast<uint16_t*>(sm + L.tml);
+    uint16_t* tlit = reinterpret_cast<uint16_t*>(sm + L.tlit);
+    uint8_t* tcmd = sm + L.tcmd;
+    uint8_t* tstat = sm + L.tstat;
+    uint8_t* lenb = sm + L.lenb;
+    uint32_t* scanbuf = reinterpret_cast<uint32_t*>(sm + L.scan);
+    volatile uint32_t* misc = reinterpret_cast<volatile uint32_t*>(sm + L.misc);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (;;) {
+        if (tid == 0) misc[0] = atomicAdd(&job.counters[1], 1u);
+        __syncthreads();
+        const uint32_t item = misc[0];
+        if (item >= job.n_items) return;
+        const int a = find_arc(job, item);
+        const ArcJob J = load_arc(job, a);
+        const uint32_t b = J.lo + (item - J.item_base);
+        const BlockDev& bd = J.blk[b];
+        const uint64_t B = (uint64_t)b * kBlock;
+        const uint32_t R = bd.raw_len, n = bd.n_tok, LB = bd.s_raw[kLen], n_lit = bd.s_raw[kLit];
+        const uint32_t n_new = bd.n_new;
+        const uint8_t* scr = J.scratch + bd.scratch;
+        const uint8_t* g_off = scr + bd.s_off[kOff];
+        const uint8_t* g_lit = scr + bd.s_off[kLit];
+        bool bad = n > job.max_tok || LB > job.max_lenb;
+        int stage = bad ? kStageLimits : 0;
+        auto mark = [&](bool cond, int st) {
+            if (cond && !bad) { bad = true; stage = st; }
+        };
+
+        // ---- stage cmd and len bytes (16-byte vectors; streams are 16-aligned and padded) ----
+        if (!bad) {
+            const uint4* c4 = reinterpret_cast<const uint4*>(scr + bd.s_off[kCmd]);
+            const uint4* l4 = reinterpret_cast<const uint4*>(scr + bd.s_off[kLen]);
+            for (uint32_t i = tid; i < (n + 15) / 16; i += kLocThreads) reinterpret_cast<uint4*>(tcmd)[i] = c4[i];
+            for (uint32_t i = tid; i < (LB + 15) / 16; i += kLocThreads) reinterpret_cast<uint4*>(lenb)[i] = l4[i];
+        }
+        for (uint32_t i = tid; i < kBlock / 32; i += kLocThreads) pend[i] = 0;
+        if (tid == 0) misc[1] = 0;
+        __syncthreads();
+
+        // ---- varints: each byte < 0x80 ends a value ----
+        uint32_t v3[3], tot3[3];
+        const uint32_t per = (LB + kLocThreads - 1) / kLocThreads;
+        const uint32_t j0 = min(LB, tid * per), j1 = min(LB, j0 + per);
+        {
+            uint32_t c = 0;
+            bool vbad = false;
+            if (!bad)
+                for (uint32_t j = j0; j < j1; j++) {
+                    const uint8_t by = lenb[j];
+                    if (by < 0x80) c++;
+                    // a value has at most three bytes
+                    if (by >= 0x80 && j >= 2 && lenb[j - 1] >= 0x80 && lenb[j - 2] >= 0x80) vbad = true;
+                }
+            if (vbad) misc[1] = 1;
+            v3[0] = c; v3[1] = 0; v3[2] = 0;
+            block_scan3(v3, tot3, scanbuf);
+        }
+        mark(tot3[0] != 2 * n || (LB > 0 && lenb[LB - 1] >= 0x80) || (LB == 0 && n > 0) || misc[1], kStageVarint);
+        if (!bad) {
+            uint32_t idx = v3[0];
+            for (uint32_t j = j0; j < j1; j++) {
+                const uint8_t by = lenb[j];
+                if (by >= 0x80) continue;
+                uint32_t val = by;
+                if (j >= 1 && lenb[j - 1] >= 0x80) {
+                    val = (val << 7) | (lenb[j - 1] & 0x7f);
+                    if (j >= 2 && lenb[j - 2] >= 0x80) val = (val << 7) | (lenb[j - 2] & 0x7f);
+                }
+                if (val > kBlock) misc[1] = 1;
+                const uint32_t tk = idx >> 1;
+                if (idx & 1) tml[tk] = (uint16_t)min(val, kBlock); else tll[tk] = (uint16_t)min(val, kBlock);
+                idx++;
+            }
+        }
+        __syncthreads();
+        mark(misc[1] != 0, kStageVarint);
+
+        // ---- token scans: positions, literal positions, NEW indices ----
+        const uint32_t tper = (n + kLocThreads - 1) / kLocThreads;
+        const uint32_t i0 = min(n, tid * tper), i1 = min(n, i0 + tper);
+        bool any_rep = false;
+        {
+            uint32_t s_len = 0, s_ll = 0, s_new = 0;
+            bool tbad = false;
+            if (!bad)
+                for (uint32_t i = i0; i < i1; i++) {
+                    const uint32_t ll = tll[i], ml = tml[i], c = tcmd[i];
+                    s_len += ll + ml;
+                    s_ll += ll;
+                    s_new += c == kNew;
+                    if (c > kLitOnly) tbad = true;
+                    if (c == kLitOnly) { if (ml != 0 || i != n - 1 || ll == 0) tbad = true; }
+                    else if (ml < J.min_match) tbad = true;
+                    any_rep |= c >= 1 && c <= 4;
+                }
+            if (tbad) misc[1] = 1;
+            v3[0] = s_len; v3[1] = s_ll; v3[2] = s_new;
+            block_scan3(v3, tot3, scanbuf);
+        }
+        mark(tot3[0] != R || tot3[1] != n_lit || tot3[2] != n_new || misc[1], kStageTokens);
+        if (!bad) {
+            uint32_t pos = v3[0], lp = v3[1], ni = v3[2];
+            for (uint32_t i = i0; i < i1; i++) {
+                const uint32_t ll = tll[i], ml = tml[i];
+                tpos[i] = (uint16_t)pos;
+                tlit[i] = (uint16_t)lp;
+                uint64_t src = 0;
+                if (tcmd[i] == kNew) {
+#pragma unroll
+                    for (int p = 0; p < 5; p++) src |= (uint64_t)__ldg(g_off + (uint64_t)p * n_new + ni) << (8 * p);
+                    ni++;
+                    if (src >= B + pos + ll) misc[1] = 1;  // every absolute offset precedes its destination
+                }
+                tsrc[i] = src;
+                pos += ll + ml;
+                lp += ll;
+            }
+        }
+        any_rep = __syncthreads_or(any_rep && !bad);
+        mark(misc[1] != 0, kStageSources);
+
+        // ---- the 4-entry history as a monoid scan (blocks with repeat codes only) ----
+        if (any_rep && !bad) {
+            HMap* hbuf = reinterpret_cast<HMap*>(sout);  // the block buffer is free until literal placement
+            HMap agg = hmap_identity();
+            for (uint32_t i = i0; i < i1; i++)
+                agg = hmap_compose(agg, hmap_token(tcmd[i], B + tpos[i] + tll[i] - tsrc[i]));
+            hbuf[tid] = agg;
+            __syncthreads();
+            for (int o = 1; o < kLocThreads; o <<= 1) {  // inclusive Hillis-Steele scan of the maps
+                const HMap mine = hbuf[tid];
+                const HMap prev = tid >= o ? hbuf[tid - o] : hmap_identity();
+                __syncthreads();
+                if (tid >= o) hbuf[tid] = hmap_compose(prev, mine);
+                __syncthreads();
+            }
+            const HMap pre = tid > 0 ? hbuf[tid - 1] : hmap_identity();
+            uint64_t h[4];
+            const uint64_t h0[4] = {1, 2, 3, 4};  // initial history, reset per block
+#pragma unroll
+            for (int k = 0; k < 4; k++) h[k] = (pre.e[k] & kRefTag) ? h0[pre.e[k] & 3] : pre.e[k];
+            for (uint32_t i = i0; i < i1; i++) {
+                const uint8_t c = tcmd[i];
+                const uint64_t dst = B + tpos[i] + tll[i];
+                if (c == kNew) {
+                    h[3] = h[2]; h[2] = h[1]; h[1] = h[0]; h[0] = dst - tsrc[i];
+                } else if (c >= 1 && c <= 4) {
+                    const int j = c - 1;
+                    const uint64_t d = h[j];
+                    if (d < 1 || d > dst) misc[1] = 1;
+                    tsrc[i] = dst - d;
+                    for (int k = j; k > 0; k--) h[k] = h[k - 1];
+                    h[0] = d;
+                }
+            }
+            __syncthreads();
+            mark(misc[1] != 0, kStageSources);
+        }
+
+        uint32_t npend = 0;
+        if (!bad) {
+            // ---- literal placement: one warp per run ----
+            for (uint32_t i = warp; i < n; i += kLocWarps) copy_run(sout, g_lit, tlit[i], tpos[i], tll[i], lane);
+            // ---- every match byte starts unresolved; external sources are pending for good ----
+            for (uint32_t i = tid; i < n; i += kLocThreads) {
+                const uint32_t ml = tml[i];
+                uint8_t st = 0;  // 0: none/done, 1: unresolved in-block, 2: pending
+                if (ml) {
+                    const uint32_t s = tpos[i] + tll[i];
+                    pend_update_smem(pend, s, s + ml, true);
+                    st = tsrc[i] >= B ? 1 : 2;
+                }
+                tstat[i] = st;
+            }
+            __syncthreads();
+            // ---- in-block matches: rounds of ready periodic fills ----
+            for (;;) {
+                bool progress = false, left = false;
+                for (uint32_t i = tid; i < n; i += kLocThreads) {
+                    if (tstat[i] != 1) continue;
+                    const uint32_t ml = tml[i];
+                    const uint32_t o = tpos[i] + tll[i];
+                    const uint32_t so = (uint32_t)(tsrc[i] - B);
+                    const uint32_t d = o - so;
+                    if (!pend_clear_smem(pend, so, so + min(d, ml))) { left = true; continue; }
+                    __threadfence_block();  // source reads after the readiness reads
+                    if (d >= ml) {
+                        for (uint32_t k = 0; k < ml; k++) sout[o + k] = sout[so + k];
+                    } else {
+                        for (uint32_t k = 0; k < ml; k++) sout[o + k] = sout[so + k];  // k >= d reads bytes just written
+                    }
+                    __threadfence_block();
+                    pend_update_smem(pend, o, o + ml, false);
+                    tstat[i] = 0;
+                    progress = true;
+                }
+                const int any_left = __syncthreads_or(left);
+                const int any_prog = __syncthreads_or(progress);
+                if (!any_left || !any_prog) break;
+            }
+            // ---- whatever is still unresolved becomes a pending span ----
+            uint32_t cnt = 0;
+            for (uint32_t i = i0; i < i1; i++) cnt += tstat[i] != 0;
+            v3[0] = cnt; v3[1] = 0; v3[2] = 0;
+            block_scan3(v3, tot3, scanbuf);
+            npend = tot3[0];
+            uint32_t k = v3[0];
+            for (uint32_t i = i0; i < i1; i++) {
+                if (!tstat[i]) continue;
+                const uint64_t src = tsrc[i];
+                J.spans[bd.tok_base + k] = SpanRec{(uint32_t)src, (uint32_t)(src >> 32), (uint32_t)(tpos[i] + tll[i]), tml[i]};
+                k++;
+            }
+        }
+        __syncthreads();
+        if (bad) {
+            if (tid == 0) set_err(job.err, kErrCorrupt, stage << 24, b);
+            npend = 0;
+        }
+        // ---- write the block (pending bytes are filled by the cross-block pass) ----
+        uint8_t* gout = J.out + B;
+        const uint32_t nv = R / 16;
+        for (uint32_t i = tid; i < nv; i += kLocThreads) reinterpret_cast<uint4*>(gout)[i] = reinterpret_cast<uint4*>(sout)[i];
+        for (uint32_t x = 16 * nv + tid; x < R; x += kLocThreads) gout[x] = sout[x];
+        if (npend) {
+            uint32_t* gp = J.pmap + (uint64_t)b * (kBlock / 32);
+            for (uint32_t i = tid; i < kBlock / 32; i += kLocThreads) gp[i] = pend[i];
+        }
+        if (tid == 0) J.npend[b] = npend;
+        __syncthreads();
+    }
+}
+
+// ---- cross-block pass --------------------------------------------------------------------
+// Are the bytes [s, e) (absolute) final?  Blocks without pending spans are
+// final after the local pass; otherwise the block's pending bitmap decides.
+__device__ __forceinline__ bool src_final(const uint32_t* npend, const uint32_t* pmap, uint64_t s, uint64_t e) {
+    for (uint64_t a = s >> 14; a <= (e - 1) >> 14; a++) {
+        if (npend[a] == 0) continue;
+        const uint64_t A = a << 14;
+        const uint32_t lo = (uint32_t)((s > A ? s : A) - A);
+        const uint32_t hi = (uint32_t)((e < A + kBlock ? e : A + kBlock) - A);
+        const uint32_t* pm = pmap + a * (kBlock / 32);
+        for (uint32_t w = lo >> 5; w <= ((hi - 1) >> 5); w++)
+            if (ld_relaxed_u32(pm + w) & range_mask(w, lo, hi)) return false;
+    }
+    return true;
+}
+
+constexpr int kExtThreads = 128;
+constexpr uint32_t kPiece = 256;                 // bytes staged per load round
+constexpr uint32_t kStageWords = kPiece / 4 + 2;  // aligned words covering a piece
+
+// Stage the n <= kPiece bytes at absolute position s into this thread's
+// word buffer with independent aligned loads (L2, bypassing L1); returns the
+// byte offset of s inside the buffer.  Words that would reach past the
+// output's end are read byte by byte.
+__device__ __forceinline__ uint32_t stage_bytes(const uint8_t* g, uint64_t total, uint64_t s, uint32_t n,
+                                                uint32_t* buf) {
+    const uint64_t w0 = s >> 2;
+    const uint32_t nw = (uint32_t)(((s + n + 3) >> 2) - w0);
+    const uint32_t* g32 = reinterpret_cast<const uint32_t*>(g);
+#pragma unroll 4
+    for (uint32_t k = 0; k < nw; k++) {
+        const uint64_t wa = (w0 + k) * 4;
+        uint32_t v;
+        if (wa + 4 <= total) {
+            v = __ldcg(g32 + w0 + k);
+        } else {
+            v = 0;
+            for (uint32_t q = 0; q < 4 && wa + q < total; q++) v |= (uint32_t)__ldcg(g + wa + q) << (8 * q);
+        }
+        buf[k] = v;
+    }
+    return (uint32_t)(s & 3);
+}
+
+// Write n bytes from the staged buffer (bytes off.. of buf) to g + dst with
+// aligned word stores in the middle.
+__device__ __forceinline__ void emit_bytes(uint8_t* g, uint64_t dst, uint32_t n, const uint32_t* buf, uint32_t off) {
+    const uint8_t* b8 = reinterpret_cast<const uint8_t*>(buf);
+    uint32_t k = 0;
+    while (k < n && ((dst + k) & 3)) { g[dst + k] = b8[off + k]; k++; }
+    uint32_t* g32 = reinterpret_cast<uint32_t*>(g + dst + k);
+    for (; k + 4 <= n; k += 4) {
+        const uint32_t p = off + k;
+        *g32++ = __funnelshift_r(buf[p >> 2], buf[(p >> 2) + 1], 8 * (p & 3));
+    }
+    for (; k < n; k++) g[dst + k] = b8[off + k];
+}
+
+// out[dst + q] = out[src + (q mod d)] for q < ml, d = dst - src.
+__device__ void span_copy(uint8_t* g, uint64_t total, uint64_t dst, uint64_t src, uint32_t ml, uint32_t* buf) {
+    const uint64_t d = dst - src;
+    if (d < ml && d <= kPiece) {
+        // short period: stage it once and repeat it
+        const uint32_t dd = (uint32_t)d;
+        const uint32_t off = stage_bytes(g, total, src, dd, buf);
+        const uint8_t* b8 = reinterpret_cast<const uint8_t*>(buf);
+        uint32_t r = 0;
+        for (uint32_t q = 0; q < ml; q++) {
+            g[dst + q] = b8[off + r];
+            if (++r == dd) r = 0;
+        }
+        return;
+    }
+    // no overlap, or a period longer than a piece: piece by piece; bytes at or
+    // past d come from the destination written by earlier pieces
+    for (uint32_t q0 = 0; q0 < ml; q0 += kPiece) {
+        const uint32_t n = min(kPiece, ml - q0);
+        const uint64_t s = q0 < d ? src + q0 : dst + q0 - d;
+        if (q0 < d && q0 + n > d) {
+            // the piece straddles the end of the first period: split it
+            const uint32_t n1 = (uint32_t)(d - q0);
+            uint32_t off = stage_bytes(g, total, s, n1, buf);
+            emit_bytes(g, dst + q0, n1, buf, off);
+            off = stage_bytes(g, total, dst, n - n1, buf);
+            emit_bytes(g, dst + q0 + n1, n - n1, buf, off);
+        } else {
+            const uint32_t off = stage_bytes(g, total, s, n, buf);
+            emit_bytes(g, dst + q0, n, buf, off);
+        }
+    }
+}
+
+// Each lane holds at most one span.  Lanes without work take the next spans
+// of the warp's current block, in order; when the block is used up the warp
+// takes the next block from the global ticket.  Spans are therefore handed
+// out in ascending destination order, so the lowest unfinished span always
+// has every source final: the waits cannot deadlock, and a slow span delays
+// only the spans that really read its bytes (no head-of-line blocking).
+__global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
+    __shared__ uint32_t stage[kExtThreads][kStageWords + 1];
+    uint32_t* buf = stage[threadIdx.x];
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1;
+    const uint64_t deadline = gtimer() + job.timeout_ns;
+    // warp-uniform queue state
+    uint32_t blk = 0, cnt = 0, next = 0, base = 0;
+    uint64_t B = 0;
+    bool exhausted = false;
+    ArcJob J = load_arc(job, 0);
+    // lane state (a lane keeps its span's archive: batched jobs mix archives)
+    bool has = false;
+    uint64_t src = 0, dst = 0, l_total = 0;
+    uint32_t ml = 0, o = 0, span_blk = 0;
+    uint32_t* pm = nullptr;
+    uint8_t* l_out = nullptr;
+    const uint32_t* l_npend = nullptr;
+    const uint32_t* l_pmap = nullptr;
+    uint32_t spins = 0;
+    for (;;) {
+        // hand out spans to idle lanes, in lane order
+        uint32_t idle = __ballot_sync(ACX_FULL, !has);
+        while (idle && !exhausted) {
+            if (next >= cnt) {
+                uint32_t item = 0;
+                if (lane == 0) item = atomicAdd(&job.counters[2], 1u);
+                item = __shfl_sync(ACX_FULL, item, 0);
+                if (item >= job.n_items) { exhausted = true; break; }
+                const int a = find_arc(job, item);
+                J = load_arc(job, a);
+                blk = J.lo + (item - J.item_base);
+                cnt = J.npend[blk];
+                next = 0;
+                base = J.blk[blk].tok_base;
+                B = (uint64_t)blk * kBlock;
+                continue;
+            }
+            const uint32_t avail = cnt - next;
+            const uint32_t r = __popc(idle & lt_mask);
+            if (!has && (idle >> lane & 1) && r < avail) {
+                const SpanRec rec = J.spans[base + next + r];
+                src = (uint64_t)rec.x | ((uint64_t)rec.y << 32);
+                o = rec.z;
+                ml = rec.w;
+                dst = B + o;
+                span_blk = blk;
+                pm = J.pmap + (uint64_t)blk * (kBlock / 32);
+                l_out = J.out;
+                l_total = J.total;
+                l_npend = J.npend;
+                l_pmap = J.pmap;
+                has = true;
+            }
+            next += min(avail, (uint32_t)__popc(idle));
+            idle = __ballot_sync(ACX_FULL, !has);
+        }
+        if (!__any_sync(ACX_FULL, has)) break;
+        bool progressed = false;
+        if (has) {
+            const uint64_t d = dst - src;
+            const uint64_t se = src + (d < ml ? d : ml);  // periodic source window
+            if (src_final(l_npend, l_pmap, src, se)) {
+                __threadfence();  // source bytes were written before their bits cleared
+                span_copy(l_out, l_total, dst, src, ml, buf);
+                __threadfence();
+                for (uint32_t w = o >> 5; w <= ((o + ml - 1) >> 5); w++) atomicAnd(pm + w, ~range_mask(w, o, o + ml));
+                has = false;
+                progressed = true;
+            }
+        }
+        if (__any_sync(ACX_FULL, progressed)) {
+            spins = 0;
+        } else {
+            __nanosleep(64);
+            // (the decision must be warp-uniform: every lane leaves together)
+            if ((++spins & 15) == 0 && __any_sync(ACX_FULL, gtimer() > deadline)) {
+                if (has) set_err(job.err, kErrTimeout, kStageWait << 24, span_blk);
+                break;
+            }
+        }
+    }
+}
+
+size_t local_smem_bytes(uint32_t T, uint32_t LB) { return loc_layout(T, LB).total; }
+
+cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st) {
+    const size_t sm = local_smem_bytes(job.max_tok, job.max_lenb);
+    cudaError_t e = cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_local<<<grid, kLocThreads, sm, st>>>(job);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st) {
+    k_external<<<grid, kExtThreads, 0, st>>>(job);
+    return cudaGetLastError();
+}
+
+int local_occupancy(size_t smem) {
+    cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_local, kLocThreads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+int external_occupancy() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_external, kExtThreads, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace acx

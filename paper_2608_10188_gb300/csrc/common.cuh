@@ -1,0 +1,93 @@
+// Device helpers shared by the decode kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace acx {
+
+#define ACX_FULL 0xffffffffu
+
+constexpr int kErrCorrupt = -2;
+constexpr int kErrTimeout = -5;
+
+// Error stages recorded beside the first error status.
+enum : int {
+    kStageRans = 1,
+    kStageVarint = 2,
+    kStageTokens = 3,
+    kStageSources = 4,
+    kStageWait = 5,
+    kStagePlain = 6,
+    kStageLimits = 7,
+};
+
+// err[0]: first status; err[1]: stage << 24 | detail; err[2]: block index.
+__device__ __forceinline__ void set_err(int* err, int code, int where, uint32_t block) {
+    if (atomicCAS(err, 0, code) == 0) {
+        err[1] = where;
+        err[2] = (int)block;
+    }
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ---- mbarrier / TMA (1-D bulk copies) ---------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ int find_arc(const JobDev& job, uint32_t item) {
+    if (!job.arcs) return 0;
+    int lo = 0, hi = (int)job.n_arcs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (job.arcs[mid].item_base <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ ArcJob load_arc(const JobDev& job, int a) { return job.arcs ? job.arcs[a] : job.one; }
+
+// Bit masks of the bytes [s, e) of a 16 KiB block bitmap, word by word.
+__device__ __forceinline__ uint32_t range_mask(uint32_t w, uint32_t s, uint32_t e) {
+    uint32_t m = 0xffffffffu;
+    if (w == (s >> 5)) m &= 0xffffffffu << (s & 31);
+    if (w == ((e - 1) >> 5)) m &= 0xffffffffu >> (31 - ((e - 1) & 31));
+    return m;
+}
+
+}  // namespace acx

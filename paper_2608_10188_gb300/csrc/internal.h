@@ -31,15 +31,17 @@ struct BlockDev {
     uint32_t s_enc[4];     // body length in bytes (without padding)
     uint32_t s_off[4];     // offset of each decoded stream inside the block's scratch region
     uint8_t s_K[4];        // rANS lanes
-    uint32_t pad[3];
+    uint32_t tok_base;     // tokens of all earlier blocks (index of this block's pending-span slots)
+    uint32_t pad[2];
 };
 static_assert(sizeof(BlockDev) % 16 == 0, "BlockDev alignment");
 
-// Publish states of a block during one decode call (low 2 bits), tagged with
-// the call's epoch in the upper 30 bits so no reset is needed between calls.
-constexpr uint32_t kStPublished = 1;   // block written, some bytes still pending (see pending bitmap)
-constexpr uint32_t kStComplete = 2;    // every byte of the block is final
-constexpr uint32_t kStAlways = 0xFFFFFFFFu;  // block final independently of the epoch (cache)
+// A pending span: match bytes whose source chain leaves their block, left for
+// the cross-block pass.  {x, y} = absolute source (lo, hi), z = destination
+// offset inside the block, w = match length.
+struct alignas(16) SpanRec {
+    uint32_t x, y, z, w;
+};
 
 // One archive inside a decode job.
 struct ArcJob {
@@ -48,8 +50,9 @@ struct ArcJob {
     const uint32_t* dtab;     // 4 x 4096 rANS decode entries: sym | (f-1)<<8 | (slot-c)<<20
     uint8_t* scratch;         // decoded streams
     uint8_t* out;             // output: block b at out + b*kBlock
-    uint32_t* state;          // per block publish state
-    uint32_t* pmap;           // per block pending bitmap, 512 words per block
+    uint32_t* npend;          // per block: number of pending spans after the local pass
+    uint32_t* pmap;           // per block pending-byte bitmap, 512 words (valid when npend > 0)
+    SpanRec* spans;           // pending spans, slots [tok_base, tok_base + n_tok) per block
     uint64_t total;           // decompressed size
     uint32_t n_blocks;
     uint32_t lo, hi;          // blocks [lo, hi) are decoded by this job
@@ -63,7 +66,7 @@ struct JobDev {
     const ArcJob* arcs;       // device array of archives (batched jobs), or nullptr
     uint32_t n_arcs;
     uint32_t n_items;         // total blocks over all archives
-    uint32_t* counters;       // [0] epoch, [1] assembly ticket, [2 + a] rANS ticket of archive a
+    uint32_t* counters;       // [1] local ticket, [2] external ticket, [3 + a] rANS ticket of archive a
     int* err;                 // first error status (0 = ok)
     uint64_t timeout_ns;
     uint32_t max_tok;         // shared-memory sizing of the assembly kernel

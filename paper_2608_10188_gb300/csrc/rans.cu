@@ -1,0 +1,257 @@
+// Entropy stage of the decode (paper, Table 1/2: "ANS"): interleaved-rANS
+// lane decoders for the four per-block streams, one warp per block.
+//
+// Stream layout (format v1): K initial 32-bit states (padded to 16 B), then
+// 16-bit renormalisation words in decode order.  Symbol i belongs to lane
+// i mod K; a step decodes one symbol per lane; lanes whose state fell below
+// 2^16 take the next words in lane order (ballot + popc gives each its rank).
+//
+// GB300 mapping:
+//  * decode tables of the four stream types (4 x 4096 u32 entries:
+//    sym | (f-1) << 8 | (slot-c) << 20) live in shared memory, shared by the
+//    16 warps of a CTA;
+//  * each warp streams its words through a 2 KiB shared-memory ring filled
+//    by 512-byte 1-D TMA bulk copies (cp.async.bulk + mbarrier), kept up to
+//    three chunks ahead of the decoder;
+//  * K = 64 / 128 lanes run as 2 / 4 independent states per warp lane (ILP);
+//  * ring residency is checked once per 4 steps, not per step.
+// Every wait is bounded by %globaltimer.
+#include "common.cuh"
+
+namespace acx {
+
+constexpr int kRansWarps = 16;
+constexpr int kRingWords = 1024;   // 2 KiB of 16-bit words per warp
+constexpr int kChunkWords = 256;   // one TMA chunk = 512 B
+constexpr int kSlots = kRingWords / kChunkWords;
+constexpr int kStepGroup = 4;      // steps between ring checks
+
+struct RansSmem {
+    uint32_t tab[4][kM];                     // 64 KiB
+    uint16_t ring[kRansWarps][kRingWords];   // 32 KiB
+    uint64_t bar[kRansWarps][kSlots];
+    int arc;                                 // archive whose tables are loaded
+    int next_arc;
+};
+
+__device__ __forceinline__ bool wait_chunk(uint64_t* bar, uint32_t q, uint64_t deadline) {
+    uint32_t spins = 0;
+    bool ok = true;
+    while (!mbar_try_wait(&bar[q % kSlots], (q / kSlots) & 1)) {
+        if ((++spins & 1023) == 0 && gtimer() > deadline) { ok = false; break; }
+    }
+    return __all_sync(ACX_FULL, ok);
+}
+
+__device__ __forceinline__ void issue_chunk(uint16_t* ring, uint64_t* bar, const uint8_t* words, uint32_t q,
+                                            uint32_t c, uint32_t wbytes, int lane) {
+    if (lane == 0) {
+        const uint32_t slot = q % kSlots;
+        const uint32_t bytes = min(512u, wbytes - 512 * c);
+        mbar_arrive_tx(&bar[slot], bytes);
+        tma_load_1d(ring + slot * kChunkWords, words + 512 * c, bytes, &bar[slot]);
+    }
+}
+
+// Decode one stream with one warp; S states per lane (S = 1 for K <= 32,
+// else K / 32).  `seq` counts the TMA chunks this warp has used (slot and
+// mbarrier phase bookkeeping across streams).  Returns false on a format
+// violation (word overrun, end states != 2^16) or an expired wait.
+template <int S>
+__device__ bool rans_stream(const uint32_t* __restrict__ tab, const uint8_t* __restrict__ body, uint32_t enc,
+                            uint32_t n, uint32_t K, uint8_t* __restrict__ out, uint16_t* ring, uint64_t* bar,
+                            uint32_t& seq, int lane, uint64_t deadline) {
+    const uint32_t hdr = (4 * K + 15) & ~15u;
+    if (enc < hdr || ((enc - hdr) & 1)) return false;
+    const uint32_t W = (enc - hdr) >> 1;
+    const uint8_t* words = body + hdr;
+    const uint32_t wbytes = (2 * W + 15) & ~15u;
+    const uint32_t nchunks = (wbytes + 511) / 512;
+    uint32_t x[S];
+    bool ok = true;
+#pragma unroll
+    for (int s = 0; s < S; s++) {
+        const uint32_t j = 32 * s + lane;
+        x[s] = j < K ? *reinterpret_cast<const uint32_t*>(body + 4 * j) : 0;
+        ok = ok && (j >= K || x[s] >= kL);
+    }
+    ok = __all_sync(ACX_FULL, ok);
+    const uint32_t seq0 = seq;
+    // local chunk c lands in ring slot (seq0 + c) % kSlots, so word w of this
+    // stream sits at ring[(rbase + w) % kRingWords]
+    const uint32_t rbase = (seq0 % kSlots) * kChunkWords;
+    uint32_t issued = 0, ready = 0;
+    for (; issued < nchunks && issued < (uint32_t)kSlots; issued++)
+        issue_chunk(ring, bar, words, seq0 + issued, issued, wbytes, lane);
+    const uint32_t lt_mask = (1u << lane) - 1;
+    uint32_t p = 0;
+    const uint32_t steps = ok ? (n + K - 1) / K : 0;
+    for (uint32_t t0 = 0; t0 < steps; t0 += kStepGroup) {
+        // the next kStepGroup steps read at most kStepGroup * 32 * S words from p on
+        while (ready < nchunks && ready * kChunkWords < p + kStepGroup * 32 * S) {
+            if (!wait_chunk(bar, seq0 + ready, deadline)) { ok = false; break; }
+            ready++;
+        }
+        if (!ok) break;
+        // refill slots whose previous chunk lies wholly below p
+        if (issued < nchunks && 256 * (issued + 1) <= p + 256 * kSlots) {
+            __syncwarp();
+            do {
+                issue_chunk(ring, bar, words, seq0 + issued, issued, wbytes, lane);
+                issued++;
+            } while (issued < nchunks && 256 * (issued + 1) <= p + 256 * kSlots);
+        }
+#pragma unroll
+        for (int u = 0; u < kStepGroup; u++) {
+            const uint32_t t = t0 + u;
+            bool need[S];
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                const uint32_t j = 32 * s + lane, i = t * K + j;
+                need[s] = false;
+                if (j < K && i < n) {
+                    const uint32_t e = tab[x[s] & (kM - 1)];
+                    out[i] = (uint8_t)e;
+                    const uint32_t q = x[s] >> kProbBits;
+                    x[s] = ((e >> 8) & 0xfffu) * q + q + (e >> 20);  // f * (x >> 12) + (slot - c)
+                    need[s] = x[s] < kL;
+                }
+            }
+            // words are taken in stream-lane order j = 0..K-1 within the step
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                const uint32_t b = __ballot_sync(ACX_FULL, need[s]);
+                if (need[s]) x[s] = (x[s] << 16) | ring[(rbase + p + __popc(b & lt_mask)) & (kRingWords - 1)];
+                p += __popc(b);
+            }
+        }
+        if (p > W) { ok = false; break; }
+    }
+    // drain chunks still in flight so the barrier phases stay in step
+    while (ready < issued) {
+        if (!wait_chunk(bar, seq0 + ready, deadline)) { ok = false; break; }
+        ready++;
+    }
+    seq = seq0 + issued;
+    ok = ok && p == W;
+    bool fin = true;
+#pragma unroll
+    for (int s = 0; s < S; s++) fin = fin && (32 * s + lane >= K || x[s] == kL);
+    return __all_sync(ACX_FULL, ok && fin);
+}
+
+__device__ void copy_stored(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, uint32_t n, int lane) {
+    const uint32_t nv = (n + 15) / 16;  // bodies and scratch streams are 16-aligned and padded
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (uint32_t i = lane; i < nv; i += 32) d[i] = s[i];
+}
+
+// Start of a decode call: every ticket restarts at zero.
+__global__ void k_prologue(uint32_t* counters, uint32_t n_counters) {
+    for (uint32_t i = threadIdx.x; i < n_counters; i += blockDim.x) counters[i] = 0;
+}
+
+// Each CTA works on one archive at a time (its tables in shared memory);
+// its warps take blocks of that archive from the archive's ticket, and when
+// the archive is exhausted the CTA moves to the archive with the most blocks
+// left.
+__global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
+    extern __shared__ __align__(128) uint8_t smraw[];
+    RansSmem& S = *reinterpret_cast<RansSmem*>(smraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < kSlots) mbar_init(&S.bar[warp][lane], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (threadIdx.x == 0) {
+        const uint64_t target = (uint64_t)blockIdx.x * job.n_items / gridDim.x;
+        S.next_arc = job.n_arcs > 1 ? find_arc(job, (uint32_t)target) : 0;
+        S.arc = -1;
+    }
+    __syncthreads();
+    const uint64_t deadline = gtimer() + job.timeout_ns;
+    uint32_t seq = 0;
+    uint32_t* tickets = job.counters + 3;
+    for (;;) {
+        const int a = S.next_arc;
+        if (a < 0) break;
+        const ArcJob J = load_arc(job, a);
+        if (S.arc != a) {
+            const uint4* src = reinterpret_cast<const uint4*>(J.dtab);
+            uint4* dst = reinterpret_cast<uint4*>(&S.tab[0][0]);
+            for (int i = threadIdx.x; i < (int)(4 * kM / 4); i += blockDim.x) dst[i] = src[i];
+            __syncthreads();
+            if (threadIdx.x == 0) S.arc = a;
+        }
+        const uint32_t n_a = J.hi - J.lo;
+        for (;;) {
+            uint32_t it = 0;
+            if (lane == 0) it = atomicAdd(&tickets[a], 1u);
+            it = __shfl_sync(ACX_FULL, it, 0);
+            if (it >= n_a) break;
+            const uint32_t b = J.lo + it;
+            const BlockDev& bd = J.blk[b];
+            const uint8_t* pay = J.arc + bd.payload;
+            uint8_t* scr = J.scratch + bd.scratch;
+            bool ok = true;
+            int fs = 0;
+            for (int s = 0; s < 4 && ok; s++) {
+                fs = s;
+                const uint32_t n = bd.s_raw[s];
+                if (n == 0) continue;
+                uint8_t* o = scr + bd.s_off[s];
+                const uint8_t* body = pay + bd.s_body[s];
+                if (bd.rans_mask & (1u << s)) {
+                    const uint32_t K = bd.s_K[s];
+                    const uint32_t* tb = &S.tab[s][0];
+                    uint16_t* ring = &S.ring[warp][0];
+                    uint64_t* bar = &S.bar[warp][0];
+                    if (K <= 32) ok = rans_stream<1>(tb, body, bd.s_enc[s], n, K, o, ring, bar, seq, lane, deadline);
+                    else if (K == 64) ok = rans_stream<2>(tb, body, bd.s_enc[s], n, K, o, ring, bar, seq, lane, deadline);
+                    else ok = rans_stream<4>(tb, body, bd.s_enc[s], n, K, o, ring, bar, seq, lane, deadline);
+                } else {
+                    copy_stored(body, o, n, lane);
+                }
+            }
+            if (!ok && lane == 0) set_err(job.err, kErrCorrupt, (kStageRans << 24) | fs, b);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int best = -1;
+            uint32_t best_left = 0;
+            for (uint32_t k = 0; k < job.n_arcs; k++) {
+                const ArcJob Jk = load_arc(job, (int)k);
+                const uint32_t taken = *((volatile uint32_t*)&tickets[k]);
+                const uint32_t n_k = Jk.hi - Jk.lo;
+                const uint32_t left = taken < n_k ? n_k - taken : 0;
+                if (left > best_left) { best_left = left; best = (int)k; }
+            }
+            S.next_arc = best;
+        }
+        __syncthreads();
+    }
+}
+
+size_t rans_smem_bytes() { return sizeof(RansSmem); }
+
+cudaError_t launch_prologue(uint32_t* counters, uint32_t n_counters, cudaStream_t st) {
+    k_prologue<<<1, 128, 0, st>>>(counters, n_counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rans(const JobDev& job, int grid, cudaStream_t st) {
+    const size_t sm = rans_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_rans, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_rans<<<grid, kRansWarps * 32, sm, st>>>(job);
+    return cudaGetLastError();
+}
+
+int rans_occupancy() {
+    const size_t sm = rans_smem_bytes();
+    cudaFuncSetAttribute(k_rans, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rans, kRansWarps * 32, sm) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace acx
