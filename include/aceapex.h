@@ -65,6 +65,10 @@ typedef struct {
     uint32_t min_match;  /* minimum match length, >= 4 (default 4) */
     uint32_t max_lanes;  /* rANS lane cap K, power of two <= 128 (default 32) */
     int threads;         /* encoder threads (default: hardware concurrency) */
+    int latest_source;   /* 1: long-range matches point at the latest earlier copy of their
+                            content (classic hash-chain choice); 0 (default): at the first
+                            occurrence, which costs the same with absolute offsets and keeps
+                            cross-block dependency chains short */
 } aceapex_enc_params;
 
 /* Decoder variants. */

@@ -163,7 +163,7 @@ int aceapex_ctx_set_params(aceapex_ctx* c, const aceapex_dec_params* p) {
 int aceapex_encode(const uint8_t* src, uint64_t n, const aceapex_enc_params* p, uint8_t** out, uint64_t* out_len) {
     aceapex_enc_params d{};
     if (p) d = *p;
-    return encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, out, out_len);
+    return encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, d.latest_source, out, out_len);
 }
 
 void aceapex_free(void* p) { free(p); }

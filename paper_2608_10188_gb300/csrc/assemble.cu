@@ -34,7 +34,7 @@ constexpr int kLocWarps = kLocThreads / 32;
 constexpr uint64_t kRefTag = 1ull << 63;  // history map entry "copy input entry k"
 
 struct LocLayout {
-    uint32_t out, pend, tsrc, tpos, tll, tml, tlit, tcmd, tstat, lenb, scan, misc, total;
+    uint32_t out, pend, tsrc, tpos, tll, tml, tlit, tcmd, tstat, lenb, soff, slit, scan, bar, misc, total;
 };
 
 __host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB) {
@@ -57,7 +57,10 @@ __host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB) {
     L.tcmd = take(T16 + 16, 16);
     L.tstat = take(T16, 16);
     L.lenb = take(((LB + 15) & ~15u) + 16, 16);
+    L.soff = take(((5 * T + 15) & ~15u) + 16, 16);
+    L.slit = take(kBlock + 16, 16);
     L.scan = take(kLocWarps * 4 * 4 + 64, 16);
+    L.bar = take(8, 8);
     L.misc = take(64, 16);
     L.total = (o + 127) & ~127u;
     return L;
@@ -145,22 +148,23 @@ __device__ __forceinline__ void pend_update_smem(uint32_t* pend, uint32_t s, uin
     }
 }
 
-// Literal run: out[b, b+L) = lit[a, a+L), one warp, 4-byte funnel-shifted words.
+// Literal run: out[b, b+L) = lit[a, a+L) (both in shared memory), one warp,
+// 4-byte funnel-shifted words in the middle, bytes at the ragged ends.
 __device__ __forceinline__ void copy_run(uint8_t* __restrict__ sout, const uint8_t* __restrict__ lit, uint32_t a,
                                          uint32_t b, uint32_t L, int lane) {
     if (!L) return;
     const uint32_t e = b + L;
     const uint32_t w0 = (b + 3) >> 2, w1 = e >> 2;  // whole words [w0, w1)
     if (w0 >= w1) {
-        for (uint32_t x = b + lane; x < e; x += 32) sout[x] = __ldg(lit + a + (x - b));
+        for (uint32_t x = b + lane; x < e; x += 32) sout[x] = lit[a + (x - b)];
         return;
     }
-    if (lane < (int)(4 * w0 - b)) sout[b + lane] = __ldg(lit + a + lane);
-    if (lane < (int)(e - 4 * w1)) sout[4 * w1 + lane] = __ldg(lit + a + (4 * w1 + lane - b));
+    if (lane < (int)(4 * w0 - b)) sout[b + lane] = lit[a + lane];
+    if (lane < (int)(e - 4 * w1)) sout[4 * w1 + lane] = lit[a + (4 * w1 + lane - b)];
     const uint32_t* lw = reinterpret_cast<const uint32_t*>(lit);
     for (uint32_t w = w0 + lane; w < w1; w += 32) {
         const uint32_t src = a + (4 * w - b);
-        const uint32_t lo = __ldg(lw + (src >> 2)), hi = __ldg(lw + (src >> 2) + 1);
+        const uint32_t lo = lw[src >> 2], hi = lw[(src >> 2) + 1];
         reinterpret_cast<uint32_t*>(sout)[w] = __funnelshift_r(lo, hi, 8 * (src & 3));
     }
 }
@@ -178,9 +182,17 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
     uint8_t* tcmd = sm + L.tcmd;
     uint8_t* tstat = sm + L.tstat;
     uint8_t* lenb = sm + L.lenb;
+    uint8_t* soff = sm + L.soff;
+    uint8_t* slit = sm + L.slit;
     uint32_t* scanbuf = reinterpret_cast<uint32_t*>(sm + L.scan);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
     volatile uint32_t* misc = reinterpret_cast<volatile uint32_t*>(sm + L.misc);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t deadline = gtimer() + job.timeout_ns;
+    if (tid == 0) mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    uint32_t phase = 0;
 
     for (;;) {
         if (tid == 0) misc[0] = atomicAdd(&job.counters[1], 1u);
@@ -195,24 +207,35 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
         const uint32_t R = bd.raw_len, n = bd.n_tok, LB = bd.s_raw[kLen], n_lit = bd.s_raw[kLit];
         const uint32_t n_new = bd.n_new;
         const uint8_t* scr = J.scratch + bd.scratch;
-        const uint8_t* g_off = scr + bd.s_off[kOff];
-        const uint8_t* g_lit = scr + bd.s_off[kLit];
-        bool bad = n > job.max_tok || LB > job.max_lenb;
+        bool bad = n > job.max_tok || LB > job.max_lenb || n_new > job.max_tok;
         int stage = bad ? kStageLimits : 0;
         auto mark = [&](bool cond, int st) {
             if (cond && !bad) { bad = true; stage = st; }
         };
 
-        // ---- stage cmd and len bytes (16-byte vectors; streams are 16-aligned and padded) ----
-        if (!bad) {
-            const uint4* c4 = reinterpret_cast<const uint4*>(scr + bd.s_off[kCmd]);
-            const uint4* l4 = reinterpret_cast<const uint4*>(scr + bd.s_off[kLen]);
-            for (uint32_t i = tid; i < (n + 15) / 16; i += kLocThreads) reinterpret_cast<uint4*>(tcmd)[i] = c4[i];
-            for (uint32_t i = tid; i < (LB + 15) / 16; i += kLocThreads) reinterpret_cast<uint4*>(lenb)[i] = l4[i];
+        // ---- stage the four decoded streams with 1-D TMA bulk copies (16-aligned, padded) ----
+        if (!bad && tid == 0) {
+            const uint32_t sz[4] = {(n + 15) & ~15u, (LB + 15) & ~15u, (5 * n_new + 15) & ~15u, (n_lit + 15) & ~15u};
+            uint8_t* dsts[4] = {tcmd, lenb, soff, slit};
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic use of the buffers
+            mbar_arrive_tx(bar, sz[0] + sz[1] + sz[2] + sz[3]);
+            for (int q = 0; q < 4; q++)
+                if (sz[q]) tma_load_1d(dsts[q], scr + bd.s_off[q], sz[q], bar);
         }
         for (uint32_t i = tid; i < kBlock / 32; i += kLocThreads) pend[i] = 0;
         if (tid == 0) misc[1] = 0;
-        __syncthreads();
+        bool timed_out = false;
+        if (!bad) {
+            uint32_t spins = 0;
+            while (!mbar_try_wait(bar, phase & 1))
+                if ((++spins & 1023) == 0 && gtimer() > deadline) { timed_out = true; break; }
+            phase++;
+        }
+        if (__syncthreads_or(timed_out)) {
+            // a copy that never lands: give up on the decode (the barrier phase is lost)
+            if (tid == 0) set_err(job.err, kErrTimeout, kStageWait << 24, b);
+            return;
+        }
 
         // ---- varints: each byte < 0x80 ends a value ----
         uint32_t v3[3], tot3[3];
@@ -284,7 +307,7 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
                 uint64_t src = 0;
                 if (tcmd[i] == kNew) {
 #pragma unroll
-                    for (int p = 0; p < 5; p++) src |= (uint64_t)__ldg(g_off + (uint64_t)p * n_new + ni) << (8 * p);
+                    for (int p = 0; p < 5; p++) src |= (uint64_t)soff[p * n_new + ni] << (8 * p);
                     ni++;
                     if (src >= B + pos + ll) misc[1] = 1;  // every absolute offset precedes its destination
                 }
@@ -337,7 +360,7 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
         uint32_t npend = 0;
         if (!bad) {
             // ---- literal placement: one warp per run ----
-            for (uint32_t i = warp; i < n; i += kLocWarps) copy_run(sout, g_lit, tlit[i], tpos[i], tll[i], lane);
+            for (uint32_t i = warp; i < n; i += kLocWarps) copy_run(sout, slit, tlit[i], tpos[i], tll[i], lane);
             // ---- every match byte starts unresolved; external sources are pending for good ----
             for (uint32_t i = tid; i < n; i += kLocThreads) {
                 const uint32_t ml = tml[i];
@@ -419,7 +442,7 @@ __device__ __forceinline__ bool src_final(const uint32_t* npend, const uint32_t*
         const uint32_t hi = (uint32_t)((e < A + kBlock ? e : A + kBlock) - A);
         const uint32_t* pm = pmap + a * (kBlock / 32);
         for (uint32_t w = lo >> 5; w <= ((hi - 1) >> 5); w++)
-            if (ld_relaxed_u32(pm + w) & range_mask(w, lo, hi)) return false;
+            if (ld_acquire_u32(pm + w) & range_mask(w, lo, hi)) return false;  // pairs with red_and_release
     }
     return true;
 }
@@ -569,10 +592,9 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             const uint64_t d = dst - src;
             const uint64_t se = src + (d < ml ? d : ml);  // periodic source window
             if (src_final(l_npend, l_pmap, src, se)) {
-                __threadfence();  // source bytes were written before their bits cleared
                 span_copy(l_out, l_total, dst, src, ml, buf);
-                __threadfence();
-                for (uint32_t w = o >> 5; w <= ((o + ml - 1) >> 5); w++) atomicAnd(pm + w, ~range_mask(w, o, o + ml));
+                for (uint32_t w = o >> 5; w <= ((o + ml - 1) >> 5); w++)
+                    red_and_release(pm + w, ~range_mask(w, o, o + ml));
                 has = false;
                 progressed = true;
             }

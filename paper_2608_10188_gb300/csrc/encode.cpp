@@ -6,8 +6,10 @@
 // suppressed and every match goes out with an explicit offset, keeping the
 // same matches (so the history-free archive differs only in coding).
 //
-// Match search: a long-window hash (16 bytes, any distance, most recent
-// position) finds copies anywhere earlier; a short-window hash (6 bytes,
+// Match search: a long-window hash (16 bytes, any distance) finds copies
+// anywhere earlier; by default it keeps the FIRST occurrence of a window, so a
+// copy of a copy points at the original bytes (with absolute offsets this
+// costs no offset bits, and it keeps cross-block dependency chains short); a short-window hash (6 bytes,
 // recent positions) finds local repeats; the four history distances and
 // distances 1..4 are always tried.  A match is taken when its estimated
 // saving in bits (length x literal cost - token cost) is positive, which
@@ -133,6 +135,7 @@ struct Parser {
     const uint8_t* s;
     uint64_t n;
     bool no_rep;
+    bool oldest;         // long-window table keeps the first occurrence instead of the latest
     uint32_t min_match;
     double lit_bits;
     int lbits, sbits;
@@ -148,7 +151,10 @@ struct Parser {
         return (uint32_t)((a * 0xCF1BBCDCB7A56463ULL) >> (64 - bits));
     }
     void insert(uint64_t p) {
-        if (p + 16 <= n) hl[hash_long(s + p, lbits)] = p + 1;
+        if (p + 16 <= n) {
+            uint64_t& slot = hl[hash_long(s + p, lbits)];
+            if (!oldest || !slot) slot = p + 1;
+        }
         if (p + 8 <= n) hs[hash_short(s + p, sbits)] = (uint32_t)(p + 1);
     }
     // cost in bits of a NEW token (cmd + two varints + absolute offset)
@@ -248,7 +254,7 @@ void parallel_for(uint32_t n, int threads, F fn) {
 }  // namespace
 
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   uint8_t** out, uint64_t* out_len) {
+                   int latest, uint8_t** out, uint64_t* out_len) {
     if (!out || !out_len || (n && !src)) return -1;
     if (min_match == 0) min_match = 4;
     if (max_lanes == 0) max_lanes = 32;
@@ -271,6 +277,7 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
         P.s = src;
         P.n = n;
         P.no_rep = no_rep != 0;
+        P.oldest = latest == 0;
         P.min_match = min_match;
         P.lit_bits = std::max(H, 1.0) + 0.1;
         P.lbits = 16;

@@ -24,7 +24,7 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why);
 
 // Library encoder (format v1); out is malloc'ed.
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   uint8_t** out, uint64_t* out_len);
+                   int latest, uint8_t** out, uint64_t* out_len);
 
 // FNV-1a 64.
 uint64_t fnv1a64(const uint8_t* p, uint64_t n);

@@ -27,7 +27,7 @@ EXPORTED = [
 
 class EncParams(ctypes.Structure):
     _fields_ = [("no_rep", ctypes.c_int), ("min_match", ctypes.c_uint32), ("max_lanes", ctypes.c_uint32),
-                ("threads", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("latest_source", ctypes.c_int)]
 
 
 class DecParams(ctypes.Structure):
@@ -99,13 +99,14 @@ def _check(rc, ctx=None, what=""):
     return rc
 
 
-def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, threads: int = 0) -> bytes:
+def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, threads: int = 0,
+           latest_source: bool = False) -> bytes:
     """aceapex_encode on host bytes (numpy uint8 array or bytes)."""
     import numpy as np
     L = load()
     a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data,
                              dtype=np.uint8)
-    p = EncParams(int(no_rep), min_match, max_lanes, threads)
+    p = EncParams(int(no_rep), min_match, max_lanes, threads, int(latest_source))
     ptr = ctypes.c_void_p()
     n = ctypes.c_uint64()
     _check(L.aceapex_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(p), ctypes.byref(ptr),
