@@ -373,25 +373,38 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
                 tstat[i] = st;
             }
             __syncthreads();
-            // ---- in-block matches: rounds of ready periodic fills ----
+            // ---- in-block matches: rounds of ready periodic fills, one warp per match ----
             for (;;) {
                 bool progress = false, left = false;
-                for (uint32_t i = tid; i < n; i += kLocThreads) {
+                for (uint32_t i = warp; i < n; i += kLocWarps) {
                     if (tstat[i] != 1) continue;
                     const uint32_t ml = tml[i];
                     const uint32_t o = tpos[i] + tll[i];
                     const uint32_t so = (uint32_t)(tsrc[i] - B);
                     const uint32_t d = o - so;
-                    if (!pend_clear_smem(pend, so, so + min(d, ml))) { left = true; continue; }
+                    const uint32_t we = so + min(d, ml);  // periodic source window [so, we)
+                    bool busy = false;
+                    for (uint32_t w = (so >> 5) + lane; w <= ((we - 1) >> 5); w += 32)
+                        busy |= (((volatile uint32_t*)pend)[w] & range_mask(w, so, we)) != 0;
+                    if (__any_sync(ACX_FULL, busy)) { left = true; continue; }
                     __threadfence_block();  // source reads after the readiness reads
                     if (d >= ml) {
-                        for (uint32_t k = 0; k < ml; k++) sout[o + k] = sout[so + k];
+                        for (uint32_t k = lane; k < ml; k += 32) sout[o + k] = sout[so + k];
                     } else {
-                        for (uint32_t k = 0; k < ml; k++) sout[o + k] = sout[so + k];  // k >= d reads bytes just written
+                        // out[o+k] = out[so + (k mod d)]: the source window only, so lanes are independent
+                        uint32_t r = lane % d;
+                        const uint32_t step = 32 % d;
+                        for (uint32_t k = lane; k < ml; k += 32) {
+                            sout[o + k] = sout[so + r];
+                            r += step;
+                            if (r >= d) r -= d;
+                        }
                     }
+                    __syncwarp();
                     __threadfence_block();
-                    pend_update_smem(pend, o, o + ml, false);
-                    tstat[i] = 0;
+                    for (uint32_t w = (o >> 5) + lane; w <= ((o + ml - 1) >> 5); w += 32)
+                        atomicAnd(&pend[w], ~range_mask(w, o, o + ml));
+                    if (lane == 0) tstat[i] = 0;
                     progress = true;
                 }
                 const int any_left = __syncthreads_or(left);
@@ -448,77 +461,47 @@ __device__ __forceinline__ bool src_final(const uint32_t* npend, const uint32_t*
 }
 
 constexpr int kExtThreads = 128;
-constexpr uint32_t kPiece = 256;                 // bytes staged per load round
-constexpr uint32_t kStageWords = kPiece / 4 + 2;  // aligned words covering a piece
+constexpr int kCopyUnroll = 8;  // 256 bytes of loads in flight per lane-group before the stores
 
-// Stage the n <= kPiece bytes at absolute position s into this thread's
-// word buffer with independent aligned loads (L2, bypassing L1); returns the
-// byte offset of s inside the buffer.  Words that would reach past the
-// output's end are read byte by byte.
-__device__ __forceinline__ uint32_t stage_bytes(const uint8_t* g, uint64_t total, uint64_t s, uint32_t n,
-                                                uint32_t* buf) {
-    const uint64_t w0 = s >> 2;
-    const uint32_t nw = (uint32_t)(((s + n + 3) >> 2) - w0);
-    const uint32_t* g32 = reinterpret_cast<const uint32_t*>(g);
-#pragma unroll 4
-    for (uint32_t k = 0; k < nw; k++) {
-        const uint64_t wa = (w0 + k) * 4;
-        uint32_t v;
-        if (wa + 4 <= total) {
-            v = __ldcg(g32 + w0 + k);
-        } else {
-            v = 0;
-            for (uint32_t q = 0; q < 4 && wa + q < total; q++) v |= (uint32_t)__ldcg(g + wa + q) << (8 * q);
-        }
-        buf[k] = v;
-    }
-    return (uint32_t)(s & 3);
-}
-
-// Write n bytes from the staged buffer (bytes off.. of buf) to g + dst with
-// aligned word stores in the middle.
-__device__ __forceinline__ void emit_bytes(uint8_t* g, uint64_t dst, uint32_t n, const uint32_t* buf, uint32_t off) {
-    const uint8_t* b8 = reinterpret_cast<const uint8_t*>(buf);
-    uint32_t k = 0;
-    while (k < n && ((dst + k) & 3)) { g[dst + k] = b8[off + k]; k++; }
-    uint32_t* g32 = reinterpret_cast<uint32_t*>(g + dst + k);
-    for (; k + 4 <= n; k += 4) {
-        const uint32_t p = off + k;
-        *g32++ = __funnelshift_r(buf[p >> 2], buf[(p >> 2) + 1], 8 * (p & 3));
-    }
-    for (; k < n; k++) g[dst + k] = b8[off + k];
-}
-
-// out[dst + q] = out[src + (q mod d)] for q < ml, d = dst - src.
-__device__ void span_copy(uint8_t* g, uint64_t total, uint64_t dst, uint64_t src, uint32_t ml, uint32_t* buf) {
+// The whole warp copies one span: out[dst + k] = out[src + (k mod d)], d =
+// dst - src; the source window [src, src + min(d, ml)) is final, so the
+// lanes are independent.  Loads are batched ahead of the stores.
+__device__ __forceinline__ void warp_copy(uint8_t* g, uint64_t dst, uint64_t src, uint32_t ml, int lane) {
     const uint64_t d = dst - src;
-    if (d < ml && d <= kPiece) {
-        // short period: stage it once and repeat it
-        const uint32_t dd = (uint32_t)d;
-        const uint32_t off = stage_bytes(g, total, src, dd, buf);
-        const uint8_t* b8 = reinterpret_cast<const uint8_t*>(buf);
-        uint32_t r = 0;
-        for (uint32_t q = 0; q < ml; q++) {
-            g[dst + q] = b8[off + r];
-            if (++r == dd) r = 0;
+    if (d >= ml) {
+        for (uint32_t k0 = 0; k0 < ml; k0 += 32 * kCopyUnroll) {
+            uint8_t v[kCopyUnroll];
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; u++) {
+                const uint32_t k = k0 + 32 * u + lane;
+                v[u] = k < ml ? __ldcg(g + src + k) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; u++) {
+                const uint32_t k = k0 + 32 * u + lane;
+                if (k < ml) g[dst + k] = v[u];
+            }
         }
-        return;
-    }
-    // no overlap, or a period longer than a piece: piece by piece; bytes at or
-    // past d come from the destination written by earlier pieces
-    for (uint32_t q0 = 0; q0 < ml; q0 += kPiece) {
-        const uint32_t n = min(kPiece, ml - q0);
-        const uint64_t s = q0 < d ? src + q0 : dst + q0 - d;
-        if (q0 < d && q0 + n > d) {
-            // the piece straddles the end of the first period: split it
-            const uint32_t n1 = (uint32_t)(d - q0);
-            uint32_t off = stage_bytes(g, total, s, n1, buf);
-            emit_bytes(g, dst + q0, n1, buf, off);
-            off = stage_bytes(g, total, dst, n - n1, buf);
-            emit_bytes(g, dst + q0 + n1, n - n1, buf, off);
-        } else {
-            const uint32_t off = stage_bytes(g, total, s, n, buf);
-            emit_bytes(g, dst + q0, n, buf, off);
+    } else {
+        const uint32_t dd = (uint32_t)d;
+        const uint32_t step = 32 % dd;
+        uint32_t r = lane % dd;
+        for (uint32_t k0 = 0; k0 < ml; k0 += 32 * kCopyUnroll) {
+            uint8_t v[kCopyUnroll];
+            uint32_t rr = r;
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; u++) {
+                const uint32_t k = k0 + 32 * u + lane;
+                v[u] = k < ml ? __ldcg(g + src + rr) : 0;
+                rr += step;
+                if (rr >= dd) rr -= dd;
+            }
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; u++) {
+                const uint32_t k = k0 + 32 * u + lane;
+                if (k < ml) g[dst + k] = v[u];
+            }
+            r = rr;
         }
     }
 }
@@ -529,9 +512,9 @@ __device__ void span_copy(uint8_t* g, uint64_t total, uint64_t dst, uint64_t src
 // out in ascending destination order, so the lowest unfinished span always
 // has every source final: the waits cannot deadlock, and a slow span delays
 // only the spans that really read its bytes (no head-of-line blocking).
+// Readiness is checked per lane; the ready spans are then copied one after
+// another by the whole warp.
 __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
-    __shared__ uint32_t stage[kExtThreads][kStageWords + 1];
-    uint32_t* buf = stage[threadIdx.x];
     const int lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1;
     const uint64_t deadline = gtimer() + job.timeout_ns;
@@ -542,7 +525,7 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
     ArcJob J = load_arc(job, 0);
     // lane state (a lane keeps its span's archive: batched jobs mix archives)
     bool has = false;
-    uint64_t src = 0, dst = 0, l_total = 0;
+    uint64_t src = 0, dst = 0;
     uint32_t ml = 0, o = 0, span_blk = 0;
     uint32_t* pm = nullptr;
     uint8_t* l_out = nullptr;
@@ -578,7 +561,6 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
                 span_blk = blk;
                 pm = J.pmap + (uint64_t)blk * (kBlock / 32);
                 l_out = J.out;
-                l_total = J.total;
                 l_npend = J.npend;
                 l_pmap = J.pmap;
                 has = true;
@@ -587,20 +569,30 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             idle = __ballot_sync(ACX_FULL, !has);
         }
         if (!__any_sync(ACX_FULL, has)) break;
-        bool progressed = false;
+        bool ready = false;
         if (has) {
             const uint64_t d = dst - src;
-            const uint64_t se = src + (d < ml ? d : ml);  // periodic source window
-            if (src_final(l_npend, l_pmap, src, se)) {
-                span_copy(l_out, l_total, dst, src, ml, buf);
+            ready = src_final(l_npend, l_pmap, src, src + (d < ml ? d : ml));  // periodic source window
+        }
+        uint32_t rmask = __ballot_sync(ACX_FULL, ready);
+        if (rmask) {
+            spins = 0;
+            const uint32_t done = rmask;
+            while (rmask) {
+                const int l = __ffs(rmask) - 1;
+                rmask &= rmask - 1;
+                const uint64_t s_src = __shfl_sync(ACX_FULL, src, l);
+                const uint64_t s_dst = __shfl_sync(ACX_FULL, dst, l);
+                const uint32_t s_ml = __shfl_sync(ACX_FULL, ml, l);
+                uint8_t* s_out = reinterpret_cast<uint8_t*>(__shfl_sync(ACX_FULL, reinterpret_cast<uint64_t>(l_out), l));
+                warp_copy(s_out, s_dst, s_src, s_ml, lane);
+            }
+            __threadfence();  // every lane's copies are visible before any bit is cleared
+            if (done >> lane & 1) {
                 for (uint32_t w = o >> 5; w <= ((o + ml - 1) >> 5); w++)
                     red_and_release(pm + w, ~range_mask(w, o, o + ml));
                 has = false;
-                progressed = true;
             }
-        }
-        if (__any_sync(ACX_FULL, progressed)) {
-            spins = 0;
         } else {
             __nanosleep(64);
             // (the decision must be warp-uniform: every lane leaves together)
