@@ -30,6 +30,7 @@ struct RansSmem {
     uint32_t tab[4][kM];                     // 64 KiB
     uint16_t ring[kRansWarps][kRingWords];   // 32 KiB
     uint64_t bar[kRansWarps][kSlots];
+    uint64_t sbar[kRansWarps];               // short-stream staging barrier of each warp
     int arc;                                 // archive whose tables are loaded
     int next_arc;
 };
@@ -86,7 +87,49 @@ __device__ bool rans_stream(const uint32_t* __restrict__ tab, const uint8_t* __r
     const uint32_t lt_mask = (1u << lane) - 1;
     uint32_t p = 0;
     const uint32_t steps = ok ? (n + K - 1) / K : 0;
-    for (uint32_t t0 = 0; t0 < steps; t0 += kStepGroup) {
+    uint32_t t0 = 0;
+    if (K == 32 * S) {
+        // Fast path: whole groups of full steps (every lane valid), with
+        // immediate store offsets and the ring position kept in one register.
+        const uint32_t full_groups = ok ? (n / K) / kStepGroup : 0;
+        uint8_t* op = out + lane;
+        for (uint32_t g = 0; g < full_groups; g++, t0 += kStepGroup) {
+            while (ready < nchunks && ready * kChunkWords < p + kStepGroup * 32 * S) {
+                if (!wait_chunk(bar, seq0 + ready, deadline)) { ok = false; break; }
+                ready++;
+            }
+            if (!ok) break;
+            if (issued < nchunks && 256 * (issued + 1) <= p + 256 * kSlots) {
+                __syncwarp();
+                do {
+                    issue_chunk(ring, bar, words, seq0 + issued, issued, wbytes, lane);
+                    issued++;
+                } while (issued < nchunks && 256 * (issued + 1) <= p + 256 * kSlots);
+            }
+            uint8_t* og = op + t0 * (32 * S);
+            uint32_t rp = rbase + p;
+#pragma unroll
+            for (int u = 0; u < kStepGroup; u++) {
+#pragma unroll
+                for (int s = 0; s < S; s++) {
+                    const uint32_t e = tab[x[s] & (kM - 1)];
+                    og[(u * S + s) * 32] = (uint8_t)e;
+                    const uint32_t q = x[s] >> kProbBits;
+                    x[s] = ((e >> 8) & 0xfffu) * q + q + (e >> 20);
+                }
+#pragma unroll
+                for (int s = 0; s < S; s++) {
+                    const bool need = x[s] < kL;
+                    const uint32_t b = __ballot_sync(ACX_FULL, need);
+                    if (need) x[s] = (x[s] << 16) | ring[(rp + __popc(b & lt_mask)) & (kRingWords - 1)];
+                    rp += __popc(b);
+                }
+            }
+            p = rp - rbase;
+            if (p > W) { ok = false; break; }
+        }
+    }
+    for (; t0 < steps; t0 += kStepGroup) {
         // the next kStepGroup steps read at most kStepGroup * 32 * S words from p on
         while (ready < nchunks && ready * kChunkWords < p + kStepGroup * 32 * S) {
             if (!wait_chunk(bar, seq0 + ready, deadline)) { ok = false; break; }
@@ -140,6 +183,93 @@ __device__ bool rans_stream(const uint32_t* __restrict__ tab, const uint8_t* __r
     return __all_sync(ACX_FULL, ok && fin);
 }
 
+// The short streams of a block (cmd, len, off) decoded concurrently by one
+// warp: stream g runs on lanes [lo_g, lo_g + K_g) with its own word pointer;
+// their words are staged whole into the warp's ring by TMA.  Returns 0 on
+// success, 1 when the layout does not fit (caller decodes them one by one),
+// -1 on a format violation or an expired wait.
+__device__ int rans_short3(const uint32_t* __restrict__ tab, const BlockDev& bd, const uint8_t* pay, uint8_t* scr,
+                           uint16_t* ring, uint64_t* sbar, uint32_t& sphase, int lane, uint64_t deadline) {
+    uint32_t lo[3], K[3], W[3], hdr[3], roff[3], nw_bytes[3];
+    uint32_t lanes = 0, bytes = 0;
+    for (int g = 0; g < 3; g++) {
+        K[g] = 0;
+        if (!bd.s_raw[g] || !(bd.rans_mask & (1u << g))) continue;
+        K[g] = bd.s_K[g];
+        if (K[g] > 32) return 1;
+        hdr[g] = (4 * K[g] + 15) & ~15u;
+        const uint32_t enc = bd.s_enc[g];
+        if (enc < hdr[g] || ((enc - hdr[g]) & 1)) return -1;
+        W[g] = (enc - hdr[g]) >> 1;
+        nw_bytes[g] = (2 * W[g] + 15) & ~15u;
+        lo[g] = lanes;
+        lanes += K[g];
+        roff[g] = bytes;
+        bytes += nw_bytes[g];
+    }
+    if (lanes > 32 || bytes > 2 * kRingWords) return 1;
+    if (lanes == 0) return 0;
+    // stage every short stream's words
+    __syncwarp();
+    if (lane == 0) {
+        mbar_arrive_tx(sbar, bytes);
+        for (int g = 0; g < 3; g++)
+            if (K[g] && nw_bytes[g])
+                tma_load_1d(reinterpret_cast<uint8_t*>(ring) + roff[g], pay + bd.s_body[g] + hdr[g], nw_bytes[g], sbar);
+    }
+    int my = -1;
+    for (int g = 0; g < 3; g++)
+        if (K[g] && lane >= (int)lo[g] && lane < (int)(lo[g] + K[g])) my = g;
+    uint32_t x = 0, n = 0, Kg = 1, Wg = 0, ro = 0, gmask = 0, steps = 0;
+    uint8_t* o = nullptr;
+    const uint32_t* tb = tab;
+    const uint32_t j = my >= 0 ? lane - lo[my] : 0;
+    bool ok = true;
+    for (int g = 0; g < 3; g++)
+        if (K[g]) steps = max(steps, (bd.s_raw[g] + K[g] - 1) / K[g]);
+    if (my >= 0) {
+        n = bd.s_raw[my];
+        Kg = K[my];
+        Wg = W[my];
+        ro = roff[my] / 2;
+        gmask = (Kg == 32 ? 0xffffffffu : ((1u << Kg) - 1)) << lo[my];
+        o = scr + bd.s_off[my];
+        tb = tab + my * kM;
+        x = *reinterpret_cast<const uint32_t*>(pay + bd.s_body[my] + 4 * j);
+        ok = x >= kL;
+    }
+    {
+        uint32_t spins = 0;
+        bool w = true;
+        while (!mbar_try_wait(sbar, sphase & 1))
+            if ((++spins & 1023) == 0 && gtimer() > deadline) { w = false; break; }
+        sphase++;
+        if (!__all_sync(ACX_FULL, w)) return -1;
+    }
+    ok = __all_sync(ACX_FULL, ok);
+    const uint32_t lt_mask = (1u << lane) - 1;
+    uint32_t p = 0;
+    for (uint32_t t = 0; t < steps && ok; t++) {
+        const uint32_t i = t * Kg + j;
+        bool need = false;
+        if (my >= 0 && i < n) {
+            const uint32_t e = tb[x & (kM - 1)];
+            o[i] = (uint8_t)e;
+            const uint32_t q = x >> kProbBits;
+            x = ((e >> 8) & 0xfffu) * q + q + (e >> 20);
+            need = x < kL;
+        }
+        const uint32_t b = __ballot_sync(ACX_FULL, need) & gmask;
+        if (need) x = (x << 16) | ring[ro + p + __popc(b & lt_mask)];
+        p += __popc(b);
+        if (p > Wg) ok = false;
+        if ((t & 7) == 7) ok = __all_sync(ACX_FULL, ok);
+    }
+    const bool fin = my < 0 || (p == Wg && x == kL);
+    __syncwarp();  // the ring is free again for the next stream's copies
+    return __all_sync(ACX_FULL, ok && fin) ? 0 : -1;
+}
+
 __device__ void copy_stored(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, uint32_t n, int lane) {
     const uint32_t nv = (n + 15) / 16;  // bodies and scratch streams are 16-aligned and padded
     const uint4* s = reinterpret_cast<const uint4*>(src);
@@ -161,6 +291,7 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
     RansSmem& S = *reinterpret_cast<RansSmem*>(smraw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane < kSlots) mbar_init(&S.bar[warp][lane], 1);
+    if (lane == kSlots) mbar_init(&S.sbar[warp], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (threadIdx.x == 0) {
         const uint64_t target = (uint64_t)blockIdx.x * job.n_items / gridDim.x;
@@ -169,7 +300,7 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
     }
     __syncthreads();
     const uint64_t deadline = gtimer() + job.timeout_ns;
-    uint32_t seq = 0;
+    uint32_t seq = 0, sphase = 0;
     uint32_t* tickets = job.counters + 3;
     for (;;) {
         const int a = S.next_arc;
@@ -194,7 +325,12 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
             uint8_t* scr = J.scratch + bd.scratch;
             bool ok = true;
             int fs = 0;
-            for (int s = 0; s < 4 && ok; s++) {
+            // the three short streams together when they fit one warp
+            const int sh = rans_short3(&S.tab[0][0], bd, pay, scr, &S.ring[warp][0], &S.sbar[warp], sphase, lane,
+                                       deadline);
+            if (sh < 0) ok = false;
+            for (int s = sh == 0 ? 0 : 0; s < 4 && ok; s++) {
+                if (sh == 0 && s < 3 && (bd.rans_mask & (1u << s))) continue;  // decoded above
                 fs = s;
                 const uint32_t n = bd.s_raw[s];
                 if (n == 0) continue;
