@@ -261,6 +261,7 @@ def main():
     clocks = ClockSampler(dev)
     clocks.start()
     ms_total, ms_ans, ms_asm, ms_ext = [], [], [], []
+    last_stats = {}
     t0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1)  # write 256 MiB > L2 between steps
@@ -271,6 +272,7 @@ def main():
         ms_ans.append(st["ms_ans"])
         ms_asm.append(st["ms_parse"])
         ms_ext.append(st["ms_copy"])
+        last_stats = st
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if dist["pg"]:
@@ -341,6 +343,8 @@ def main():
                        "ratio": round(size / len(arc), 4),
                        "l2": "256 MiB buffer written between steps; per-step CUDA events exclude it"},
             "stage_ms": {"ans": round(a_ms, 4), "local_parse_copy": round(s_ms, 4), "cross_block": round(x_ms, 4)},
+            "cross_block_stats": {"pending_spans": last_stats.get("pending_spans"),
+                                  "empty_polls": last_stats.get("wait_polls")},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                          "peak_kind": peak_kind,

@@ -69,6 +69,12 @@ typedef struct {
                             content (classic hash-chain choice); 0 (default): at the first
                             occurrence, which costs the same with absolute offsets and keeps
                             cross-block dependency chains short */
+    uint32_t max_depth;  /* cap on the chain depth of any byte (a match only reads bytes whose
+                            own chains are shorter); 0 = default 16, 0xFFFFFFFF = no cap.
+                            Paper, "Depth Does Not Govern Latency": a depth bound is an
+                            encode-time choice of matches */
+    int short_latest;    /* 1: short-range matches point at the latest copy (default 0: the
+                            oldest copy inside the short-range window) */
 } aceapex_enc_params;
 
 /* Decoder variants. */
@@ -91,6 +97,8 @@ typedef struct {
     double ms_copy;   /* cross-block pass: matches whose source chain leaves their block */
     uint64_t blocks;  /* blocks decoded */
     uint64_t bytes;   /* bytes written to the output */
+    uint64_t pending_spans;  /* matches left to the cross-block pass */
+    uint64_t wait_polls;     /* cross-block rounds after the first (the dependency depth met) */
 } aceapex_stats;
 
 typedef struct {

@@ -54,7 +54,7 @@ struct DevBuf {
     }
 };
 
-constexpr uint32_t kMaxCounters = 4096 + 2;
+constexpr uint32_t kMaxCounters = kCounterWords;
 
 }  // namespace
 
@@ -63,7 +63,7 @@ struct aceapex_ctx {
     aceapex_dec_params params{};
     std::string err;
     int n_sms = 0;
-    DevBuf streams, npend, pmap, spans, arcs, in_arc, out_buf;
+    DevBuf streams, npend, pmap, spans, lists, arcs, in_arc, out_buf;
     uint32_t* counters = nullptr;  // device
     int* d_err = nullptr;          // device
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -142,6 +142,7 @@ int aceapex_ctx_destroy(aceapex_ctx* c) {
     c->npend.release();
     c->pmap.release();
     c->spans.release();
+    c->lists.release();
     c->arcs.release();
     c->in_arc.release();
     c->out_buf.release();
@@ -163,7 +164,7 @@ int aceapex_ctx_set_params(aceapex_ctx* c, const aceapex_dec_params* p) {
 int aceapex_encode(const uint8_t* src, uint64_t n, const aceapex_enc_params* p, uint8_t** out, uint64_t* out_len) {
     aceapex_enc_params d{};
     if (p) d = *p;
-    return encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, d.latest_source, out, out_len);
+    return encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, d.latest_source, d.max_depth, d.short_latest, out, out_len);
 }
 
 void aceapex_free(void* p) { free(p); }
@@ -220,6 +221,15 @@ int aceapex_archive_check(const void* h_arc, uint64_t len, aceapex_archive_info*
     return ACEAPEX_OK;
 }
 
+// Diagnostics (not part of the documented ABI): copy the context's device
+// counter block (tickets, statistics, cross-block round trace) to host memory.
+int acx_debug_counters(aceapex_ctx* c, uint32_t* out, uint32_t n) {
+    if (!c || !out || n > kCounterWords) return ACEAPEX_E_ARG;
+    cudaSetDevice(c->device);
+    return cudaMemcpy(out, c->counters, n * sizeof(uint32_t), cudaMemcpyDeviceToHost) == cudaSuccess ? 0
+                                                                                                   : ACEAPEX_E_CUDA;
+}
+
 int aceapex_archive_get_info(const aceapex_archive* A, aceapex_archive_info* info) {
     if (!A || !info) return ACEAPEX_E_ARG;
     info->total_size = A->plan.total;
@@ -245,8 +255,10 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     if ((e = c->streams.ensure(P.scratch_bytes)) != cudaSuccess) return cuda_fail(c, e, "scratch allocation");
     if ((e = c->npend.ensure(nb * 4)) != cudaSuccess) return cuda_fail(c, e, "pending-count allocation");
     if ((e = c->pmap.ensure(nb * (kBlock / 8))) != cudaSuccess) return cuda_fail(c, e, "bitmap allocation");
-    if ((e = c->spans.ensure(std::max<uint64_t>(P.tokens, 1) * sizeof(SpanRec))) != cudaSuccess)
+    if ((e = c->spans.ensure(std::max<uint64_t>(P.span_slots, 1) * sizeof(SpanRec))) != cudaSuccess)
         return cuda_fail(c, e, "span allocation");
+    if ((e = c->lists.ensure(2 * std::max<uint64_t>(P.span_slots, 1) * sizeof(JobDev::ListEnt))) != cudaSuccess)
+        return cuda_fail(c, e, "work-list allocation");
     JobDev job{};
     ArcJob& J = job.one;
     J.arc = (const uint8_t*)d_arc;
@@ -271,6 +283,8 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     job.timeout_ns = (uint64_t)c->params.timeout_us * 1000ull;
     job.max_tok = P.max_tok;
     job.max_lenb = P.max_lenb;
+    job.lists[0] = (JobDev::ListEnt*)c->lists.p;
+    job.lists[1] = (JobDev::ListEnt*)c->lists.p + std::max<uint64_t>(P.span_slots, 1);
     if (P.n_blocks == 0) return ACEAPEX_OK;
     const size_t lsm = local_smem_bytes(P.max_tok, P.max_lenb);
     if (c->params.variant != ACEAPEX_VARIANT_PLAIN && lsm > 227 * 1024)
@@ -323,6 +337,10 @@ static void fill_stats(aceapex_ctx* c, const Plan& P, aceapex_stats* s) {
     s->ms_total = t;
     s->blocks = P.n_blocks;
     s->bytes = P.total;
+    uint32_t st[2] = {0, 0};
+    cudaMemcpy(st, c->counters + kStatPending, sizeof st, cudaMemcpyDeviceToHost);
+    s->pending_spans = st[0];
+    s->wait_polls = st[1];
 }
 
 extern "C" {

@@ -411,18 +411,18 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
                 const int any_prog = __syncthreads_or(progress);
                 if (!any_left || !any_prog) break;
             }
-            // ---- whatever is still unresolved becomes a pending span ----
+            // ---- whatever is still unresolved becomes pending pieces ----
             uint32_t cnt = 0;
-            for (uint32_t i = i0; i < i1; i++) cnt += tstat[i] != 0;
+            for (uint32_t i = i0; i < i1; i++)
+                if (tstat[i]) cnt += pieces_of(tml[i]);
             v3[0] = cnt; v3[1] = 0; v3[2] = 0;
             block_scan3(v3, tot3, scanbuf);
             npend = tot3[0];
             uint32_t k = v3[0];
             for (uint32_t i = i0; i < i1; i++) {
                 if (!tstat[i]) continue;
-                const uint64_t src = tsrc[i];
-                J.spans[bd.tok_base + k] = SpanRec{(uint32_t)src, (uint32_t)(src >> 32), (uint32_t)(tpos[i] + tll[i]), tml[i]};
-                k++;
+                const uint32_t o = tpos[i] + tll[i];
+                k += emit_pieces(J.spans + bd.span_base + k, o, tsrc[i], tml[i], B + o - tsrc[i]);
             }
         }
         __syncthreads();
@@ -435,21 +435,27 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
         const uint32_t nv = R / 16;
         for (uint32_t i = tid; i < nv; i += kLocThreads) reinterpret_cast<uint4*>(gout)[i] = reinterpret_cast<uint4*>(sout)[i];
         for (uint32_t x = 16 * nv + tid; x < R; x += kLocThreads) gout[x] = sout[x];
-        if (npend) {
-            uint32_t* gp = J.pmap + (uint64_t)b * (kBlock / 32);
-            for (uint32_t i = tid; i < kBlock / 32; i += kLocThreads) gp[i] = pend[i];
+        {
+            // the pending bitmap is written for every block (zero when nothing is
+            // pending), so readers need no second lookup
+            uint4* gp = reinterpret_cast<uint4*>(J.pmap + (uint64_t)b * (kBlock / 32));
+            const uint4* sp = reinterpret_cast<const uint4*>(pend);
+            for (uint32_t i = tid; i < kBlock / 128; i += kLocThreads) gp[i] = sp[i];
         }
-        if (tid == 0) J.npend[b] = npend;
+        if (tid == 0) {
+            J.npend[b] = npend;
+            if (npend) atomicAdd(&job.counters[kStatPending], npend);
+        }
         __syncthreads();
     }
 }
 
 // ---- cross-block pass --------------------------------------------------------------------
-// Are the bytes [s, e) (absolute) final?  Blocks without pending spans are
-// final after the local pass; otherwise the block's pending bitmap decides.
+// Are the bytes [s, e) (absolute) final?  The local pass writes every
+// block's pending-byte bitmap; a clear bit means a final byte.
 __device__ __forceinline__ bool src_final(const uint32_t* npend, const uint32_t* pmap, uint64_t s, uint64_t e) {
+    (void)npend;
     for (uint64_t a = s >> 14; a <= (e - 1) >> 14; a++) {
-        if (npend[a] == 0) continue;
         const uint64_t A = a << 14;
         const uint32_t lo = (uint32_t)((s > A ? s : A) - A);
         const uint32_t hi = (uint32_t)((e < A + kBlock ? e : A + kBlock) - A);
@@ -460,146 +466,250 @@ __device__ __forceinline__ bool src_final(const uint32_t* npend, const uint32_t*
     return true;
 }
 
-constexpr int kExtThreads = 128;
-constexpr int kCopyUnroll = 8;  // 256 bytes of loads in flight per lane-group before the stores
+constexpr int kExtThreads = 1024;  // one CTA per SM: grid barriers stay cheap
+constexpr uint64_t kRound0WaitNs = 4000;  // how long a round-0 lane waits for its sources
 
-// The whole warp copies one span: out[dst + k] = out[src + (k mod d)], d =
-// dst - src; the source window [src, src + min(d, ml)) is final, so the
-// lanes are independent.  Loads are batched ahead of the stores.
-__device__ __forceinline__ void warp_copy(uint8_t* g, uint64_t dst, uint64_t src, uint32_t ml, int lane) {
-    const uint64_t d = dst - src;
-    if (d >= ml) {
-        for (uint32_t k0 = 0; k0 < ml; k0 += 32 * kCopyUnroll) {
-            uint8_t v[kCopyUnroll];
-#pragma unroll
-            for (int u = 0; u < kCopyUnroll; u++) {
-                const uint32_t k = k0 + 32 * u + lane;
-                v[u] = k < ml ? __ldcg(g + src + k) : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < kCopyUnroll; u++) {
-                const uint32_t k = k0 + 32 * u + lane;
-                if (k < ml) g[dst + k] = v[u];
-            }
-        }
-    } else {
-        const uint32_t dd = (uint32_t)d;
-        const uint32_t step = 32 % dd;
-        uint32_t r = lane % dd;
-        for (uint32_t k0 = 0; k0 < ml; k0 += 32 * kCopyUnroll) {
-            uint8_t v[kCopyUnroll];
-            uint32_t rr = r;
-#pragma unroll
-            for (int u = 0; u < kCopyUnroll; u++) {
-                const uint32_t k = k0 + 32 * u + lane;
-                v[u] = k < ml ? __ldcg(g + src + rr) : 0;
-                rr += step;
-                if (rr >= dd) rr -= dd;
-            }
-#pragma unroll
-            for (int u = 0; u < kCopyUnroll; u++) {
-                const uint32_t k = k0 + 32 * u + lane;
-                if (k < ml) g[dst + k] = v[u];
-            }
-            r = rr;
-        }
-    }
+// Are the bytes a piece reads final?  (period 0: [src, src+len); otherwise the
+// residues phase.. of the period window [src, src+period), one or two ranges.)
+__device__ __forceinline__ bool piece_final(const uint32_t* npend, const uint32_t* pmap, uint64_t src,
+                                            uint32_t phase, uint32_t period, uint32_t len) {
+    if (period == 0) return src_final(npend, pmap, src, src + len);
+    if (len >= period) return src_final(npend, pmap, src, src + period);
+    if (phase + len <= period) return src_final(npend, pmap, src + phase, src + phase + len);
+    return src_final(npend, pmap, src + phase, src + period) &&
+           src_final(npend, pmap, src, src + (phase + len - period));
 }
 
-// Each lane holds at most one span.  Lanes without work take the next spans
-// of the warp's current block, in order; when the block is used up the warp
-// takes the next block from the global ticket.  Spans are therefore handed
-// out in ascending destination order, so the lowest unfinished span always
-// has every source final: the waits cannot deadlock, and a slow span delays
-// only the spans that really read its bytes (no head-of-line blocking).
-// Readiness is checked per lane; the ready spans are then copied one after
-// another by the whole warp.
-__global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1;
-    const uint64_t deadline = gtimer() + job.timeout_ns;
-    // warp-uniform queue state
-    uint32_t blk = 0, cnt = 0, next = 0, base = 0;
-    uint64_t B = 0;
-    bool exhausted = false;
-    ArcJob J = load_arc(job, 0);
-    // lane state (a lane keeps its span's archive: batched jobs mix archives)
-    bool has = false;
-    uint64_t src = 0, dst = 0;
-    uint32_t ml = 0, o = 0, span_blk = 0;
-    uint32_t* pm = nullptr;
-    uint8_t* l_out = nullptr;
-    const uint32_t* l_npend = nullptr;
-    const uint32_t* l_pmap = nullptr;
-    uint32_t spins = 0;
-    for (;;) {
-        // hand out spans to idle lanes, in lane order
-        uint32_t idle = __ballot_sync(ACX_FULL, !has);
-        while (idle && !exhausted) {
-            if (next >= cnt) {
-                uint32_t item = 0;
-                if (lane == 0) item = atomicAdd(&job.counters[2], 1u);
-                item = __shfl_sync(ACX_FULL, item, 0);
-                if (item >= job.n_items) { exhausted = true; break; }
-                const int a = find_arc(job, item);
-                J = load_arc(job, a);
-                blk = J.lo + (item - J.item_base);
-                cnt = J.npend[blk];
-                next = 0;
-                base = J.blk[blk].tok_base;
-                B = (uint64_t)blk * kBlock;
-                continue;
-            }
-            const uint32_t avail = cnt - next;
-            const uint32_t r = __popc(idle & lt_mask);
-            if (!has && (idle >> lane & 1) && r < avail) {
-                const SpanRec rec = J.spans[base + next + r];
-                src = (uint64_t)rec.x | ((uint64_t)rec.y << 32);
-                o = rec.z;
-                ml = rec.w;
-                dst = B + o;
-                span_blk = blk;
-                pm = J.pmap + (uint64_t)blk * (kBlock / 32);
-                l_out = J.out;
-                l_npend = J.npend;
-                l_pmap = J.pmap;
-                has = true;
-            }
-            next += min(avail, (uint32_t)__popc(idle));
-            idle = __ballot_sync(ACX_FULL, !has);
+// A warp's attempt at its lanes' pieces (lane `has` a piece `rec` of block
+// `blk`, all of archive L).  Each lane checks its own piece; the ready pieces
+// are then copied by the whole warp, lane i moving byte i (one coalesced
+// request per piece), eight pieces' loads in flight before their stores;
+// after one fence the owners clear the pieces' pending bits with release
+// reductions.  Returns true on the lanes whose piece is done.
+constexpr int kCopyBatch = 8;
+__device__ bool try_pieces(bool has, const ArcJob& L, uint32_t blk, SpanRec rec, SpanRec* wrec, uint64_t* wdst,
+                           int lane) {
+    const uint64_t src = (uint64_t)rec.x | ((uint64_t)(rec.y & 0xff) << 32);
+    const uint32_t phase = rec.y >> 8, period = rec.w, o = rec.z & 0xffff, len = rec.z >> 16;
+    const bool ready = has && piece_final(L.npend, L.pmap, src, phase, period, len);
+    const uint32_t rmask = __ballot_sync(ACX_FULL, ready);
+    if (!rmask) return false;
+    wrec[lane] = rec;
+    wdst[lane] = (uint64_t)blk * kBlock + o;
+    __syncwarp();
+    uint8_t* g = L.out;
+    uint32_t m = rmask;
+    while (m) {
+        int ls[kCopyBatch];
+#pragma unroll
+        for (int u = 0; u < kCopyBatch; u++) {
+            ls[u] = m ? __ffs(m) - 1 : -1;
+            if (m) m &= m - 1;
         }
-        if (!__any_sync(ACX_FULL, has)) break;
-        bool ready = false;
-        if (has) {
-            const uint64_t d = dst - src;
-            ready = src_final(l_npend, l_pmap, src, src + (d < ml ? d : ml));  // periodic source window
+        uint32_t v[(kCopyBatch + 3) / 4];
+#pragma unroll
+        for (int u = 0; u < (kCopyBatch + 3) / 4; u++) v[u] = 0;
+#pragma unroll
+        for (int u = 0; u < kCopyBatch; u++) {
+            if (ls[u] >= 0) {
+                const SpanRec r = wrec[ls[u]];
+                if ((uint32_t)lane < (r.z >> 16)) {
+                    const uint64_t rs = (uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32);
+                    const uint32_t rp = r.w;
+                    const uint64_t q = rp ? rs + ((r.y >> 8) + (uint32_t)lane) % rp : rs + lane;
+                    v[u >> 2] |= (uint32_t)__ldcg(g + q) << (8 * (u & 3));
+                }
+            }
         }
-        uint32_t rmask = __ballot_sync(ACX_FULL, ready);
-        if (rmask) {
-            spins = 0;
-            const uint32_t done = rmask;
-            while (rmask) {
-                const int l = __ffs(rmask) - 1;
-                rmask &= rmask - 1;
-                const uint64_t s_src = __shfl_sync(ACX_FULL, src, l);
-                const uint64_t s_dst = __shfl_sync(ACX_FULL, dst, l);
-                const uint32_t s_ml = __shfl_sync(ACX_FULL, ml, l);
-                uint8_t* s_out = reinterpret_cast<uint8_t*>(__shfl_sync(ACX_FULL, reinterpret_cast<uint64_t>(l_out), l));
-                warp_copy(s_out, s_dst, s_src, s_ml, lane);
+#pragma unroll
+        for (int u = 0; u < kCopyBatch; u++) {
+            if (ls[u] >= 0) {
+                const uint32_t rl = wrec[ls[u]].z >> 16;
+                if ((uint32_t)lane < rl) g[wdst[ls[u]] + lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
             }
-            __threadfence();  // every lane's copies are visible before any bit is cleared
-            if (done >> lane & 1) {
-                for (uint32_t w = o >> 5; w <= ((o + ml - 1) >> 5); w++)
-                    red_and_release(pm + w, ~range_mask(w, o, o + ml));
-                has = false;
-            }
+        }
+    }
+    __threadfence();  // every lane's stores are visible before any bit is cleared
+    if (ready) {
+        uint32_t* pm = L.pmap + (uint64_t)blk * (kBlock / 32);
+        for (uint32_t w = o >> 5; w <= ((o + len - 1) >> 5); w++) red_and_release(pm + w, ~range_mask(w, o, o + len));
+    }
+    __syncwarp();
+    return ready;
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident): bounded
+// wait; the last CTA to arrive clears the count `reset` before it releases
+// the others.  Returns false when the wait ran out.
+__device__ bool grid_barrier(uint32_t* counters, uint32_t reset, uint64_t deadline) {
+    __syncthreads();
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        ok_s = 1;
+        const uint32_t gen = ld_acquire_u32(counters + kBarGen);
+        __threadfence();
+        if (atomicAdd(counters + kBarCount, 1u) == gridDim.x - 1) {
+            counters[kBarCount] = 0;
+            counters[reset] = 0;
+            __threadfence();
+            atomicAdd(counters + kBarGen, 1u);
         } else {
-            __nanosleep(64);
-            // (the decision must be warp-uniform: every lane leaves together)
-            if ((++spins & 15) == 0 && __any_sync(ACX_FULL, gtimer() > deadline)) {
-                if (has) set_err(job.err, kErrTimeout, kStageWait << 24, span_blk);
-                break;
+            uint32_t spins = 0;
+            while (ld_acquire_u32(counters + kBarGen) == gen) {
+                __nanosleep(32);
+                if ((++spins & 255) == 0 && gtimer() > deadline) { ok_s = 0; break; }
             }
+        }
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Append the lanes' unfinished spans to a work list (warp-aggregated).
+typedef JobDev::ListEnt ListEnt;
+__device__ __forceinline__ void append(bool keep, ListEnt e, ListEnt* list, uint32_t* cnt, int lane) {
+    const uint32_t m = __ballot_sync(ACX_FULL, keep);
+    if (!m) return;
+    uint32_t base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(cnt, (uint32_t)__popc(m));
+    base = __shfl_sync(ACX_FULL, base, __ffs(m) - 1);
+    if (keep) list[base + __popc(m & ((1u << lane) - 1))] = e;
+}
+
+// Cross-block pass in rounds.  Round 0 walks every block's pending spans (in
+// ascending order); each later round walks the spans the previous round could
+// not finish.  A span is attempted once per round and never waited on, so
+// the pass needs no ordering argument: every round finishes at least the
+// lowest pending span (its sources are final), and the number of rounds is
+// the depth of the cross-block dependency chains.  Spans finished earlier in
+// the same round are visible to later ones.  Rounds are separated by a grid
+// barrier (cooperative launch).
+__global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
+    __shared__ SpanRec recs[kExtThreads];
+    __shared__ uint64_t dsts[kExtThreads];
+    SpanRec* wrec = recs + (threadIdx.x & ~31u);
+    uint64_t* wdst = dsts + (threadIdx.x & ~31u);
+    const int lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint64_t deadline = gtimer() + job.timeout_ns;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint64_t t = gtimer();
+        job.counters[kTrace] = 0;
+        job.counters[kTrace + 1] = (uint32_t)t;
+        job.counters[kTrace + 2] = (uint32_t)(t >> 32);
+    }
+    // round 0: pieces handed out in ascending order (the warp takes blocks from
+    // a ticket, its idle lanes take the block's next pieces); a lane waits a
+    // short while for sources that are about to be finished by lower pieces,
+    // then defers its piece to the rounds below.
+    {
+        uint32_t blk = 0, cnt = 0, next = 0, base = 0, item = 0;
+        int arc = 0;
+        bool exhausted = false;
+        ArcJob J = load_arc(job, 0);
+        bool has = false;
+        SpanRec rec{0, 0, 0, 0};
+        uint32_t l_blk = 0, l_slot = 0, l_item = 0;
+        int l_arc = 0;
+        uint64_t t0 = 0;
+        uint32_t spins = 0;
+        const uint32_t lt_mask = (1u << lane) - 1;
+        for (;;) {
+            uint32_t idle = __ballot_sync(ACX_FULL, !has);
+            while (idle && !exhausted) {
+                if (next >= cnt) {
+                    if (lane == 0) item = atomicAdd(&job.counters[2], 1u);
+                    item = __shfl_sync(ACX_FULL, item, 0);
+                    if (item >= job.n_items) { exhausted = true; break; }
+                    arc = find_arc(job, item);
+                    J = load_arc(job, arc);
+                    blk = J.lo + (item - J.item_base);
+                    cnt = J.npend[blk];
+                    next = 0;
+                    base = J.blk[blk].span_base;
+                    continue;
+                }
+                const uint32_t avail = cnt - next;
+                const uint32_t r = __popc(idle & lt_mask);
+                if ((idle >> lane & 1) && r < avail) {
+                    l_slot = base + next + r;
+                    rec = J.spans[l_slot];
+                    l_blk = blk;
+                    l_item = item;
+                    l_arc = arc;
+                    t0 = gtimer();
+                    has = true;
+                }
+                next += min(avail, (uint32_t)__popc(idle));
+                idle = __ballot_sync(ACX_FULL, !has);
+            }
+            if (!__any_sync(ACX_FULL, has)) break;
+            // attempt the held pieces, one archive at a time
+            bool progressed = false;
+            uint32_t todo = __ballot_sync(ACX_FULL, has);
+            while (todo) {
+                const int a0 = __shfl_sync(ACX_FULL, l_arc, __ffs(todo) - 1);
+                const bool mine = has && l_arc == a0;
+                const bool done = try_pieces(mine, load_arc(job, a0), l_blk, rec, wrec, wdst, lane);
+                if (done) { has = false; progressed = true; }
+                todo &= ~__ballot_sync(ACX_FULL, mine);
+            }
+            // give up on pieces that waited too long: the rounds finish them
+            const bool giveup = has && gtimer() - t0 > kRound0WaitNs;
+            append(giveup, ListEnt{l_slot, l_item}, job.lists[0], &job.counters[kListCnt], lane);
+            if (giveup) has = false;
+            if (__any_sync(ACX_FULL, progressed || giveup)) {
+                spins = 0;
+            } else {
+                __nanosleep(64);
+                if ((++spins & 255) == 0 && __any_sync(ACX_FULL, gtimer() > deadline)) {
+                    if (lane == 0) set_err(job.err, kErrTimeout, kStageWait << 24, l_blk);
+                    break;
+                }
+            }
+        }
+    }
+    for (uint32_t round = 1;; round++) {
+        const uint32_t in = (round - 1) & 1, out = round & 1;
+        if (!grid_barrier(job.counters, kListCnt + out, deadline)) {
+            if (threadIdx.x == 0) set_err(job.err, kErrTimeout, kStageWait << 24, 0);
+            return;
+        }
+        const uint32_t n = *((volatile uint32_t*)&job.counters[kListCnt + in]);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && round < kTraceRounds) {
+            // round trace: work-list size and start time (ns) of every round
+            job.counters[kTrace + 3 * round] = n;
+            const uint64_t t = gtimer();
+            job.counters[kTrace + 3 * round + 1] = (uint32_t)t;
+            job.counters[kTrace + 3 * round + 2] = (uint32_t)(t >> 32);
+        }
+        if (n == 0) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&job.counters[kStatPolls], 1u);
+        if (round > (1u << 20)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) set_err(job.err, kErrTimeout, kStageWait << 24, 0);
+            return;
+        }
+        for (uint32_t i0 = gwarp * 32; i0 < n; i0 += nwarps * 32) {
+            const uint32_t i = i0 + lane;
+            const bool has = i < n;
+            ListEnt e{0, 0};
+            if (has) e = job.lists[in][i];
+            // (the lanes' pieces may come from several archives: one archive at a time)
+            const int arc_i = has ? find_arc(job, e.y) : -1;
+            bool done = false;
+            uint32_t todo = __ballot_sync(ACX_FULL, has);
+            while (todo) {
+                const int a0 = __shfl_sync(ACX_FULL, arc_i, __ffs(todo) - 1);
+                const bool mine = has && arc_i == a0;
+                const ArcJob J = load_arc(job, a0);
+                SpanRec r{0, 0, 0, 0};
+                if (mine) r = J.spans[e.x];
+                const bool d2 = try_pieces(mine, J, mine ? J.lo + (e.y - J.item_base) : 0, r, wrec, wdst, lane);
+                if (mine) done = d2;
+                todo &= ~__ballot_sync(ACX_FULL, mine);
+            }
+            append(has && !done, e, job.lists[out], &job.counters[kListCnt + out], lane);
         }
     }
 }
@@ -615,8 +725,9 @@ cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st) {
 }
 
 cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st) {
-    k_external<<<grid, kExtThreads, 0, st>>>(job);
-    return cudaGetLastError();
+    JobDev j = job;
+    void* args[] = {&j};
+    return cudaLaunchCooperativeKernel((const void*)k_external, dim3(grid), dim3(kExtThreads), args, 0, st);
 }
 
 int local_occupancy(size_t smem) {

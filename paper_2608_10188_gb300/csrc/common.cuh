@@ -101,4 +101,26 @@ __device__ __forceinline__ uint32_t range_mask(uint32_t w, uint32_t s, uint32_t 
     return m;
 }
 
+// Cut a pending match (destination offset o in its block, absolute source src,
+// length ml, distance d = destination - source) into pieces of at most kPiece
+// bytes at slots out[0..); returns the number of pieces.
+__device__ __forceinline__ uint32_t emit_pieces(SpanRec* out, uint32_t o, uint64_t src, uint32_t ml, uint64_t d) {
+    uint32_t k = 0;
+    for (uint32_t q = 0; q < ml; q += kPiece, k++) {
+        const uint32_t len = ml - q < kPiece ? ml - q : kPiece;
+        uint64_t s;
+        uint32_t phase = 0, period = 0;
+        if (d >= ml) {
+            s = src + q;
+        } else {
+            s = src;
+            period = (uint32_t)d;
+            phase = q % period;
+        }
+        out[k] = SpanRec{(uint32_t)s, (uint32_t)(s >> 32) | (phase << 8), (o + q) | (len << 16), period};
+    }
+    return k;
+}
+__host__ __device__ inline uint32_t pieces_of(uint32_t ml) { return (ml + kPiece - 1) / kPiece; }
+
 }  // namespace acx

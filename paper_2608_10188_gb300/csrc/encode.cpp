@@ -9,7 +9,11 @@
 // Match search: a long-window hash (16 bytes, any distance) finds copies
 // anywhere earlier; by default it keeps the FIRST occurrence of a window, so a
 // copy of a copy points at the original bytes (with absolute offsets this
-// costs no offset bits, and it keeps cross-block dependency chains short); a short-window hash (6 bytes,
+// costs no offset bits, and it keeps cross-block dependency chains short);
+// the short-window hash likewise keeps the oldest occurrence inside its 4 MiB
+// window; every output byte's chain depth is tracked and a match whose
+// source bytes are already at the depth cap is not taken (paper, "Depth Does
+// Not Govern Latency": a depth bound is an encode-time choice, nearly free); a short-window hash (6 bytes,
 // recent positions) finds local repeats; the four history distances and
 // distances 1..4 are always tried.  A match is taken when its estimated
 // saving in bits (length x literal cost - token cost) is positive, which
@@ -36,6 +40,11 @@ uint64_t fnv1a64(const uint8_t* p, uint64_t n) {
 }
 
 namespace {
+
+// Default chain-depth cap.  At 16 it costs nothing measurable on the genome
+// and 0.02% on text, while bounding the dependency chains the cross-block
+// pass must follow.
+constexpr uint32_t kDefaultMaxDepth = 16;
 
 struct BlockStreams {
     std::vector<uint8_t> s[4];
@@ -136,11 +145,46 @@ struct Parser {
     uint64_t n;
     bool no_rep;
     bool oldest;         // long-window table keeps the first occurrence instead of the latest
+    bool short_oldest;   // short-window table keeps the oldest occurrence inside its window
+    uint32_t max_depth;  // chain-depth cap (0 = none)
     uint32_t min_match;
     double lit_bits;
     int lbits, sbits;
     std::vector<uint64_t> hl;  // 16-byte window -> most recent position + 1
-    std::vector<uint32_t> hs;  // 6-byte window  -> most recent position + 1 (low 32 bits)
+    std::vector<uint32_t> hs;  // 6-byte window  -> position + 1 (low 32 bits)
+    std::vector<uint8_t> depth;  // chain depth of every output byte (0 = literal), saturating
+    // every match emitted so far, in output order, and the index of each
+    // block's first match (for source forwarding)
+    struct Emitted {
+        uint64_t dst, src;
+        uint32_t len;
+    };
+    std::vector<Emitted> emitted;
+    std::vector<uint64_t> block_first;
+
+    // Follow a non-periodic source window [s, s + w) back through the
+    // non-periodic matches that produced it: their bytes equal their sources,
+    // so the window can be read at its root instead.  The output is the same;
+    // the decoder's cross-block dependency chains become short.
+    uint64_t forward(uint64_t s, uint32_t w) const {
+        for (int hop = 0; hop < 64; hop++) {
+            const uint64_t b = s / kBlock;
+            if (b + 1 >= block_first.size() && b >= block_first.size()) break;
+            const uint64_t lo = block_first[b];
+            const uint64_t hi = b + 1 < block_first.size() ? block_first[b + 1] : emitted.size();
+            // last match of the block starting at or before s
+            uint64_t a = lo, z = hi;
+            while (a < z) {
+                const uint64_t m = (a + z) / 2;
+                if (emitted[m].dst <= s) a = m + 1; else z = m;
+            }
+            if (a == lo) break;
+            const Emitted& M = emitted[a - 1];
+            if (s + w > M.dst + M.len || M.dst - M.src < M.len) break;  // not inside, or periodic
+            s = M.src + (s - M.dst);
+        }
+        return s;
+    }
 
     static inline uint32_t hash_long(const uint8_t* p, int bits) {
         const uint64_t a = load64(p), b = load64(p + 8);
@@ -155,7 +199,18 @@ struct Parser {
             uint64_t& slot = hl[hash_long(s + p, lbits)];
             if (!oldest || !slot) slot = p + 1;
         }
-        if (p + 8 <= n) hs[hash_short(s + p, sbits)] = (uint32_t)(p + 1);
+        if (p + 8 <= n) {
+            uint32_t& slot = hs[hash_short(s + p, sbits)];
+            if (!short_oldest || !slot || p - (slot - 1) >= kShortWindow) slot = (uint32_t)(p + 1);
+        }
+    }
+    static constexpr uint64_t kShortWindow = 1u << 22;
+    // deepest chain among the bytes a match would read (its periodic source window)
+    uint32_t window_depth(uint64_t pos, uint64_t d, uint32_t L) const {
+        const uint64_t w = d < L ? d : L;
+        uint32_t m = 0;
+        for (uint64_t k = 0; k < w; k++) m = m > depth[pos - d + k] ? m : depth[pos - d + k];
+        return m;
     }
     // cost in bits of a NEW token (cmd + two varints + absolute offset)
     double new_cost(uint64_t src) const {
@@ -165,6 +220,7 @@ struct Parser {
     }
 
     void parse_block(uint64_t B, uint64_t E, BlockStreams& out, uint64_t& ins) {
+        block_first.push_back(emitted.size());
         std::vector<uint8_t>& cmd = out.s[kCmd];
         std::vector<uint8_t>& len = out.s[kLen];
         std::vector<uint8_t>& lit = out.s[kLit];
@@ -175,7 +231,7 @@ struct Parser {
             while (ins < pos) insert(ins++);
             if (pos + 24 <= n) __builtin_prefetch(&hl[hash_long(s + pos + 8, lbits)]);
             const uint64_t limit = E - pos;
-            uint32_t bestL = 0;
+            uint32_t bestL = 0, bestDepth = 0;
             uint64_t bestD = 0;
             int bestRep = -1;
             double bestGain = 0.0;
@@ -191,7 +247,10 @@ struct Parser {
                 // archive keeps exactly the same matches
                 const double cost = ri >= 0 ? 14.0 : new_cost(pos - d);
                 const double gain = L * lit_bits - cost;
-                if (gain > bestGain) { bestGain = gain; bestL = L; bestD = d; bestRep = ri; }
+                if (gain <= bestGain) return;
+                const uint32_t sd = window_depth(pos, d, L);
+                if (max_depth && sd + 1 > max_depth) return;  // would exceed the chain-depth cap
+                bestGain = gain; bestL = L; bestD = d; bestRep = ri; bestDepth = sd + 1;
             };
             for (int j = 0; j < 4; j++) consider(hist[j], j);
             for (uint64_t d = 1; d <= 4; d++) consider(d, -1);
@@ -201,9 +260,26 @@ struct Parser {
             }
             if (pos + 8 <= n) {
                 const uint64_t q = hs[hash_short(s + pos, sbits)];
-                if (q && q - 1 < pos && pos - (q - 1) < (1u << 22)) consider(pos - (q - 1), -1);
+                if (q && q - 1 < pos && pos - (q - 1) < kShortWindow) consider(pos - (q - 1), -1);
             }
             if (!bestL) { pos++; continue; }
+            if (bestRep < 0 && bestD >= bestL) {
+                // an explicit offset: read the same bytes at their root (decided in
+                // history-mode terms, so both modes keep identical matches)
+                const uint64_t s0 = forward(pos - bestD, bestL);
+                if (s0 != pos - bestD) {
+                    const uint32_t sd = window_depth(pos, pos - s0, bestL);
+                    if (!max_depth || sd + 1 <= max_depth) {
+                        bestD = pos - s0;
+                        bestDepth = sd + 1;
+                        bestRep = -1;
+                        for (int j = 0; j < 4; j++)
+                            if (hist[j] == bestD) { bestRep = j; break; }
+                    }
+                }
+            }
+            memset(&depth[pos], bestDepth > 255 ? 255 : (int)bestDepth, bestL);
+            emitted.push_back({pos, pos - bestD, bestL});
             const uint32_t LL = (uint32_t)(pos - lit0);
             const bool rep_code = bestRep >= 0 && !no_rep;
             cmd.push_back(rep_code ? (uint8_t)(1 + bestRep) : kNew);
@@ -254,7 +330,7 @@ void parallel_for(uint32_t n, int threads, F fn) {
 }  // namespace
 
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   int latest, uint8_t** out, uint64_t* out_len) {
+                   int latest, uint32_t max_depth, int short_latest, uint8_t** out, uint64_t* out_len) {
     if (!out || !out_len || (n && !src)) return -1;
     if (min_match == 0) min_match = 4;
     if (max_lanes == 0) max_lanes = 32;
@@ -278,6 +354,9 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
         P.n = n;
         P.no_rep = no_rep != 0;
         P.oldest = latest == 0;
+        P.short_oldest = short_latest == 0;
+        P.max_depth = max_depth == 0 ? kDefaultMaxDepth : max_depth;
+        P.depth.assign(n, 0);
         P.min_match = min_match;
         P.lit_bits = std::max(H, 1.0) + 0.1;
         P.lbits = 16;

@@ -31,14 +31,21 @@ struct BlockDev {
     uint32_t s_enc[4];     // body length in bytes (without padding)
     uint32_t s_off[4];     // offset of each decoded stream inside the block's scratch region
     uint8_t s_K[4];        // rANS lanes
-    uint32_t tok_base;     // tokens of all earlier blocks (index of this block's pending-span slots)
+    uint32_t span_base;    // first pending-span slot of the block (n_tok + kSpanSlack slots per block)
     uint32_t pad[2];
 };
 static_assert(sizeof(BlockDev) % 16 == 0, "BlockDev alignment");
 
-// A pending span: match bytes whose source chain leaves their block, left for
-// the cross-block pass.  {x, y} = absolute source (lo, hi), z = destination
-// offset inside the block, w = match length.
+// A pending piece: at most kPiece bytes of a match whose source chain leaves
+// its block, left for the cross-block pass.  Long matches are cut into pieces
+// so every piece is one lane's small copy.
+//   x = source bits 0..31, y = source bits 32..39 | phase << 8,
+//   z = destination offset in the block | length << 16, w = period.
+// period 0: byte j comes from source + j; otherwise from
+// source + ((phase + j) mod period), source being the start of the match's
+// period window (the periodic fill of a self-overlapping match).
+constexpr uint32_t kPiece = 32;
+constexpr uint32_t kSpanSlack = kBlock / kPiece;  // pieces a block may add beyond one per token
 struct alignas(16) SpanRec {
     uint32_t x, y, z, w;
 };
@@ -52,7 +59,7 @@ struct ArcJob {
     uint8_t* out;             // output: block b at out + b*kBlock
     uint32_t* npend;          // per block: number of pending spans after the local pass
     uint32_t* pmap;           // per block pending-byte bitmap, 512 words (valid when npend > 0)
-    SpanRec* spans;           // pending spans, slots [tok_base, tok_base + n_tok) per block
+    SpanRec* spans;           // pending pieces, slots [span_base, span_base + n_tok + kSpanSlack) per block
     uint64_t total;           // decompressed size
     uint32_t n_blocks;
     uint32_t lo, hi;          // blocks [lo, hi) are decoded by this job
@@ -61,16 +68,31 @@ struct ArcJob {
     uint32_t pad;
 };
 
+constexpr uint32_t kMaxArcsPerJob = 4000;
+constexpr uint32_t kTrace = 3800;        // [kTrace + 3r]: cross-block round r list size, start time lo, hi
+constexpr uint32_t kTraceRounds = 64;
+constexpr uint32_t kListCnt = 4086;      // [kListCnt + 0/1]: entries of the two cross-block work lists
+constexpr uint32_t kBarCount = 4088;     // grid barrier arrivals
+constexpr uint32_t kBarGen = 4089;       // grid barrier generation
+constexpr uint32_t kStatPending = 4093;
+constexpr uint32_t kStatPolls = 4094;    // cross-block rounds
+constexpr uint32_t kCounterWords = 4096;
+
 struct JobDev {
     ArcJob one;               // the archive when arcs == nullptr
     const ArcJob* arcs;       // device array of archives (batched jobs), or nullptr
     uint32_t n_arcs;
     uint32_t n_items;         // total blocks over all archives
-    uint32_t* counters;       // [1] local ticket, [2] external ticket, [3 + a] rANS ticket of archive a
+    uint32_t* counters;       // [1] local ticket, [2] external ticket, [3 + a] rANS ticket of archive a,
+                              // [kStatPending] pending spans, [kStatPolls] empty cross-block polls
     int* err;                 // first error status (0 = ok)
     uint64_t timeout_ns;
     uint32_t max_tok;         // shared-memory sizing of the assembly kernel
     uint32_t max_lenb;
+    struct alignas(8) ListEnt {
+        uint32_t x, y;        // span slot, item
+    };
+    ListEnt* lists[2];        // cross-block work lists
 };
 
 }  // namespace acx

@@ -98,8 +98,7 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain(JobDev job) {
                     for (uint32_t j = 0; j < ML; j++) sout[o + j] = sout[src - B + j];
                 } else {
                     for (uint32_t w = o >> 5; w <= ((o + ML - 1) >> 5); w++) pend[w] |= range_mask(w, o, o + ML);
-                    J.spans[bd.tok_base + np] = SpanRec{(uint32_t)src, (uint32_t)(src >> 32), o, ML};
-                    np++;
+                    np += emit_pieces(J.spans + bd.span_base + np, o, src, ML, pos - src);
                 }
                 pos += ML;
             }
@@ -116,11 +115,14 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain(JobDev job) {
         const uint32_t R = bd.raw_len, nv = R / 16;
         for (uint32_t i = lane; i < nv; i += 32) reinterpret_cast<uint4*>(gout)[i] = reinterpret_cast<uint4*>(sout)[i];
         for (uint32_t x = 16 * nv + lane; x < R; x += 32) gout[x] = sout[x];
-        if (np) {
-            uint32_t* gp = J.pmap + (uint64_t)b * (kBlock / 32);
+        {
+            uint32_t* gp = J.pmap + (uint64_t)b * (kBlock / 32);  // written for every block
             for (uint32_t i = lane; i < kBlock / 32; i += 32) gp[i] = pend[i];
         }
-        if (lane == 0) J.npend[b] = np;
+        if (lane == 0) {
+            J.npend[b] = np;
+            if (np) atomicAdd(&job.counters[kStatPending], np);
+        }
         __syncwarp();
     }
 }

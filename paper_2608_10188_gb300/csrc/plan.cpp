@@ -120,12 +120,13 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why) {
         if (bd.s_raw[kOff] % 5) return fail("offset stream not a multiple of 5");
         bd.n_new = bd.s_raw[kOff] / 5;
         bd.scratch = scratch;
-        bd.tok_base = (uint32_t)P->tokens;
+        bd.span_base = (uint32_t)P->span_slots;
+        P->span_slots += n_tok + kSpanSlack;
         scratch += soff;
         if (n_tok > P->max_tok) P->max_tok = n_tok;
         if (bd.s_raw[kLen] > P->max_lenb) P->max_lenb = bd.s_raw[kLen];
         P->tokens += n_tok;
-        if (P->tokens >= (1ull << 32)) return fail("more than 2^32 tokens");
+        if (P->span_slots >= (1ull << 32)) return fail("too many tokens");
     }
     P->scratch_bytes = scratch + 64;
     return 0;

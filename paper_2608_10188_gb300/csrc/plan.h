@@ -10,7 +10,7 @@
 namespace acx {
 
 struct Plan {
-    uint64_t total = 0, archive_bytes = 0, tokens = 0, scratch_bytes = 0;
+    uint64_t total = 0, archive_bytes = 0, tokens = 0, scratch_bytes = 0, span_slots = 0;
     uint32_t n_blocks = 0, flags = 0, min_match = 0, max_tok = 0, max_lenb = 0;
     uint16_t freq[4][256];
     bool table_ok[4];
@@ -24,7 +24,7 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why);
 
 // Library encoder (format v1); out is malloc'ed.
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   int latest, uint8_t** out, uint64_t* out_len);
+                   int latest, uint32_t max_depth, int short_latest, uint8_t** out, uint64_t* out_len);
 
 // FNV-1a 64.
 uint64_t fnv1a64(const uint8_t* p, uint64_t n);

@@ -277,9 +277,16 @@ __device__ void copy_stored(const uint8_t* __restrict__ src, uint8_t* __restrict
     for (uint32_t i = lane; i < nv; i += 32) d[i] = s[i];
 }
 
-// Start of a decode call: every ticket restarts at zero.
+// Start of a decode call: every ticket and statistic restarts at zero.
 __global__ void k_prologue(uint32_t* counters, uint32_t n_counters) {
     for (uint32_t i = threadIdx.x; i < n_counters; i += blockDim.x) counters[i] = 0;
+    if (threadIdx.x == 0) {
+        counters[kStatPending] = 0;
+        counters[kStatPolls] = 0;
+        counters[kListCnt] = 0;
+        counters[kListCnt + 1] = 0;
+        counters[kBarCount] = 0;
+    }
 }
 
 // Each CTA works on one archive at a time (its tables in shared memory);

@@ -27,7 +27,8 @@ EXPORTED = [
 
 class EncParams(ctypes.Structure):
     _fields_ = [("no_rep", ctypes.c_int), ("min_match", ctypes.c_uint32), ("max_lanes", ctypes.c_uint32),
-                ("threads", ctypes.c_int), ("latest_source", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("latest_source", ctypes.c_int),
+                ("max_depth", ctypes.c_uint32), ("short_latest", ctypes.c_int)]
 
 
 class DecParams(ctypes.Structure):
@@ -37,7 +38,8 @@ class DecParams(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("ms_total", ctypes.c_double), ("ms_ans", ctypes.c_double), ("ms_parse", ctypes.c_double),
-                ("ms_copy", ctypes.c_double), ("blocks", ctypes.c_uint64), ("bytes", ctypes.c_uint64)]
+                ("ms_copy", ctypes.c_double), ("blocks", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
+                ("pending_spans", ctypes.c_uint64), ("wait_polls", ctypes.c_uint64)]
 
 
 class ArchiveInfo(ctypes.Structure):
@@ -100,13 +102,13 @@ def _check(rc, ctx=None, what=""):
 
 
 def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, threads: int = 0,
-           latest_source: bool = False) -> bytes:
+           latest_source: bool = False, max_depth: int = 0, short_latest: bool = False) -> bytes:
     """aceapex_encode on host bytes (numpy uint8 array or bytes)."""
     import numpy as np
     L = load()
     a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data,
                              dtype=np.uint8)
-    p = EncParams(int(no_rep), min_match, max_lanes, threads, int(latest_source))
+    p = EncParams(int(no_rep), min_match, max_lanes, threads, int(latest_source), max_depth, int(short_latest))
     ptr = ctypes.c_void_p()
     n = ctypes.c_uint64()
     _check(L.aceapex_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(p), ctypes.byref(ptr),
