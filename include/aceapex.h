@@ -173,6 +173,26 @@ int aceapex_sync(aceapex_ctx* ctx, void* stream);
 int aceapex_decode_host(aceapex_ctx* ctx, aceapex_archive* arc, const void* h_arc, uint64_t arc_len,
                         void* h_out, uint64_t out_cap, void* stream, aceapex_stats* stats);
 
+/*
+ * Decode without allocating anything (the paper has no counterpart: this is a
+ * service of this library).  For callers that cannot allocate device memory
+ * at decode time — code running while a CUDA graph is being captured,
+ * processes whose device memory belongs to a framework pool, latency-bound
+ * paths where an allocation may stall or fail.  It needs no context and no
+ * opened archive: d_arc (device pointer, arc_len bytes) is validated and
+ * planned on the device, and all scratch lives in one static device array of
+ * about 5.3 MiB that every device loading this library holds until the
+ * process exits.  Limits: at most 64 blocks (1 MiB of output), at most
+ * 2 MiB of decoded streams and 96K pending pieces; larger archives return
+ * ACEAPEX_E_ARG.  The output goes to d_out (device pointer, out_cap >= the
+ * decompressed size).  The call enqueues on `stream` and synchronises it;
+ * it returns the decode status.  The first call on a device looks up the
+ * array's device address (make that first call before any stream capture).
+ * Every call on a device shares the array: calls that overlap on the GPU
+ * (from other streams or threads) race and must be serialised by the caller.
+ */
+int aceapex_decode_noalloc(const void* d_arc, uint64_t arc_len, void* d_out, uint64_t out_cap, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,8 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("rans.cu", "assemble.cu", "plain.cu", "api.cpp", "plan.cpp", "encode.cpp")]
+    return [os.path.join(CSRC, f) for f in ("rans.cu", "assemble.cu", "plain.cu", "noalloc.cu", "api.cpp", "plan.cpp",
+                                          "encode.cpp")]
 
 
 def _deps():

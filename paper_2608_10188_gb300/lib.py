@@ -21,7 +21,7 @@ EXPORTED = [
     "aceapex_status_string", "aceapex_last_error", "aceapex_ctx_create", "aceapex_ctx_destroy",
     "aceapex_ctx_set_params", "aceapex_encode", "aceapex_free", "aceapex_archive_open", "aceapex_archive_close",
     "aceapex_archive_get_info", "aceapex_decode_all", "aceapex_decode_all_async", "aceapex_sync",
-    "aceapex_decode_host", "aceapex_archive_check",
+    "aceapex_decode_host", "aceapex_archive_check", "aceapex_decode_noalloc",
 ]
 
 
@@ -82,6 +82,7 @@ def load(path: str | None = None):
     L.aceapex_archive_close.argtypes = [vp]
     L.aceapex_archive_get_info.argtypes = [vp, c.POINTER(ArchiveInfo)]
     L.aceapex_archive_check.argtypes = [vp, u64, c.POINTER(ArchiveInfo)]
+    L.aceapex_decode_noalloc.argtypes = [vp, u64, vp, u64, vp]
     L.aceapex_decode_all.argtypes = [vp, vp, vp, u64, vp, c.POINTER(Stats)]
     L.aceapex_decode_all_async.argtypes = [vp, vp, vp, u64, vp]
     L.aceapex_sync.argtypes = [vp, vp]
@@ -217,3 +218,10 @@ def decode_host(ctx: Context, arc, h_arc, h_out, stream: int = 0, stats: bool = 
     if stats:
         return rc, {k: getattr(st, k) for k, _ in Stats._fields_}
     return rc
+
+
+def decode_noalloc(d_arc: int, arc_len: int, d_out: int, out_cap: int, stream: int = 0) -> int:
+    """aceapex_decode_noalloc: decode a small archive (<= 64 blocks) that is
+    already in device memory, using only the library's static scratch; for
+    callers that must not allocate.  Returns the status."""
+    return load().aceapex_decode_noalloc(d_arc, arc_len, d_out, out_cap, stream)
