@@ -13,7 +13,9 @@
  *                   streams (each sums to 4096, or is all zero)
  *   index    40 B per block: u64 payload_off, u32 payload_len, u32 n_tokens,
  *                   u32 raw_len, u32 dep_off, u32 n_deps, u32 0, u64 fnv1a64
- *   deps     optional u32 source-block ids (ascending, < own id)
+ *   deps     optional u32 source-block ids (ascending, < own id); when the
+ *            section is present, every block other than its own that a
+ *            match reads must be listed (else the archive is corrupt)
  *   payload  per block, 16-aligned: 4 descriptors of 12 B (u32 raw_len,
  *            u32 enc_len, u8 mode (0 stored, 1 rANS), u8 K, u16 0) in the
  *            order cmd, len, off, lit, then the 4 bodies, each starting on a
@@ -503,6 +505,7 @@ int orc_info(const uint8_t* arc, uint64_t arc_len, uint64_t* total, uint32_t* n_
 
 typedef struct {
     uint32_t raw_len, n_tok, payload_len;
+    uint32_t dep_off, n_deps; /* dependency list (archives that carry lists) */
     uint64_t payload_off, fnv;
     uint8_t* s[4];      /* decoded streams (malloc'ed) */
     uint32_t n[4];      /* their lengths */
@@ -522,6 +525,8 @@ static int block_streams(const arc_t* A, uint32_t b, dblk_t* d) {
     d->n_tok = rd32(e + 12);
     d->raw_len = rd32(e + 16);
     uint32_t dep_off = rd32(e + 20), n_deps = rd32(e + 24);
+    d->dep_off = dep_off;
+    d->n_deps = n_deps;
     d->fnv = rd64(e + 32);
     uint64_t B = (uint64_t)b * ORC_BLOCK;
     uint64_t R = A->total - B < ORC_BLOCK ? A->total - B : ORC_BLOCK;
@@ -578,6 +583,23 @@ typedef struct {
     uint64_t cap;
 } tok_out_t;
 
+/* Format v1 dependency lists: the match at pos reading from src reads the
+ * bytes [src, src + min(ML, pos - src)) (a self-overlapping match reads one
+ * period); every block of that window other than block b itself must appear
+ * in block b's list. */
+static int deps_cover(const arc_t* A, const dblk_t* d, uint32_t b, uint64_t src, uint64_t pos, uint32_t ML) {
+    uint64_t dist = pos - src;
+    uint64_t end = src + (dist < ML ? dist : ML);
+    for (uint64_t blk = src / ORC_BLOCK; blk <= (end - 1) / ORC_BLOCK; blk++) {
+        if (blk == b) continue;
+        int found = 0;
+        for (uint32_t k = 0; k < d->n_deps; k++)
+            if (rd32(A->a + A->off_deps + 4 * ((uint64_t)d->dep_off + k)) == blk) found = 1;
+        if (!found) return 0;
+    }
+    return 1;
+}
+
 static int block_decode(const arc_t* A, uint32_t b, const dblk_t* d, uint8_t* out, tok_out_t* T) {
     uint64_t B = (uint64_t)b * ORC_BLOCK, R = d->raw_len, E = B + R;
     const uint8_t* cmd = d->s[ORC_CMD];
@@ -633,6 +655,7 @@ static int block_decode(const arc_t* A, uint32_t b, const dblk_t* d, uint8_t* ou
         }
         if (k != 5) {
             if (ML < A->min_match || ML > E - pos) return ORC_E_CORRUPT;
+            if (A->off_deps && src < B && !deps_cover(A, d, b, src, pos, ML)) return ORC_E_CORRUPT;
             if (out) for (uint32_t j = 0; j < ML; j++) out[pos + j] = out[src + j]; /* byte-serial */
         }
         if (T && i < T->cap) {

@@ -44,11 +44,13 @@ def pad16(n: int) -> int:
 
 
 def build_archive(blocks, *, min_match=4, flags=0, expected=None, fnv=None, raw_streams=None,
-                  raw_lens=None, total=None, tables=None, encoded=None):
+                  raw_lens=None, total=None, tables=None, encoded=None, deps=None):
     """blocks: list of token lists.  raw_streams: optional {block: [cmd, len,
     off, lit]} overriding the streams derived from tokens.  encoded: optional
     {(block, stream): (mode, K, body)} to place an entropy-coded body.
-    expected: decoded bytes (for the per-block FNV via fnv).  Returns bytes."""
+    expected: decoded bytes (for the per-block FNV via fnv).  deps: optional
+    per-block lists of source-block ids (writes the dependency section).
+    Returns bytes."""
     nb = len(blocks)
     streams = [block_streams(t) for t in blocks]
     if raw_streams:
@@ -60,7 +62,17 @@ def build_archive(blocks, *, min_match=4, flags=0, expected=None, fnv=None, raw_
         total = sum(raw_lens)
     off_tables = 64
     off_index = 64 + 2048
-    off_payload = pad16(off_index + 40 * nb)
+    dep_ids, dep_pos = [], []
+    if deps is not None:
+        for lst in deps:
+            dep_pos.append((len(dep_ids), len(lst)))
+            dep_ids += list(lst)
+        off_deps = pad16(off_index + 40 * nb)
+        off_payload = pad16(off_deps + 4 * len(dep_ids))
+    else:
+        dep_pos = [(0, 0)] * nb
+        off_deps = 0
+        off_payload = pad16(off_index + 40 * nb)
     payload = bytearray()
     index = bytearray()
     for b in range(nb):
@@ -82,16 +94,20 @@ def build_archive(blocks, *, min_match=4, flags=0, expected=None, fnv=None, raw_
         h = 0
         if fnv is not None and expected is not None:
             h = fnv(expected[b * BLOCK: b * BLOCK + raw_lens[b]])
-        index += struct.pack("<QIIIIIIQ", off_payload + base, len(payload) - base, n_tok, raw_lens[b], 0, 0, 0, h)
+        index += struct.pack("<QIIIIIIQ", off_payload + base, len(payload) - base, n_tok, raw_lens[b],
+                             dep_pos[b][0], dep_pos[b][1], 0, h)
     hdr = bytearray(64)
     hdr[0:4] = b"ACX1"
     struct.pack_into("<HHIIQI", hdr, 4, 1, flags, BLOCK, min_match, total, nb)
-    struct.pack_into("<QQQQ", hdr, 32, off_tables, off_index, 0, off_payload)
+    struct.pack_into("<QQQQ", hdr, 32, off_tables, off_index, off_deps, off_payload)
     tab = bytearray(2048)
     if tables is not None:
         for s in range(4):
             for k in range(256):
                 struct.pack_into("<H", tab, 512 * s + 2 * k, int(tables[s][k]))
     arc = bytes(hdr) + bytes(tab) + bytes(index)
+    if deps is not None:
+        arc += b"\0" * (off_deps - len(arc))
+        arc += b"".join(struct.pack("<I", i) for i in dep_ids)
     arc += b"\0" * (off_payload - len(arc))
     return arc + bytes(payload)

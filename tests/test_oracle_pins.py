@@ -282,3 +282,56 @@ def test_truncation_and_bit_flips_never_crash(dna4m):
         assert rc in (0, oracle.E_CORRUPT, oracle.E_ARG)
         if rc == 0:
             assert np.array_equal(out, data)
+
+
+# ---- dependency lists -----------------------------------------------------------------
+
+def _three_blocks(src, ml):
+    """Blocks 0 and 1 are 16 KiB literal runs; block 2 (the short last block)
+    holds one NEW match reading `ml` bytes from absolute position `src`."""
+    rng = np.random.default_rng(21)
+    b0 = bytes(rng.integers(0, 256, 16384, dtype=np.uint8))
+    b1 = bytes(rng.integers(0, 256, 16384, dtype=np.uint8))
+    blocks = [[{"cmd": 5, "lits": b0, "ml": 0}], [{"cmd": 5, "lits": b1, "ml": 0}],
+              [{"cmd": 0, "lits": b"AB", "ml": ml, "src": src}]]
+    full = b0 + b1 + b"AB"
+    for j in range(ml):  # byte-serial definition of the copy
+        full += bytes([full[src + j]])
+    return blocks, full
+
+
+@pytest.mark.parametrize("src,ml,need", [
+    (100, 50, {0}),                 # reads block 0 only
+    (16384 - 10, 50, {0, 1}),       # the read window straddles blocks 0 and 1
+    (2 * 16384 - 4, 30, {1}),       # window runs into block 2 itself: only block 1 is listed
+])
+def test_dependency_lists_must_cover_every_block_read(src, ml, need):
+    """Format v1 reading of the paper's block dependencies (Setup: a block is
+    decodable once the blocks holding its sources exist): with a dependency
+    section present, every other block a match reads must be listed in the
+    reading block's list.  A list that covers the reads (or more) decodes to
+    the byte-serial definition; a list that misses one is corrupt."""
+    blocks, full = _three_blocks(src, ml)
+    ok = build_archive(blocks, deps=[[], [], sorted(need)])
+    assert oracle.decode(ok, verify=False).tobytes() == full
+    over = build_archive(blocks, deps=[[], [0], [0, 1]])
+    assert oracle.decode(over, verify=False).tobytes() == full
+    for drop in need:
+        short = build_archive(blocks, deps=[[], [], sorted(need - {drop})])
+        assert oracle.decode_status(short, verify=False)[0] == oracle.E_CORRUPT
+    # without a dependency section nothing is required
+    assert oracle.decode(build_archive(blocks), verify=False).tobytes() == full
+
+
+def test_self_overlap_reads_one_period_across_a_block_boundary():
+    """A self-overlapping match reads one period (paper, Periods, Not Chains):
+    at the start of block 1 with distance 6 it reads 4 bytes of block 0 and 2
+    of its own block, so only block 0 must be listed."""
+    rng = np.random.default_rng(3)
+    b0 = bytes(rng.integers(0, 256, 16384, dtype=np.uint8))
+    blocks = [[{"cmd": 5, "lits": b0, "ml": 0}], [{"cmd": 0, "lits": b"QR", "ml": 40, "src": 16384 - 4}]]
+    full = bytearray(b0 + b"QR")
+    for j in range(40):
+        full.append(full[16384 - 4 + j])
+    assert oracle.decode(build_archive(blocks, deps=[[], [0]]), verify=False).tobytes() == bytes(full)
+    assert oracle.decode_status(build_archive(blocks, deps=[[], []]), verify=False)[0] == oracle.E_CORRUPT
