@@ -45,6 +45,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="single", choices=["single", "batch"],
+                   help="single: one archive (--corpus); batch: the 96-archive mixed batch")
     p.add_argument("--corpus", default="dna", choices=["dna", "text"])
     p.add_argument("--size", type=int, default=0)
     p.add_argument("--encoding", default="history", choices=["history", "no_rep"])
@@ -52,6 +54,7 @@ def parse_args():
     p.add_argument("--lanes", type=int, default=32)
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-graph", action="store_true", help="batch: plain launches instead of a graph replay")
     p.add_argument("--cache-dir", default=os.environ.get("ACEAPEX_CACHE", "/tmp/aceapex_bench_cache"))
     return p.parse_args()
 
@@ -92,6 +95,46 @@ def get_archive(args, acx):
         except OSError:
             pass
     return data, arc
+
+
+def cached_encode(args, acx, data, key, **kw):
+    path = os.path.join(args.cache_dir, key)
+    if os.path.exists(path):
+        return open(path, "rb").read()
+    arc = acx.encode(data, **kw)
+    try:
+        os.makedirs(args.cache_dir, exist_ok=True)
+        tmp = path + f".{os.getpid()}.{threading.get_ident()}"
+        with open(tmp, "wb") as f:
+            f.write(arc)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return arc
+
+
+def batch_archives(args, acx):
+    """The mixed batch workload: 96 archives, sizes log-uniform in
+    [64 KiB, 64 MiB] (seed 4), archive i from seed 1000+i, DNA for even i and
+    text for odd i, history-free encoding for i mod 4 in {2, 3}.  Archives are
+    encoded in parallel (one encoder thread each)."""
+    from concurrent.futures import ThreadPoolExecutor
+    specs = synth.batch_specs()
+    ek = encoder_key()
+
+    def one(s):
+        data = synth.corpus(s["kind"], s["size"], s["seed"])
+        key = f"batch-{s['kind']}-{s['size']}-s{s['seed']}-{int(s['no_rep'])}-k{args.lanes}-{ek}.acx"
+        arc = cached_encode(args, acx, data, key, no_rep=s["no_rep"], max_lanes=args.lanes, threads=1)
+        return data, arc
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        res = list(ex.map(one, sorted(specs, key=lambda s: -s["size"])))
+    order = sorted(range(len(specs)), key=lambda i: -specs[i]["size"])
+    out = [None] * len(specs)
+    for k, i in enumerate(order):
+        out[i] = res[k]
+    return specs, out
 
 
 class ClockSampler:
@@ -203,6 +246,142 @@ def run_reference(args, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, dist):
+    """The mixed batch workload: 96 archives decoded by one graph-replayed
+    batch per step (aceapex_batch_run), against the same archives decoded by
+    one aceapex_decode_all_async per archive."""
+    import torch
+
+    import paper_2608_10188_gb300 as acx
+    acx.build.build()
+    dev = dist["local"]
+    torch.cuda.set_device(dev)
+    device = f"cuda:{dev}"
+    specs, pairs = batch_archives(args, acx)
+    variant = acx.lib.VARIANT_PLAIN if args.variant == "plain" else acx.lib.VARIANT_FAST
+    ctx = acx.Context(dev, variant=variant)
+    d_arcs, archives, outs = [], [], []
+    for data, arc in pairs:
+        h = np.frombuffer(arc, dtype=np.uint8).copy()
+        d = torch.from_numpy(h).to(device)
+        d_arcs.append(d)
+        A = acx.Archive(ctx, d.data_ptr(), h, h.size)
+        archives.append(A)
+        outs.append(torch.empty(max(A.total, 1), dtype=torch.uint8, device=device))
+    total = sum(A.total for A in archives)
+    arc_total = sum(len(a) for _, a in pairs)
+    entries = [(A, o.data_ptr(), A.total) for A, o in zip(archives, outs)]
+    graph = not args.no_graph
+    B = acx.Batch(ctx, entries, graph=graph)
+    flush = torch.empty(L2_FLUSH, dtype=torch.uint8, device=device)
+    sh = torch.cuda.current_stream().cuda_stream
+
+    def check(tag):
+        for (data, _), A, o in zip(pairs, archives, outs):
+            if not torch.equal(o[:A.total], torch.from_numpy(data).to(device)):
+                raise RuntimeError(f"{tag}: GPU decode differs from the input")
+
+    rc, per = B.run(sh)
+    if rc != 0 or any(per):
+        raise RuntimeError(f"batch decode failed: {rc} {per} {ctx.last_error()}")
+    check("batch")
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        B.run(sh)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ms = []
+    st = {}
+    for _ in range(args.steps):
+        flush.fill_(1)
+        rc, per, st = B.run(sh, stats=True)
+        if rc != 0:
+            raise RuntimeError(f"batch decode failed: {rc} {ctx.last_error()}")
+        ms.append(st["ms_total"])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = statistics.median(ms)
+    value = total / (ms_step / 1e3) / 1e9
+
+    # stage split from the same batch without a graph (events between the launches)
+    Bs = acx.Batch(ctx, entries, graph=False)
+    sa, sl, sx, sst = [], [], [], {}
+    for _ in range(max(3, min(args.steps, 5))):
+        flush.fill_(1)
+        rc, per, sst = Bs.run(sh, stats=True)
+        sa.append(sst["ms_ans"])
+        sl.append(sst["ms_parse"])
+        sx.append(sst["ms_copy"])
+    Bs.close()
+    pb = {"payload": 0, "decoded": 0}
+    for _, a in pairs:
+        q = stream_bytes(a)
+        pb["payload"] += q["payload"]
+        pb["decoded"] += q["decoded"]
+    n_blocks = sum(A.info["n_blocks"] for A in archives)
+    roof, path_roof = rooflines({"ans": statistics.median(sa), "local": statistics.median(sl),
+                                 "cross": statistics.median(sx)}, pb, total, arc_total, sst, n_blocks,
+                                args.variant, ms_step)
+
+    # the same archives, one decode launch sequence per archive
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per_ms = []
+    for it in range(args.warmup + max(3, min(args.steps, 10))):
+        flush.fill_(1)
+        e0.record()
+        for A, o in zip(archives, outs):
+            acx.decode_all_async(ctx, A, o.data_ptr(), A.total, sh)
+        e1.record()
+        if ctx.sync(sh) != 0:
+            raise RuntimeError(f"per-archive decode failed: {ctx.last_error()}")
+        if it >= args.warmup:
+            per_ms.append(e0.elapsed_time(e1))
+    check("per-archive")
+    per_gbs = total / (statistics.median(per_ms) / 1e3) / 1e9
+
+    cpu = None
+    if dist["rank"] == 0 and not args.no_cpu_baseline:
+        import oracle
+        small = sorted(range(len(specs)), key=lambda i: specs[i]["size"])[: len(specs) // 2]
+        t = time.perf_counter()
+        nb = 0
+        for i in small:
+            oracle.decode(pairs[i][1], verify=False)
+            nb += specs[i]["size"]
+        el = time.perf_counter() - t
+        cpu = {"value": round(nb / el / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"the {len(small)} smallest archives of the batch ({nb:,} B), single-threaded C oracle"}
+    if dist["rank"] == 0:
+        kinds = {k: sum(1 for s in specs if s["kind"] == k) for k in ("dna", "text")}
+        line = {
+            "metric": "device-resident decode GB/s", "value": round(value, 3), "unit": "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded generators)",
+            "config": {"workload": f"batch of {len(specs)} archives, {total:,} B (log-uniform 64 KiB-64 MiB; "
+                                   f"{kinds['dna']} DNA, {kinds['text']} text; history-free for i mod 4 in {{2,3}})",
+                       "launch": "one CUDA graph replay per step" if graph else "one launch sequence per step",
+                       "variant": args.variant, "rans_lanes": args.lanes, "blocks": n_blocks,
+                       "archive_bytes": arc_total, "ratio": round(total / arc_total, 4),
+                       "l2": "256 MiB buffer written between steps; per-step CUDA events exclude it"},
+            "per_archive_launches": {"value": round(per_gbs, 3), "unit": "GB/s",
+                                     "ms_per_step": round(statistics.median(per_ms), 4),
+                                     "launches_per_step": 4 * len(specs)},
+            "stage_ms": {"ans": round(statistics.median(sa), 4), "local_parse_copy": round(statistics.median(sl), 4),
+                         "cross_block": round(statistics.median(sx), 4)},
+            "cross_block_stats": {"pending_pieces": sst.get("pending_spans"), "pending_bytes": sst.get("pending_bytes"),
+                                  "rounds_after_first": sst.get("wait_polls")},
+            "roofline": roof, "path_roofline": path_roof, "e2e": None, "cpu_baseline": cpu,
+            "gpu_launches": 4 * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    B.close()
+    for A in archives:
+        A.close()
+    ctx.close()
+
+
 def init_dist(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -224,6 +403,9 @@ def main():
         run_reference(args, dist)
         if dist["pg"]:
             dist["pg"].barrier()
+        return
+    if args.workload == "batch":
+        run_batch(args, dist)
         return
     import torch
 
@@ -290,22 +472,11 @@ def main():
     ms_step = dev_ms / args.steps
 
     # roofline of the dominant kernel and of the whole path
-    peak, peak_kind = measured_peaks()
-    plan_bytes = stream_bytes(arc)
     a_ms = statistics.mean(ms_ans)
     s_ms = statistics.mean(ms_asm)
     x_ms = statistics.mean(ms_ext)
-    # algorithmic bytes per launch: k_rans reads the block payloads and writes
-    # the decoded streams; k_local reads the decoded streams and writes the
-    # output; k_external reads and writes the cross-block match bytes
-    k_rans_bytes = plan_bytes["payload"] + plan_bytes["decoded"]
-    k_loc_bytes = plan_bytes["decoded"] + size
-    dom, dom_ms, dom_bytes = max([("k_rans", a_ms, k_rans_bytes),
-                                  ("k_plain" if args.variant == "plain" else "k_local", s_ms, k_loc_bytes),
-                                  ("k_external", x_ms, 0)], key=lambda t: t[1])
-    achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_bytes else 0.0
-    path_bytes = len(arc) + size
-    path_gbs = path_bytes / (ms_step / 1e3) / 1e9
+    roof, path_roof = rooflines({"ans": a_ms, "local": s_ms, "cross": x_ms}, stream_bytes(arc), size, len(arc),
+                                last_stats, info["n_blocks"], args.variant, ms_step)
 
     # end to end through the C ABI from pinned host memory
     e2e = None
@@ -343,14 +514,11 @@ def main():
                        "ratio": round(size / len(arc), 4),
                        "l2": "256 MiB buffer written between steps; per-step CUDA events exclude it"},
             "stage_ms": {"ans": round(a_ms, 4), "local_parse_copy": round(s_ms, 4), "cross_block": round(x_ms, 4)},
-            "cross_block_stats": {"pending_spans": last_stats.get("pending_spans"),
-                                  "empty_polls": last_stats.get("wait_polls")},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                         "peak_kind": peak_kind,
-                         "algorithmic_bytes": int(dom_bytes)},
-            "path_roofline": {"bytes": path_bytes, "achieved": round(path_gbs, 1), "peak": peak,
-                              "frac": round(path_gbs / peak, 4), "frac_nominal_8tbs": round(path_gbs / 8000, 4)},
+            "cross_block_stats": {"pending_pieces": last_stats.get("pending_spans"),
+                                  "pending_bytes": last_stats.get("pending_bytes"),
+                                  "rounds_after_first": last_stats.get("wait_polls")},
+            "roofline": roof,
+            "path_roofline": path_roof,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": 4 * args.steps,
@@ -363,6 +531,45 @@ def main():
     if dist["pg"]:
         dist["pg"].barrier()
         dist["pg"].destroy_process_group()
+
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel, keyed by (workload, kernel); None until a capture of the current
+# kernel exists
+TRAFFIC = {}
+
+
+def rooflines(stage, pb, size, arc_len, st, n_blocks, variant, ms_step):
+    """HBM roofline of each decode kernel from its algorithmic bytes per launch
+    over its CUDA-event time, the dominant (slowest) kernel first, and of the
+    whole path (archive bytes read + output bytes written over the step)."""
+    peak, peak_kind = measured_peaks()
+    pend_b = int(st.get("pending_bytes") or 0)
+    pend_n = int(st.get("pending_spans") or 0)
+    local = "k_plain" if variant == "plain" else "k_local"
+    kern = {
+        # payload read + decoded streams written
+        "k_rans": (stage["ans"], pb["payload"] + pb["decoded"]),
+        # decoded streams read + output written
+        local: (stage["local"], pb["decoded"] + size),
+        # source bytes read + destination bytes written + 16 B per piece record
+        # + 4 B pending count per block
+        "k_external": (stage["cross"], 2 * pend_b + 16 * pend_n + 4 * n_blocks),
+    }
+    per = {k: {"ms": round(ms, 4), "algorithmic_bytes": int(b),
+               "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1) if ms > 0 else None,
+               "frac": round(b / (ms / 1e3) / 1e9 / peak, 4) if ms > 0 else None} for k, (ms, b) in kern.items()}
+    dom = max(kern, key=lambda k: kern[k][0])
+    ms, b = kern[dom]
+    achieved = b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(dom), "peak_kind": peak_kind + " hbm_gbs",
+            "algorithmic_bytes": int(b), "kernels": per}
+    path_bytes = arc_len + size
+    path_gbs = path_bytes / (ms_step / 1e3) / 1e9
+    path = {"bytes": path_bytes, "achieved": round(path_gbs, 1), "peak": peak, "frac": round(path_gbs / peak, 4),
+            "frac_nominal_8tbs": round(path_gbs / 8000, 4)}
+    return roof, path
 
 
 def stream_bytes(arc: bytes) -> dict:

@@ -75,6 +75,10 @@ typedef struct {
                             encode-time choice of matches */
     int short_latest;    /* 1: short-range matches point at the latest copy (default 0: the
                             oldest copy inside the short-range window) */
+    int deps;            /* 1: write each block's dependency list (the earlier blocks its matches
+                            read), so range decodes touch only a block's dependency closure
+                            (paper, Random Access at Scale); 0 (default): no lists, a range
+                            decode then covers every block up to the range */
 } aceapex_enc_params;
 
 /* Decoder variants. */
@@ -84,8 +88,8 @@ typedef struct {
 typedef struct {
     uint32_t variant;     /* ACEAPEX_VARIANT_* */
     uint32_t timeout_us;  /* limit of every device-side dependency wait (default 2,000,000) */
-    uint32_t ctas_per_sm; /* persistent CTAs per SM for the assembly kernel (0 = occupancy maximum) */
-    uint32_t reserved;
+    uint32_t ctas_per_sm; /* persistent CTAs per SM for the local pass (0 = occupancy maximum) */
+    uint32_t rans_ctas_per_sm; /* persistent CTAs per SM for the entropy stage (0 = occupancy maximum) */
 } aceapex_dec_params;
 
 /* Timing of the last call, measured with CUDA events on the call's stream
@@ -99,6 +103,7 @@ typedef struct {
     uint64_t bytes;   /* bytes written to the output */
     uint64_t pending_spans;  /* matches left to the cross-block pass */
     uint64_t wait_polls;     /* cross-block rounds after the first (the dependency depth met) */
+    uint64_t pending_bytes;  /* bytes of the matches left to the cross-block pass */
 } aceapex_stats;
 
 typedef struct {
@@ -164,6 +169,21 @@ int aceapex_decode_all_async(aceapex_ctx* ctx, aceapex_archive* arc, void* d_out
 int aceapex_sync(aceapex_ctx* ctx, void* stream);
 
 /*
+ * Decode the original bytes [start, start + len) into d_out (device pointer,
+ * len bytes).  Paper, Random Access at Scale: only the blocks the region
+ * covers and their block-dependency closure (the earlier blocks their
+ * matches read, transitively) are decoded — through the archive's dependency
+ * lists when it has them (aceapex_enc_params.deps), else every block up to
+ * the region's last — into context scratch, and the region is gathered out.
+ * A source outside its block's dependency list is ACEAPEX_E_CORRUPT.
+ * Returns ACEAPEX_E_RANGE when the region leaves the archive.  Synchronises
+ * `stream`; stats (may be NULL): blocks = closure size, bytes = len, ms_copy
+ * includes the gather.
+ */
+int aceapex_decode_range(aceapex_ctx* ctx, aceapex_archive* arc, uint64_t start, uint64_t len, void* d_out,
+                         void* stream, aceapex_stats* stats);
+
+/*
  * End-to-end decode from host memory: copies the archive (host pointer
  * h_arc, arc_len bytes, ideally pinned) to the device, decodes it, and copies
  * the output to h_out (host pointer, out_cap >= total size).  Device buffers
@@ -172,6 +192,52 @@ int aceapex_sync(aceapex_ctx* ctx, void* stream);
  */
 int aceapex_decode_host(aceapex_ctx* ctx, aceapex_archive* arc, const void* h_arc, uint64_t arc_len,
                         void* h_out, uint64_t out_cap, void* stream, aceapex_stats* stats);
+
+/*
+ * Batched decode: many archives decoded by one set of launches.  Paper,
+ * Setup (Table 1): a persistent queue over blocks, whose time follows the
+ * token count rather than the number of archives.  Here the kernels take
+ * (archive, block) items from shared device tickets, so archives of any
+ * size and encoding (history-bound or history-free) share the GPU.
+ *
+ * One item per archive: `arc` an archive opened on the batch's context (its
+ * device bytes must stay valid while the batch exists), `d_out` a device
+ * pointer with out_cap >= the archive's total size; `status` is written by
+ * aceapex_batch_wait / aceapex_batch_run / aceapex_batch_decode with that
+ * archive's own status (a corrupt archive fails alone: the others decode).
+ * At most 3000 archives per batch.
+ */
+typedef struct {
+    aceapex_archive* arc;
+    void* d_out;
+    uint64_t out_cap;
+    int status;
+} aceapex_batch_item;
+
+typedef struct aceapex_batch aceapex_batch;
+
+#define ACEAPEX_BATCH_GRAPH 1u  /* capture the decode launches into a CUDA graph once; runs replay it */
+
+/* Build a reusable batch: validates the items, allocates the batch's own
+ * device scratch (one partition per archive) and the device job table, and
+ * with ACEAPEX_BATCH_GRAPH captures the launches into a CUDA graph.  The
+ * context's decoder parameters at this call apply to every run.  The items
+ * array is read during this call only; the batch decodes into the d_out
+ * pointers given here. */
+int aceapex_batch_create(aceapex_ctx* ctx, const aceapex_batch_item* items, int n, uint32_t flags,
+                         aceapex_batch** out);
+/* Enqueue one decode of every archive of the batch on `stream` (a graph
+ * replay with ACEAPEX_BATCH_GRAPH).  Runs of one batch must not overlap. */
+int aceapex_batch_run_async(aceapex_batch* batch, void* stream);
+/* Synchronise `stream`, write each item's status into items[0..n) (may be
+ * NULL), fill stats (may be NULL; the stage split only without a graph) and
+ * return the first error of the run (ACEAPEX_OK when every archive decoded). */
+int aceapex_batch_wait(aceapex_batch* batch, void* stream, aceapex_batch_item* items, aceapex_stats* stats);
+/* aceapex_batch_run_async then aceapex_batch_wait. */
+int aceapex_batch_run(aceapex_batch* batch, void* stream, aceapex_batch_item* items, aceapex_stats* stats);
+int aceapex_batch_destroy(aceapex_batch* batch);
+/* One-shot batch: create (no graph), run, destroy. */
+int aceapex_batch_decode(aceapex_ctx* ctx, aceapex_batch_item* items, int n, void* stream, aceapex_stats* stats);
 
 /*
  * Decode without allocating anything (the paper has no counterpart: this is a

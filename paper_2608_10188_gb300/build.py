@@ -27,12 +27,12 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("rans.cu", "assemble.cu", "plain.cu", "noalloc.cu", "api.cpp", "plan.cpp",
-                                          "encode.cpp")]
+    return [os.path.join(CSRC, f) for f in ("rans.cu", "assemble.cu", "plain.cu", "noalloc.cu", "gather.cu", "api.cpp",
+                                          "batch.cpp", "subset.cpp", "plan.cpp", "encode.cpp")]
 
 
 def _deps():
-    return sources() + [os.path.join(CSRC, f) for f in ("internal.h", "plan.h", "common.cuh")] + [
+    return sources() + [os.path.join(CSRC, f) for f in ("internal.h", "plan.h", "common.cuh", "launch.h", "host.h")] + [
         os.path.join(os.path.dirname(HERE), "include", "aceapex.h")]
 
 

@@ -8,83 +8,11 @@
 #include <string>
 #include <vector>
 
-#include "../../include/aceapex.h"
-#include "internal.h"
-#include "plan.h"
-
-namespace acx {
-cudaError_t launch_prologue(uint32_t* counters, uint32_t n_counters, cudaStream_t st);
-cudaError_t launch_rans(const JobDev& job, int grid, cudaStream_t st);
-cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st);
-cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st);
-cudaError_t launch_plain(const JobDev& job, int grid, cudaStream_t st);
-size_t local_smem_bytes(uint32_t T, uint32_t LB);
-int rans_occupancy();
-int local_occupancy(size_t smem);
-int external_occupancy();
-int plain_occupancy();
-}  // namespace acx
+#include "host.h"
 
 using namespace acx;
 
-namespace {
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t cap = 0;
-    cudaError_t ensure(size_t n) {
-        if (n <= cap) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        size_t want = std::max(n, cap + cap / 4);
-        cudaError_t e = cudaMalloc(&p, want);
-        if (e != cudaSuccess) {
-            e = cudaMalloc(&p, n);
-            if (e != cudaSuccess) { p = nullptr; return e; }
-            want = n;
-        }
-        cap = want;
-        return cudaSuccess;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-};
-
-constexpr uint32_t kMaxCounters = kCounterWords;
-
-}  // namespace
-
-struct aceapex_ctx {
-    int device = 0;
-    aceapex_dec_params params{};
-    std::string err;
-    int n_sms = 0;
-    DevBuf streams, npend, pmap, spans, lists, arcs, in_arc, out_buf;
-    uint32_t* counters = nullptr;  // device
-    int* d_err = nullptr;          // device
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    int occ_rans = 0, occ_ext = 0, occ_plain = 0;
-};
-
-struct aceapex_archive {
-    aceapex_ctx* ctx = nullptr;
-    const void* d_arc = nullptr;
-    Plan plan;
-    BlockDev* d_blk = nullptr;
-    uint32_t* d_dtab = nullptr;
-};
-
-static int fail(aceapex_ctx* c, int code, const std::string& m) {
-    if (c) c->err = m;
-    return code;
-}
-static int cuda_fail(aceapex_ctx* c, cudaError_t e, const char* where) {
-    return fail(c, ACEAPEX_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
-}
+static constexpr uint32_t kMaxCounters = kCounterWords;
 
 extern "C" {
 
@@ -146,6 +74,8 @@ int aceapex_ctx_destroy(aceapex_ctx* c) {
     c->arcs.release();
     c->in_arc.release();
     c->out_buf.release();
+    c->slot_out.release();
+    c->items.release();
     if (c->counters) cudaFree(c->counters);
     if (c->d_err) cudaFree(c->d_err);
     for (auto& ev : c->ev)
@@ -164,7 +94,8 @@ int aceapex_ctx_set_params(aceapex_ctx* c, const aceapex_dec_params* p) {
 int aceapex_encode(const uint8_t* src, uint64_t n, const aceapex_enc_params* p, uint8_t** out, uint64_t* out_len) {
     aceapex_enc_params d{};
     if (p) d = *p;
-    return encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, d.latest_source, d.max_depth, d.short_latest, out, out_len);
+    return encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, d.latest_source, d.max_depth,
+                          d.short_latest, d.deps, out, out_len);
 }
 
 void aceapex_free(void* p) { free(p); }
@@ -187,6 +118,12 @@ int aceapex_archive_open(aceapex_ctx* c, const void* d_arc, const void* h_arc, u
     if (e == cudaSuccess) e = cudaMalloc(&A->d_dtab, 4 * kM * sizeof(uint32_t));
     if (e == cudaSuccess && nb) e = cudaMemcpy(A->d_blk, A->plan.blk.data(), nb * sizeof(BlockDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(A->d_dtab, A->plan.dtab.data(), 4 * kM * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && A->plan.has_deps) {
+        const size_t nd = std::max<size_t>(A->plan.deps.size(), 1);
+        e = cudaMalloc(&A->d_deps, nd * sizeof(uint32_t));
+        if (e == cudaSuccess && !A->plan.deps.empty())
+            e = cudaMemcpy(A->d_deps, A->plan.deps.data(), A->plan.deps.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         aceapex_archive_close(A);
         return cuda_fail(c, e, "archive_open");
@@ -200,6 +137,8 @@ int aceapex_archive_close(aceapex_archive* A) {
     if (A->ctx) cudaSetDevice(A->ctx->device);
     if (A->d_blk) cudaFree(A->d_blk);
     if (A->d_dtab) cudaFree(A->d_dtab);
+    if (A->d_deps) cudaFree(A->d_deps);
+    if (A->d_slot) cudaFree(A->d_slot);
     delete A;
     return ACEAPEX_OK;
 }
@@ -275,6 +214,7 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     J.hi = P.n_blocks;
     J.min_match = P.min_match;
     J.item_base = 0;
+    J.deps = A->d_deps;
     job.arcs = nullptr;
     job.n_arcs = 1;
     job.n_items = P.n_blocks;
@@ -286,27 +226,62 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     job.lists[0] = (JobDev::ListEnt*)c->lists.p;
     job.lists[1] = (JobDev::ListEnt*)c->lists.p + std::max<uint64_t>(P.span_slots, 1);
     if (P.n_blocks == 0) return ACEAPEX_OK;
-    const size_t lsm = local_smem_bytes(P.max_tok, P.max_lenb);
-    if (c->params.variant != ACEAPEX_VARIANT_PLAIN && lsm > 227 * 1024)
-        return fail(c, ACEAPEX_E_CORRUPT, "block too large for the local pass");
-    if (timed && (e = cudaEventRecord(c->ev[0], st)) != cudaSuccess) return cuda_fail(c, e, "event");
-    if ((e = launch_prologue(c->counters, 3 + 1, st)) != cudaSuccess) return cuda_fail(c, e, "prologue launch");
-    if ((e = launch_rans(job, c->occ_rans * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "rANS launch");
-    if (timed && (e = cudaEventRecord(c->ev[1], st)) != cudaSuccess) return cuda_fail(c, e, "event");
-    if (c->params.variant == ACEAPEX_VARIANT_PLAIN) {
-        if ((e = launch_plain(job, c->occ_plain * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "plain launch");
-    } else {
+    LaunchPlan lp;
+    int rc = launch_plan(c, c->params, P.max_tok, P.max_lenb, &lp);
+    if (rc) return rc;
+    return enqueue_job(c, job, lp, 3 + 1, nullptr, 0, st, timed ? c->ev : nullptr);
+}
+
+int acx::launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_tok, uint32_t max_lenb,
+                     LaunchPlan* lp) {
+    lp->variant = p.variant;
+    lp->grid_rans = (p.rans_ctas_per_sm ? std::min<int>(c->occ_rans, (int)p.rans_ctas_per_sm) : c->occ_rans) * c->n_sms;
+    lp->grid_ext = c->occ_ext * c->n_sms;
+    lp->grid_plain = c->occ_plain * c->n_sms;
+    lp->grid_local = 0;
+    if (p.variant != ACEAPEX_VARIANT_PLAIN) {
+        const size_t lsm = local_smem_bytes(max_tok, max_lenb);
+        if (lsm > 227 * 1024) return fail(c, ACEAPEX_E_CORRUPT, "block too large for the local pass");
         int occ = std::max(1, local_occupancy(lsm));
-        if (c->params.ctas_per_sm) occ = std::min<int>(occ, (int)c->params.ctas_per_sm);
-        if ((e = launch_local(job, occ * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "local launch");
+        if (p.ctas_per_sm) occ = std::min<int>(occ, (int)p.ctas_per_sm);
+        lp->grid_local = occ * c->n_sms;
     }
-    if (timed && (e = cudaEventRecord(c->ev[2], st)) != cudaSuccess) return cuda_fail(c, e, "event");
-    if ((e = launch_external(job, c->occ_ext * c->n_sms, st)) != cudaSuccess) return cuda_fail(c, e, "external launch");
-    if (timed && (e = cudaEventRecord(c->ev[3], st)) != cudaSuccess) return cuda_fail(c, e, "event");
     return ACEAPEX_OK;
 }
 
-static int read_status(aceapex_ctx* c, cudaStream_t st) {
+// The four launches of a decode job on `st`: ticket/status reset, entropy
+// stage, local pass (or the plain serial pass), cross-block pass.  With
+// `ev` (4 events), events bracket the three stages.
+int acx::enqueue_job(aceapex_ctx* c, const JobDev& job, const LaunchPlan& lp, uint32_t n_counters, int* errs,
+                     uint32_t n_errs, cudaStream_t st, cudaEvent_t* ev) {
+    cudaError_t e;
+    if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    if ((e = launch_prologue(job.counters, n_counters, st, errs, n_errs)) != cudaSuccess)
+        return cuda_fail(c, e, "prologue launch");
+    if ((e = launch_rans(job, lp.grid_rans, st)) != cudaSuccess) return cuda_fail(c, e, "rANS launch");
+    if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    if (lp.variant == ACEAPEX_VARIANT_PLAIN) {
+        if ((e = launch_plain(job, lp.grid_plain, st)) != cudaSuccess) return cuda_fail(c, e, "plain launch");
+    } else {
+        if ((e = launch_local(job, lp.grid_local, st)) != cudaSuccess) return cuda_fail(c, e, "local launch");
+    }
+    if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    if ((e = launch_external(job, lp.grid_ext, st)) != cudaSuccess) return cuda_fail(c, e, "external launch");
+    if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    return ACEAPEX_OK;
+}
+
+std::string acx::device_error_text(const int h[3]) {
+    static const char* stages[] = {"?", "rANS stream", "varint lengths", "token sums/commands",
+                                   "offsets/history", "dependency wait", "plain parse", "block limits"};
+    const int st = (h[1] >> 24) & 7;
+    std::string m = std::string("device reported: ") + aceapex_status_string(h[0]) + " (" + stages[st];
+    if (st == 1) m += " " + std::to_string(h[1] & 0xff);
+    m += ", block " + std::to_string((unsigned)h[2]) + ")";
+    return m;
+}
+
+int acx::ctx_read_status(aceapex_ctx* c, cudaStream_t st) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
     int h[4] = {0, 0, 0, 0};
@@ -314,13 +289,7 @@ static int read_status(aceapex_ctx* c, cudaStream_t st) {
         return cuda_fail(c, e, "error word");
     if (h[0]) {
         cudaMemset(c->d_err, 0, sizeof(h));
-        static const char* stages[] = {"?", "rANS stream", "varint lengths", "token sums/commands",
-                                       "offsets/history", "dependency wait", "plain parse", "block limits"};
-        const int st = (h[1] >> 24) & 7;
-        std::string m = std::string("device reported: ") + aceapex_status_string(h[0]) + " (" + stages[st];
-        if (st == 1) m += " " + std::to_string(h[1] & 0xff);
-        m += ", block " + std::to_string((unsigned)h[2]) + ")";
-        return fail(c, h[0], m);
+        return fail(c, h[0], device_error_text(h));
     }
     return ACEAPEX_OK;
 }
@@ -337,10 +306,11 @@ static void fill_stats(aceapex_ctx* c, const Plan& P, aceapex_stats* s) {
     s->ms_total = t;
     s->blocks = P.n_blocks;
     s->bytes = P.total;
-    uint32_t st[2] = {0, 0};
-    cudaMemcpy(st, c->counters + kStatPending, sizeof st, cudaMemcpyDeviceToHost);
-    s->pending_spans = st[0];
-    s->wait_polls = st[1];
+    uint32_t st[6] = {0, 0, 0, 0, 0, 0};
+    cudaMemcpy(st, c->counters + kStatPendBytes, sizeof st, cudaMemcpyDeviceToHost);
+    s->pending_bytes = (uint64_t)st[0] | ((uint64_t)st[1] << 32);
+    s->pending_spans = st[kStatPending - kStatPendBytes];
+    s->wait_polls = st[kStatPolls - kStatPendBytes];
 }
 
 extern "C" {
@@ -355,7 +325,7 @@ int aceapex_decode_all_async(aceapex_ctx* c, aceapex_archive* A, void* d_out, ui
 int aceapex_sync(aceapex_ctx* c, void* stream) {
     if (!c) return ACEAPEX_E_ARG;
     cudaSetDevice(c->device);
-    return read_status(c, (cudaStream_t)stream);
+    return ctx_read_status(c, (cudaStream_t)stream);
 }
 
 int aceapex_decode_all(aceapex_ctx* c, aceapex_archive* A, void* d_out, uint64_t out_cap, void* stream,
@@ -365,7 +335,7 @@ int aceapex_decode_all(aceapex_ctx* c, aceapex_archive* A, void* d_out, uint64_t
     cudaSetDevice(c->device);
     int rc = enqueue_decode(c, A, A->d_arc, d_out, (cudaStream_t)stream, stats != nullptr);
     if (rc) return rc;
-    rc = read_status(c, (cudaStream_t)stream);
+    rc = ctx_read_status(c, (cudaStream_t)stream);
     if (rc == ACEAPEX_OK && stats) fill_stats(c, A->plan, stats);
     return rc;
 }
@@ -394,7 +364,7 @@ int aceapex_decode_host(aceapex_ctx* c, aceapex_archive* A, const void* h_arc, u
         (e = cudaMemcpyAsync(h_out, c->out_buf.p, A->plan.total, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         rc = cuda_fail(c, e, "output download");
     if (rc == ACEAPEX_OK && stats && (e = cudaEventRecord(c->ev[3], st)) != cudaSuccess) rc = cuda_fail(c, e, "event");
-    if (rc == ACEAPEX_OK) rc = read_status(c, st);
+    if (rc == ACEAPEX_OK) rc = ctx_read_status(c, st);
     if (rc == ACEAPEX_OK && stats) {
         float ms = 0;
         cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]);

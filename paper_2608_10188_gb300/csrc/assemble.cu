@@ -26,6 +26,7 @@
 //   depends on, which lie at lower positions and were taken earlier: the
 //   ascending order makes the bounded waits deadlock-free.
 #include "common.cuh"
+#include "launch.h"
 
 namespace acx {
 
@@ -201,12 +202,13 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
         if (item >= job.n_items) return;
         const int a = find_arc(job, item);
         const ArcJob J = load_arc(job, a);
-        const uint32_t b = J.lo + (item - J.item_base);
+        const ItemRef ir = item_ref(J, item - J.item_base);
+        const uint32_t b = ir.blk;
         const BlockDev& bd = J.blk[b];
         const uint64_t B = (uint64_t)b * kBlock;
         const uint32_t R = bd.raw_len, n = bd.n_tok, LB = bd.s_raw[kLen], n_lit = bd.s_raw[kLit];
         const uint32_t n_new = bd.n_new;
-        const uint8_t* scr = J.scratch + bd.scratch;
+        const uint8_t* scr = J.scratch + ir.scratch;
         bool bad = n > job.max_tok || LB > job.max_lenb || n_new > job.max_tok;
         int stage = bad ? kStageLimits : 0;
         auto mark = [&](bool cond, int st) {
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
         }
         if (__syncthreads_or(timed_out)) {
             // a copy that never lands: give up on the decode (the barrier phase is lost)
-            if (tid == 0) set_err(job.err, kErrTimeout, kStageWait << 24, b);
+            if (tid == 0) set_err_arc(job, a, kErrTimeout, kStageWait << 24, b);
             return;
         }
 
@@ -357,7 +359,26 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
             mark(misc[1] != 0, kStageSources);
         }
 
-        uint32_t npend = 0;
+        // ---- with dependency lists: every block a match reads outside its own
+        //      block must be listed (range decodes read only the listed closure) ----
+        if (J.deps && !bad) {
+            const uint32_t* dl = J.deps + bd.dep_off;
+            const uint32_t nd = bd.n_deps;
+            bool dbad = false;
+            for (uint32_t i = i0; i < i1; i++) {
+                const uint32_t ml = tml[i];
+                if (!ml || tsrc[i] >= B) continue;
+                const uint64_t d = B + tpos[i] + tll[i] - tsrc[i];
+                const uint64_t e = tsrc[i] + (d < ml ? d : ml);
+                for (uint64_t a = tsrc[i] >> 14; a <= (e - 1) >> 14 && a < b && !dbad; a++)
+                    dbad = !listed(dl, nd, (uint32_t)a);
+            }
+            if (dbad) misc[1] = 1;
+            __syncthreads();
+            mark(misc[1] != 0, kStageSources);
+        }
+
+        uint32_t npend = 0, pbytes = 0;
         if (!bad) {
             // ---- literal placement: one warp per run ----
             for (uint32_t i = warp; i < n; i += kLocWarps) copy_run(sout, slit, tlit[i], tpos[i], tll[i], lane);
@@ -412,39 +433,47 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
                 if (!any_left || !any_prog) break;
             }
             // ---- whatever is still unresolved becomes pending pieces ----
-            uint32_t cnt = 0;
+            uint32_t cnt = 0, nbytes = 0;
             for (uint32_t i = i0; i < i1; i++)
-                if (tstat[i]) cnt += pieces_of(tml[i]);
-            v3[0] = cnt; v3[1] = 0; v3[2] = 0;
+                if (tstat[i]) {
+                    cnt += pieces_of(tml[i]);
+                    nbytes += tml[i];
+                }
+            v3[0] = cnt; v3[1] = nbytes; v3[2] = 0;
             block_scan3(v3, tot3, scanbuf);
             npend = tot3[0];
+            pbytes = tot3[1];
             uint32_t k = v3[0];
             for (uint32_t i = i0; i < i1; i++) {
                 if (!tstat[i]) continue;
                 const uint32_t o = tpos[i] + tll[i];
-                k += emit_pieces(J.spans + bd.span_base + k, o, tsrc[i], tml[i], B + o - tsrc[i]);
+                k += emit_pieces(J.spans + ir.span_base + k, o, tsrc[i], tml[i], B + o - tsrc[i]);
             }
         }
         __syncthreads();
         if (bad) {
-            if (tid == 0) set_err(job.err, kErrCorrupt, stage << 24, b);
+            if (tid == 0) set_err_arc(job, a, kErrCorrupt, stage << 24, b);
             npend = 0;
         }
         // ---- write the block (pending bytes are filled by the cross-block pass) ----
-        uint8_t* gout = J.out + B;
+        uint8_t* gout = J.out + (uint64_t)ir.slot * kBlock;
         const uint32_t nv = R / 16;
         for (uint32_t i = tid; i < nv; i += kLocThreads) reinterpret_cast<uint4*>(gout)[i] = reinterpret_cast<uint4*>(sout)[i];
         for (uint32_t x = 16 * nv + tid; x < R; x += kLocThreads) gout[x] = sout[x];
         {
-            // the pending bitmap is written for every block (zero when nothing is
-            // pending), so readers need no second lookup
-            uint4* gp = reinterpret_cast<uint4*>(J.pmap + (uint64_t)b * (kBlock / 32));
+            // the pending bitmap is written for every block (all clear when nothing
+            // is pending, a corrupt block included), so readers need no second
+            // lookup and never wait on a corrupt block
+            uint4* gp = reinterpret_cast<uint4*>(J.pmap + (uint64_t)ir.slot * (kBlock / 32));
             const uint4* sp = reinterpret_cast<const uint4*>(pend);
-            for (uint32_t i = tid; i < kBlock / 128; i += kLocThreads) gp[i] = sp[i];
+            for (uint32_t i = tid; i < kBlock / 128; i += kLocThreads) gp[i] = npend ? sp[i] : make_uint4(0, 0, 0, 0);
         }
         if (tid == 0) {
-            J.npend[b] = npend;
-            if (npend) atomicAdd(&job.counters[kStatPending], npend);
+            J.npend[ir.slot] = npend;
+            if (npend) {
+                atomicAdd(&job.counters[kStatPending], npend);
+                atomicAdd(reinterpret_cast<unsigned long long*>(job.counters + kStatPendBytes), (unsigned long long)pbytes);
+            }
         }
         __syncthreads();
     }
@@ -453,13 +482,14 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
 // ---- cross-block pass --------------------------------------------------------------------
 // Are the bytes [s, e) (absolute) final?  The local pass writes every
 // block's pending-byte bitmap; a clear bit means a final byte.
-__device__ __forceinline__ bool src_final(const uint32_t* npend, const uint32_t* pmap, uint64_t s, uint64_t e) {
-    (void)npend;
+__device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t e) {
     for (uint64_t a = s >> 14; a <= (e - 1) >> 14; a++) {
         const uint64_t A = a << 14;
         const uint32_t lo = (uint32_t)((s > A ? s : A) - A);
         const uint32_t hi = (uint32_t)((e < A + kBlock ? e : A + kBlock) - A);
-        const uint32_t* pm = pmap + a * (kBlock / 32);
+        const uint64_t sl = slot_of(L, a);
+        if (sl == kNoSlot) return false;  // not in this decode's output: never final
+        const uint32_t* pm = L.pmap + sl * (kBlock / 32);
         for (uint32_t w = lo >> 5; w <= ((hi - 1) >> 5); w++)
             if (ld_acquire_u32(pm + w) & range_mask(w, lo, hi)) return false;  // pairs with red_and_release
     }
@@ -471,31 +501,30 @@ constexpr uint64_t kRound0WaitNs = 4000;  // how long a round-0 lane waits for i
 
 // Are the bytes a piece reads final?  (period 0: [src, src+len); otherwise the
 // residues phase.. of the period window [src, src+period), one or two ranges.)
-__device__ __forceinline__ bool piece_final(const uint32_t* npend, const uint32_t* pmap, uint64_t src,
-                                            uint32_t phase, uint32_t period, uint32_t len) {
-    if (period == 0) return src_final(npend, pmap, src, src + len);
-    if (len >= period) return src_final(npend, pmap, src, src + period);
-    if (phase + len <= period) return src_final(npend, pmap, src + phase, src + phase + len);
-    return src_final(npend, pmap, src + phase, src + period) &&
-           src_final(npend, pmap, src, src + (phase + len - period));
+__device__ __forceinline__ bool piece_final(const ArcJob& L, uint64_t src, uint32_t phase, uint32_t period,
+                                            uint32_t len) {
+    if (period == 0) return src_final(L, src, src + len);
+    if (len >= period) return src_final(L, src, src + period);
+    if (phase + len <= period) return src_final(L, src + phase, src + phase + len);
+    return src_final(L, src + phase, src + period) && src_final(L, src, src + (phase + len - period));
 }
 
-// A warp's attempt at its lanes' pieces (lane `has` a piece `rec` of block
-// `blk`, all of archive L).  Each lane checks its own piece; the ready pieces
+// A warp's attempt at its lanes' pieces (lane `has` a piece `rec` of the
+// block in output slot `dslot`, all of archive L).  Each lane checks its own piece; the ready pieces
 // are then copied by the whole warp, lane i moving byte i (one coalesced
 // request per piece), eight pieces' loads in flight before their stores;
 // after one fence the owners clear the pieces' pending bits with release
 // reductions.  Returns true on the lanes whose piece is done.
 constexpr int kCopyBatch = 8;
-__device__ bool try_pieces(bool has, const ArcJob& L, uint32_t blk, SpanRec rec, SpanRec* wrec, uint64_t* wdst,
+__device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec rec, SpanRec* wrec, uint64_t* wdst,
                            int lane) {
     const uint64_t src = (uint64_t)rec.x | ((uint64_t)(rec.y & 0xff) << 32);
     const uint32_t phase = rec.y >> 8, period = rec.w, o = rec.z & 0xffff, len = rec.z >> 16;
-    const bool ready = has && piece_final(L.npend, L.pmap, src, phase, period, len);
+    const bool ready = has && piece_final(L, src, phase, period, len);
     const uint32_t rmask = __ballot_sync(ACX_FULL, ready);
     if (!rmask) return false;
     wrec[lane] = rec;
-    wdst[lane] = (uint64_t)blk * kBlock + o;
+    wdst[lane] = (uint64_t)dslot * kBlock + o;
     __syncwarp();
     uint8_t* g = L.out;
     uint32_t m = rmask;
@@ -517,7 +546,7 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t blk, SpanRec rec,
                     const uint64_t rs = (uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32);
                     const uint32_t rp = r.w;
                     const uint64_t q = rp ? rs + ((r.y >> 8) + (uint32_t)lane) % rp : rs + lane;
-                    v[u >> 2] |= (uint32_t)__ldcg(g + q) << (8 * (u & 3));
+                    v[u >> 2] |= (uint32_t)__ldcg(g + out_off(L, q)) << (8 * (u & 3));
                 }
             }
         }
@@ -531,7 +560,7 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t blk, SpanRec rec,
     }
     __threadfence();  // every lane's stores are visible before any bit is cleared
     if (ready) {
-        uint32_t* pm = L.pmap + (uint64_t)blk * (kBlock / 32);
+        uint32_t* pm = L.pmap + (uint64_t)dslot * (kBlock / 32);
         for (uint32_t w = o >> 5; w <= ((o + len - 1) >> 5); w++) red_and_release(pm + w, ~range_mask(w, o, o + len));
     }
     __syncwarp();
@@ -604,13 +633,13 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
     // short while for sources that are about to be finished by lower pieces,
     // then defers its piece to the rounds below.
     {
-        uint32_t blk = 0, cnt = 0, next = 0, base = 0, item = 0;
+        uint32_t blk = 0, dsl = 0, cnt = 0, next = 0, base = 0, item = 0;
         int arc = 0;
         bool exhausted = false;
         ArcJob J = load_arc(job, 0);
         bool has = false;
         SpanRec rec{0, 0, 0, 0};
-        uint32_t l_blk = 0, l_slot = 0, l_item = 0;
+        uint32_t l_blk = 0, l_dsl = 0, l_span = 0, l_item = 0;
         int l_arc = 0;
         uint64_t t0 = 0;
         uint32_t spins = 0;
@@ -624,18 +653,21 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
                     if (item >= job.n_items) { exhausted = true; break; }
                     arc = find_arc(job, item);
                     J = load_arc(job, arc);
-                    blk = J.lo + (item - J.item_base);
-                    cnt = J.npend[blk];
+                    const ItemRef ir = item_ref(J, item - J.item_base);
+                    blk = ir.blk;
+                    dsl = ir.slot;
+                    cnt = J.npend[dsl];
                     next = 0;
-                    base = J.blk[blk].span_base;
+                    base = ir.span_base;
                     continue;
                 }
                 const uint32_t avail = cnt - next;
                 const uint32_t r = __popc(idle & lt_mask);
                 if ((idle >> lane & 1) && r < avail) {
-                    l_slot = base + next + r;
-                    rec = J.spans[l_slot];
+                    l_span = base + next + r;
+                    rec = J.spans[l_span];
                     l_blk = blk;
+                    l_dsl = dsl;
                     l_item = item;
                     l_arc = arc;
                     t0 = gtimer();
@@ -651,25 +683,26 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             while (todo) {
                 const int a0 = __shfl_sync(ACX_FULL, l_arc, __ffs(todo) - 1);
                 const bool mine = has && l_arc == a0;
-                const bool done = try_pieces(mine, load_arc(job, a0), l_blk, rec, wrec, wdst, lane);
+                const bool done = try_pieces(mine, load_arc(job, a0), l_dsl, rec, wrec, wdst, lane);
                 if (done) { has = false; progressed = true; }
                 todo &= ~__ballot_sync(ACX_FULL, mine);
             }
             // give up on pieces that waited too long: the rounds finish them
             const bool giveup = has && gtimer() - t0 > kRound0WaitNs;
-            append(giveup, ListEnt{l_slot, l_item}, job.lists[0], &job.counters[kListCnt], lane);
+            append(giveup, ListEnt{l_span, l_item}, job.lists[0], &job.counters[kListCnt], lane);
             if (giveup) has = false;
             if (__any_sync(ACX_FULL, progressed || giveup)) {
                 spins = 0;
             } else {
                 __nanosleep(64);
                 if ((++spins & 255) == 0 && __any_sync(ACX_FULL, gtimer() > deadline)) {
-                    if (lane == 0) set_err(job.err, kErrTimeout, kStageWait << 24, l_blk);
+                    if (lane == 0) set_err_arc(job, l_arc, kErrTimeout, kStageWait << 24, l_blk);
                     break;
                 }
             }
         }
     }
+    uint32_t n_prev = 0xffffffffu;
     for (uint32_t round = 1;; round++) {
         const uint32_t in = (round - 1) & 1, out = round & 1;
         if (!grid_barrier(job.counters, kListCnt + out, deadline)) {
@@ -685,6 +718,20 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             job.counters[kTrace + 3 * round + 2] = (uint32_t)(t >> 32);
         }
         if (n == 0) return;
+        if (n == n_prev) {
+            // the last round finished no piece.  In a valid archive the lowest
+            // pending piece always has final sources (every source precedes its
+            // destination), so the pieces left wait on bytes that no piece
+            // writes: their archives are corrupt.
+            for (uint32_t i = gwarp * 32 + lane; i < n; i += nwarps * 32) {
+                const ListEnt e = job.lists[in][i];
+                const int a = find_arc(job, e.y);
+                const ArcJob J = load_arc(job, a);
+                set_err_arc(job, a, kErrCorrupt, kStageSources << 24, item_ref(J, e.y - J.item_base).blk);
+            }
+            return;
+        }
+        n_prev = n;
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&job.counters[kStatPolls], 1u);
         if (round > (1u << 20)) {
             if (blockIdx.x == 0 && threadIdx.x == 0) set_err(job.err, kErrTimeout, kStageWait << 24, 0);
@@ -705,7 +752,7 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
                 const ArcJob J = load_arc(job, a0);
                 SpanRec r{0, 0, 0, 0};
                 if (mine) r = J.spans[e.x];
-                const bool d2 = try_pieces(mine, J, mine ? J.lo + (e.y - J.item_base) : 0, r, wrec, wdst, lane);
+                const bool d2 = try_pieces(mine, J, mine ? item_ref(J, e.y - J.item_base).slot : 0, r, wrec, wdst, lane);
                 if (mine) done = d2;
                 todo &= ~__ballot_sync(ACX_FULL, mine);
             }
@@ -725,9 +772,17 @@ cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st) {
 }
 
 cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st) {
-    JobDev j = job;
-    void* args[] = {&j};
-    return cudaLaunchCooperativeKernel((const void*)k_external, dim3(grid), dim3(kExtThreads), args, 0, st);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kExtThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_external, job);
 }
 
 int local_occupancy(size_t smem) {

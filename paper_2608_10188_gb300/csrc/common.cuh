@@ -31,6 +31,12 @@ __device__ __forceinline__ void set_err(int* err, int code, int where, uint32_t 
     }
 }
 
+// The same, also recorded as archive a's own status in a batched job.
+__device__ __forceinline__ void set_err_arc(const JobDev& job, int a, int code, int where, uint32_t block) {
+    set_err(job.err, code, where, block);
+    if (job.arc_err && a >= 0) atomicCAS(job.arc_err + a, 0, code);
+}
+
 __device__ __forceinline__ uint64_t gtimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -92,6 +98,46 @@ __device__ __forceinline__ int find_arc(const JobDev& job, uint32_t item) {
 }
 
 __device__ __forceinline__ ArcJob load_arc(const JobDev& job, int a) { return job.arcs ? job.arcs[a] : job.one; }
+
+// Where a work item's block goes: its block id, output slot, pending-piece
+// base and decoded-stream offset (idx counted from the archive's item_base).
+struct ItemRef {
+    uint32_t blk, slot, span_base;
+    uint64_t scratch;
+};
+__device__ __forceinline__ ItemRef item_ref(const ArcJob& J, uint32_t idx) {
+    ItemRef r;
+    if (J.items) {
+        const ItemDev it = J.items[idx];
+        r.blk = it.block;
+        r.slot = it.slot;
+        r.span_base = it.span_base;
+        r.scratch = it.scratch;
+    } else {
+        r.blk = J.lo + idx;
+        r.slot = r.blk;
+        r.span_base = J.blk[r.blk].span_base;
+        r.scratch = J.blk[r.blk].scratch;
+    }
+    return r;
+}
+// Output slot of block a, and the output offset of absolute position pos.
+__device__ __forceinline__ uint64_t slot_of(const ArcJob& J, uint64_t a) { return J.slot ? J.slot[a] : a; }
+__device__ __forceinline__ uint64_t out_off(const ArcJob& J, uint64_t pos) {
+    return J.slot ? (uint64_t)J.slot[pos >> 14] * kBlock + (pos & (kBlock - 1)) : pos;
+}
+
+// Is block id a in the ascending list dl[0, n)?
+__device__ __forceinline__ bool listed(const uint32_t* dl, uint32_t n, uint32_t a) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        const uint32_t v = dl[m];
+        if (v == a) return true;
+        if (v < a) lo = m + 1; else hi = m;
+    }
+    return false;
+}
 
 // Bit masks of the bytes [s, e) of a 16 KiB block bitmap, word by word.
 __device__ __forceinline__ uint32_t range_mask(uint32_t w, uint32_t s, uint32_t e) {

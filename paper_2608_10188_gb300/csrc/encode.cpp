@@ -330,7 +330,7 @@ void parallel_for(uint32_t n, int threads, F fn) {
 }  // namespace
 
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   int latest, uint32_t max_depth, int short_latest, uint8_t** out, uint64_t* out_len) {
+                   int latest, uint32_t max_depth, int short_latest, int deps, uint8_t** out, uint64_t* out_len) {
     if (!out || !out_len || (n && !src)) return -1;
     if (min_match == 0) min_match = 4;
     if (max_lanes == 0) max_lanes = 32;
@@ -339,6 +339,9 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
     if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
     const uint32_t nb = (uint32_t)((n + kBlock - 1) / kBlock);
     std::vector<BlockStreams> blocks(nb);
+    // dependency lists: per block, the ascending ids of the earlier blocks
+    // holding bytes that its matches read
+    std::vector<uint32_t> dep_ids, dep_off(nb, 0), dep_n(nb, 0);
     try {
         // order-0 literal cost estimate
         uint64_t hist[256] = {0};
@@ -368,6 +371,25 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
         for (uint32_t b = 0; b < nb; b++) {
             const uint64_t B = (uint64_t)b * kBlock, E = std::min<uint64_t>(n, B + kBlock);
             P.parse_block(B, E, blocks[b], ins);
+        }
+        if (deps) {
+            std::vector<uint32_t> ids;
+            for (uint32_t b = 0; b < nb; b++) {
+                const uint64_t lo = P.block_first[b];
+                const uint64_t hi = b + 1 < nb ? P.block_first[b + 1] : P.emitted.size();
+                ids.clear();
+                for (uint64_t m = lo; m < hi; m++) {
+                    const Parser::Emitted& M = P.emitted[m];
+                    const uint64_t d = M.dst - M.src;
+                    const uint64_t end = M.src + (d < M.len ? d : M.len);  // bytes the match reads
+                    for (uint64_t a = M.src / kBlock; a <= (end - 1) / kBlock && a < b; a++) ids.push_back((uint32_t)a);
+                }
+                std::sort(ids.begin(), ids.end());
+                ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+                dep_off[b] = (uint32_t)dep_ids.size();
+                dep_n[b] = (uint32_t)ids.size();
+                dep_ids.insert(dep_ids.end(), ids.begin(), ids.end());
+            }
         }
     } catch (...) {
         return -3;
@@ -430,7 +452,9 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
         }
         blocks[b] = BlockStreams();
     });
-    const uint64_t off_tab = 64, off_idx = 64 + 2048, off_pay = (off_idx + 40ull * nb + 15) & ~15ull;
+    const uint64_t off_tab = 64, off_idx = 64 + 2048;
+    const uint64_t off_deps = deps ? (off_idx + 40ull * nb + 15) & ~15ull : 0;
+    const uint64_t off_pay = deps ? (off_deps + 4ull * dep_ids.size() + 15) & ~15ull : (off_idx + 40ull * nb + 15) & ~15ull;
     uint64_t total = off_pay;
     std::vector<uint64_t> poff(nb);
     for (uint32_t b = 0; b < nb; b++) {
@@ -450,8 +474,8 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
     memcpy(a + 24, &nb, 4);
     memcpy(a + 32, &off_tab, 8);
     memcpy(a + 40, &off_idx, 8);
-    const uint64_t zero = 0;
-    memcpy(a + 48, &zero, 8);
+    memcpy(a + 48, &off_deps, 8);
+    if (deps && !dep_ids.empty()) memcpy(a + off_deps, dep_ids.data(), 4 * dep_ids.size());
     memcpy(a + 56, &off_pay, 8);
     for (int s = 0; s < 4; s++) memcpy(a + off_tab + 512 * s, freq[s], 512);
     parallel_for(nb, threads, [&](uint32_t b) {
@@ -465,6 +489,8 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
         memcpy(e + 8, &pl, 4);
         memcpy(e + 12, &ntok, 4);
         memcpy(e + 16, &R, 4);
+        memcpy(e + 20, &dep_off[b], 4);
+        memcpy(e + 24, &dep_n[b], 4);
         const uint64_t h = fnv1a64(src + B, R);
         memcpy(e + 32, &h, 8);
         memcpy(a + poff[b], pay[b].data(), pay[b].size());

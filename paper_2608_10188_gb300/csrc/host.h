@@ -1,0 +1,119 @@
+// Host-side state of the C ABI: device buffers, contexts, opened archives.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/aceapex.h"
+#include "internal.h"
+#include "launch.h"
+#include "plan.h"
+
+namespace acx {
+
+// A device allocation that only grows (by at least a quarter each time, so a
+// sequence of slightly larger requests does not reallocate every call).
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t n) {
+        if (n <= cap) return cudaSuccess;
+        const size_t want = std::max(n, cap + cap / 4);
+        release();
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) {
+            cap = want;
+            return e;
+        }
+        e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        cap = n;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+}  // namespace acx
+
+struct aceapex_ctx {
+    int device = 0;
+    aceapex_dec_params params{};
+    std::string err;
+    int n_sms = 0;
+    acx::DevBuf streams, npend, pmap, spans, lists, arcs, in_arc, out_buf;
+    acx::DevBuf slot_out, items;   // range decodes: decoded closure blocks, work items
+    uint32_t* counters = nullptr;  // device
+    int* d_err = nullptr;          // device
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int occ_rans = 0, occ_ext = 0, occ_plain = 0;
+};
+
+struct aceapex_archive {
+    aceapex_ctx* ctx = nullptr;
+    const void* d_arc = nullptr;
+    acx::Plan plan;
+    acx::BlockDev* d_blk = nullptr;
+    uint32_t* d_dtab = nullptr;
+    uint32_t* d_deps = nullptr;    // dependency lists (archives that carry them)
+    uint32_t* d_slot = nullptr;    // block -> output slot of subset decodes (allocated on first use)
+    std::vector<uint32_t> seen;    // closure walk marks (epoch per block)
+    uint32_t epoch = 0;
+};
+
+namespace acx {
+
+inline int fail(aceapex_ctx* c, int code, const std::string& m) {
+    if (c) c->err = m;
+    return code;
+}
+inline int cuda_fail(aceapex_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, ACEAPEX_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Text of a device-reported error (err[0..2] as the kernels write it).
+std::string device_error_text(const int h[3]);
+
+// Grid sizes and variant of one decode job.
+struct LaunchPlan {
+    uint32_t variant = 0;
+    int grid_rans = 0, grid_local = 0, grid_plain = 0, grid_ext = 0;
+};
+// Grids for a job whose largest block has max_tok tokens and max_lenb length
+// bytes, under decoder parameters p (fails when a block cannot fit the local
+// pass's shared memory).
+int launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_tok, uint32_t max_lenb, LaunchPlan* lp);
+// Synchronise st and return (and clear) the context's device error status.
+int ctx_read_status(aceapex_ctx* c, cudaStream_t st);
+
+// Block-dependency closure of blocks [b0, b1] of an opened archive, sorted:
+// with dependency lists the blocks reachable through them, without lists
+// every block up to b1 (sources always precede their destinations).
+void block_closure(aceapex_archive* A, uint32_t b0, uint32_t b1, std::vector<uint32_t>* out);
+
+// Work items of a job that decodes `blocks` (ascending) of plan P into the
+// output slots `slots`: per item its piece base and stream offset, and the
+// job's scratch sizes.
+struct SubsetPlan {
+    std::vector<ItemDev> items;
+    uint64_t scratch_bytes = 0, span_slots = 0;
+    uint32_t max_tok = 1, max_lenb = 1;
+};
+void subset_plan(const Plan& P, const uint32_t* blocks, const uint32_t* slots, size_t n, SubsetPlan* S);
+
+// Make sure the archive's device slot table exists (all kNoSlot at first).
+int ensure_slot_table(aceapex_ctx* c, aceapex_archive* A);
+
+// Enqueue the decode launches of `job` on st (see api.cpp).
+int enqueue_job(aceapex_ctx* c, const JobDev& job, const LaunchPlan& lp, uint32_t n_counters, int* errs,
+                uint32_t n_errs, cudaStream_t st, cudaEvent_t* ev);
+
+}  // namespace acx

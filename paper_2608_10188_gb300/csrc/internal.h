@@ -32,7 +32,8 @@ struct BlockDev {
     uint32_t s_off[4];     // offset of each decoded stream inside the block's scratch region
     uint8_t s_K[4];        // rANS lanes
     uint32_t span_base;    // first pending-span slot of the block (n_tok + kSpanSlack slots per block)
-    uint32_t pad[2];
+    uint32_t dep_off;      // the block's dependency list: deps[dep_off, dep_off + n_deps) (archives with lists)
+    uint32_t n_deps;
 };
 static_assert(sizeof(BlockDev) % 16 == 0, "BlockDev alignment");
 
@@ -48,6 +49,24 @@ constexpr uint32_t kPiece = 32;
 constexpr uint32_t kSpanSlack = kBlock / kPiece;  // pieces a block may add beyond one per token
 struct alignas(16) SpanRec {
     uint32_t x, y, z, w;
+};
+
+// One work item of a job that decodes chosen blocks of an archive (range
+// decodes, serving ticks): the block, and where its pending pieces and
+// decoded streams go in the job's scratch.
+struct ItemDev {
+    uint32_t block;
+    uint32_t slot;            // output slot of the block
+    uint32_t span_base;       // first pending-piece slot (n_tok + kSpanSlack slots)
+    uint32_t pad;
+    uint64_t scratch;         // offset of the block's decoded streams
+};
+constexpr uint32_t kNoSlot = 0xffffffffu;  // slot-table entry of a block not in the output
+
+// One region to copy out of the block slots after a subset decode.
+struct GatherReq {
+    uint8_t* dst;             // device destination (len bytes)
+    uint64_t start, len;      // original byte range
 };
 
 // One archive inside a decode job.
@@ -66,14 +85,23 @@ struct ArcJob {
     uint32_t min_match;
     uint32_t item_base;       // first item index of this archive in the job's item space
     uint32_t pad;
+    const uint32_t* deps;     // dependency lists (BlockDev::dep_off / n_deps), or nullptr: when present,
+                              // every source outside a block must lie in a listed block
+    // Subset decodes (both nullptr for whole-archive jobs, where item i is
+    // block lo + i with the plan's offsets and block b lives at out + b*kBlock):
+    const ItemDev* items;     // item i (counted from item_base) of this archive; hi - lo = item count
+    uint32_t* slot;           // block -> output slot: block b's bytes at out + slot[b]*kBlock, its
+                              // pending count at npend[slot[b]] and bitmap at pmap + slot[b]*512;
+                              // the entropy stage writes the entries of the job's items
 };
 
-constexpr uint32_t kMaxArcsPerJob = 4000;
+constexpr uint32_t kMaxArcsPerJob = 3000;  // rANS tickets [3, 3 + n_arcs) stay below kTrace
 constexpr uint32_t kTrace = 3800;        // [kTrace + 3r]: cross-block round r list size, start time lo, hi
 constexpr uint32_t kTraceRounds = 64;
 constexpr uint32_t kListCnt = 4086;      // [kListCnt + 0/1]: entries of the two cross-block work lists
 constexpr uint32_t kBarCount = 4088;     // grid barrier arrivals
 constexpr uint32_t kBarGen = 4089;       // grid barrier generation
+constexpr uint32_t kStatPendBytes = 4090; // [4090, 4091]: u64 bytes of the pending pieces
 constexpr uint32_t kStatPending = 4093;
 constexpr uint32_t kStatPolls = 4094;    // cross-block rounds
 constexpr uint32_t kCounterWords = 4096;
@@ -86,6 +114,7 @@ struct JobDev {
     uint32_t* counters;       // [1] local ticket, [2] external ticket, [3 + a] rANS ticket of archive a,
                               // [kStatPending] pending spans, [kStatPolls] empty cross-block polls
     int* err;                 // first error status (0 = ok)
+    int* arc_err;             // per archive: first error status of that archive (batched jobs), or nullptr
     uint64_t timeout_ns;
     uint32_t max_tok;         // shared-memory sizing of the assembly kernel
     uint32_t max_lenb;

@@ -1,0 +1,31 @@
+// Host-side launchers of the decode kernels (defined in the .cu files).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace acx {
+
+// Clears counters[0, n_counters) and the statistics/list/barrier words, and
+// errs[0, n_errs) (status words that the kernels set).
+cudaError_t launch_prologue(uint32_t* counters, uint32_t n_counters, cudaStream_t st, int* errs = nullptr,
+                            uint32_t n_errs = 0);
+cudaError_t launch_rans(const JobDev& job, int grid, cudaStream_t st);
+cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st);
+// Cooperative launch (every CTA resident); recorded as a cooperative kernel
+// node when the stream is being captured into a graph.
+cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st);
+cudaError_t launch_plain(const JobDev& job, int grid, cudaStream_t st);
+size_t local_smem_bytes(uint32_t T, uint32_t LB);
+int rans_occupancy();
+int local_occupancy(size_t smem);
+int external_occupancy();
+int plain_occupancy();
+// Copy regions out of block slots (block a at out + slot[a]*kBlock): the one
+// request `one` (list == nullptr) or list[0, n_req); max_len sizes the grid.
+cudaError_t launch_gather(const GatherReq* one, const GatherReq* list, uint32_t n_req, uint64_t max_len,
+                          const uint8_t* out, const uint32_t* slot, cudaStream_t st);
+
+}  // namespace acx

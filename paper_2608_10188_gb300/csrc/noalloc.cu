@@ -19,17 +19,9 @@
 
 #include "../../include/aceapex.h"
 #include "common.cuh"
+#include "launch.h"
 
 namespace acx {
-
-cudaError_t launch_prologue(uint32_t* counters, uint32_t n_counters, cudaStream_t st);
-cudaError_t launch_rans(const JobDev& job, int grid, cudaStream_t st);
-cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st);
-cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st);
-size_t local_smem_bytes(uint32_t T, uint32_t LB);
-int rans_occupancy();
-int local_occupancy(size_t smem);
-int external_occupancy();
 
 namespace {
 

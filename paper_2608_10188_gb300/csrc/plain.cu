@@ -7,6 +7,7 @@
 // cross-block pass finishes it and the two variants differ only in the
 // paper's two levers: scan parse and periodic fill.
 #include "common.cuh"
+#include "launch.h"
 
 namespace acx {
 
@@ -25,13 +26,14 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain(JobDev job) {
         if (item >= job.n_items) return;
         const int a = find_arc(job, item);
         const ArcJob J = load_arc(job, a);
-        const uint32_t b = J.lo + (item - J.item_base);
+        const ItemRef ir = item_ref(J, item - J.item_base);
+        const uint32_t b = ir.blk;
         const BlockDev& bd = J.blk[b];
         const uint64_t B = (uint64_t)b * kBlock;
         for (uint32_t i = lane; i < kBlock / 32; i += 32) pend[i] = 0;
         __syncwarp();
         if (lane == 0) {
-            const uint8_t* scr = J.scratch + bd.scratch;
+            const uint8_t* scr = J.scratch + ir.scratch;
             const uint8_t* cmd = scr + bd.s_off[kCmd];
             const uint8_t* lb = scr + bd.s_off[kLen];
             const uint8_t* off = scr + bd.s_off[kOff];
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain(JobDev job) {
             uint64_t hist[4] = {1, 2, 3, 4};
             const uint64_t E = B + bd.raw_len;
             uint64_t pos = B;
-            uint32_t lp = 0, ni = 0, vp = 0, np = 0;
+            uint32_t lp = 0, ni = 0, vp = 0, np = 0, pb = 0;
             bool bad = false;
             for (uint32_t i = 0; i < n && !bad; i++) {
                 uint32_t v[2] = {0, 0};
@@ -85,6 +87,12 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain(JobDev job) {
                     break;
                 }
                 if (ML < J.min_match || ML > E - pos) { bad = true; break; }
+                if (J.deps && src < B) {  // blocks read outside this block must be listed
+                    const uint64_t d = pos - src, e = src + (d < ML ? d : ML);
+                    for (uint64_t a = src >> 14; a <= (e - 1) >> 14 && a < b && !bad; a++)
+                        bad = !listed(J.deps + bd.dep_off, bd.n_deps, (uint32_t)a);
+                    if (bad) break;
+                }
                 const uint32_t o = (uint32_t)(pos - B);
                 // in-block source whose bytes are all final: copy byte by byte now
                 bool local = src >= B;
@@ -98,30 +106,38 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain(JobDev job) {
                     for (uint32_t j = 0; j < ML; j++) sout[o + j] = sout[src - B + j];
                 } else {
                     for (uint32_t w = o >> 5; w <= ((o + ML - 1) >> 5); w++) pend[w] |= range_mask(w, o, o + ML);
-                    np += emit_pieces(J.spans + bd.span_base + np, o, src, ML, pos - src);
+                    np += emit_pieces(J.spans + ir.span_base + np, o, src, ML, pos - src);
+                    pb += ML;
                 }
                 pos += ML;
             }
             if (!bad && (pos != E || lp != n_lit || ni != n_new || vp != LB)) bad = true;
             if (bad) {
-                set_err(job.err, kErrCorrupt, kStagePlain << 24, b);
+                set_err_arc(job, a, kErrCorrupt, kStagePlain << 24, b);
                 np = 0;
+                pb = 0;
             }
             misc[0] = np;
+            misc[1] = pb;
         }
         __syncwarp();
-        const uint32_t np = misc[0];
-        uint8_t* gout = J.out + B;
+        const uint32_t np = misc[0], pbytes = misc[1];
+        uint8_t* gout = J.out + (uint64_t)ir.slot * kBlock;
         const uint32_t R = bd.raw_len, nv = R / 16;
         for (uint32_t i = lane; i < nv; i += 32) reinterpret_cast<uint4*>(gout)[i] = reinterpret_cast<uint4*>(sout)[i];
         for (uint32_t x = 16 * nv + lane; x < R; x += 32) gout[x] = sout[x];
         {
-            uint32_t* gp = J.pmap + (uint64_t)b * (kBlock / 32);  // written for every block
-            for (uint32_t i = lane; i < kBlock / 32; i += 32) gp[i] = pend[i];
+            // written for every block; all clear when nothing is pending (also for a
+            // corrupt block, so other blocks never wait on its bytes)
+            uint32_t* gp = J.pmap + (uint64_t)ir.slot * (kBlock / 32);
+            for (uint32_t i = lane; i < kBlock / 32; i += 32) gp[i] = np ? pend[i] : 0u;
         }
         if (lane == 0) {
-            J.npend[b] = np;
-            if (np) atomicAdd(&job.counters[kStatPending], np);
+            J.npend[ir.slot] = np;
+            if (np) {
+                atomicAdd(&job.counters[kStatPending], np);
+                atomicAdd(reinterpret_cast<unsigned long long*>(job.counters + kStatPendBytes), (unsigned long long)pbytes);
+            }
         }
         __syncwarp();
     }

@@ -60,6 +60,8 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why) {
         }
     }
     P->blk.assign(P->n_blocks, BlockDev{});
+    P->has_deps = off_deps != 0;
+    P->deps.clear();
     P->max_tok = 1;
     P->max_lenb = 1;
     P->tokens = 0;
@@ -73,19 +75,23 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why) {
         const uint64_t R = P->total - B < kBlock ? P->total - B : kBlock;
         if (raw != R) return fail("block raw length mismatch");
         if (off_deps == 0 && (dep_off || n_deps)) return fail("dependency list without a dependency section");
+        BlockDev& bd = P->blk[b];
         if (off_deps) {
             if (off_deps > len || (len - off_deps) / 4 < (uint64_t)dep_off + n_deps) return fail("deps out of bounds");
             uint32_t prev = 0;
+            bd.dep_off = (uint32_t)P->deps.size();
+            bd.n_deps = n_deps;
             for (uint32_t k = 0; k < n_deps; k++) {
                 const uint32_t id = rd32(a + off_deps + 4 * ((uint64_t)dep_off + k));
                 if (id >= b || (k && id <= prev)) return fail("dependency list not ascending below the block");
                 prev = id;
+                P->deps.push_back(id);
             }
+            if (P->deps.size() >= (1ull << 32)) return fail("dependency lists too long");
         }
         if ((poff & 15) || (plen & 15) || plen < 48) return fail("payload misaligned");
         if (poff > len || len - poff < plen) return fail("payload out of bounds");
         const uint8_t* pay = a + poff;
-        BlockDev& bd = P->blk[b];
         bd.payload = poff;
         bd.raw_len = raw;
         bd.n_tok = n_tok;

@@ -16,6 +16,8 @@ struct Plan {
     bool table_ok[4];
     std::vector<uint32_t> dtab;   // 4 x 4096 decode entries
     std::vector<BlockDev> blk;
+    bool has_deps = false;        // the archive carries dependency lists
+    std::vector<uint32_t> deps;   // all lists, block b's at [blk[b].dep_off, + blk[b].n_deps)
 };
 
 // Validate the archive structure and build its plan.  Returns 0 or -2
@@ -24,7 +26,7 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why);
 
 // Library encoder (format v1); out is malloc'ed.
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   int latest, uint32_t max_depth, int short_latest, uint8_t** out, uint64_t* out_len);
+                   int latest, uint32_t max_depth, int short_latest, int deps, uint8_t** out, uint64_t* out_len);
 
 // FNV-1a 64.
 uint64_t fnv1a64(const uint8_t* p, uint64_t n);

@@ -17,6 +17,7 @@
 //  * ring residency is checked once per 4 steps, not per step.
 // Every wait is bounded by %globaltimer.
 #include "common.cuh"
+#include "launch.h"
 
 namespace acx {
 
@@ -278,14 +279,17 @@ __device__ void copy_stored(const uint8_t* __restrict__ src, uint8_t* __restrict
 }
 
 // Start of a decode call: every ticket and statistic restarts at zero.
-__global__ void k_prologue(uint32_t* counters, uint32_t n_counters) {
+__global__ void k_prologue(uint32_t* counters, uint32_t n_counters, int* errs, uint32_t n_errs) {
     for (uint32_t i = threadIdx.x; i < n_counters; i += blockDim.x) counters[i] = 0;
+    for (uint32_t i = threadIdx.x; i < n_errs; i += blockDim.x) errs[i] = 0;
     if (threadIdx.x == 0) {
         counters[kStatPending] = 0;
         counters[kStatPolls] = 0;
         counters[kListCnt] = 0;
         counters[kListCnt + 1] = 0;
         counters[kBarCount] = 0;
+        counters[kStatPendBytes] = 0;
+        counters[kStatPendBytes + 1] = 0;
     }
 }
 
@@ -326,10 +330,12 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
             if (lane == 0) it = atomicAdd(&tickets[a], 1u);
             it = __shfl_sync(ACX_FULL, it, 0);
             if (it >= n_a) break;
-            const uint32_t b = J.lo + it;
+            const ItemRef ir = item_ref(J, it);
+            const uint32_t b = ir.blk;
+            if (J.items && lane == 0) J.slot[b] = ir.slot;  // read by the cross-block pass
             const BlockDev& bd = J.blk[b];
             const uint8_t* pay = J.arc + bd.payload;
-            uint8_t* scr = J.scratch + bd.scratch;
+            uint8_t* scr = J.scratch + ir.scratch;
             bool ok = true;
             int fs = 0;
             // the three short streams together when they fit one warp
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
                     copy_stored(body, o, n, lane);
                 }
             }
-            if (!ok && lane == 0) set_err(job.err, kErrCorrupt, (kStageRans << 24) | fs, b);
+            if (!ok && lane == 0) set_err_arc(job, a, kErrCorrupt, (kStageRans << 24) | fs, b);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -376,8 +382,8 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
 
 size_t rans_smem_bytes() { return sizeof(RansSmem); }
 
-cudaError_t launch_prologue(uint32_t* counters, uint32_t n_counters, cudaStream_t st) {
-    k_prologue<<<1, 128, 0, st>>>(counters, n_counters);
+cudaError_t launch_prologue(uint32_t* counters, uint32_t n_counters, cudaStream_t st, int* errs, uint32_t n_errs) {
+    k_prologue<<<1, 128, 0, st>>>(counters, n_counters, errs, n_errs);
     return cudaGetLastError();
 }
 

@@ -21,31 +21,40 @@ EXPORTED = [
     "aceapex_status_string", "aceapex_last_error", "aceapex_ctx_create", "aceapex_ctx_destroy",
     "aceapex_ctx_set_params", "aceapex_encode", "aceapex_free", "aceapex_archive_open", "aceapex_archive_close",
     "aceapex_archive_get_info", "aceapex_decode_all", "aceapex_decode_all_async", "aceapex_sync",
-    "aceapex_decode_host", "aceapex_archive_check", "aceapex_decode_noalloc",
+    "aceapex_decode_host", "aceapex_archive_check", "aceapex_decode_noalloc", "aceapex_batch_create",
+    "aceapex_batch_run_async", "aceapex_batch_wait", "aceapex_batch_run", "aceapex_batch_destroy",
+    "aceapex_batch_decode", "aceapex_decode_range",
 ]
+BATCH_GRAPH = 1
 
 
 class EncParams(ctypes.Structure):
     _fields_ = [("no_rep", ctypes.c_int), ("min_match", ctypes.c_uint32), ("max_lanes", ctypes.c_uint32),
                 ("threads", ctypes.c_int), ("latest_source", ctypes.c_int),
-                ("max_depth", ctypes.c_uint32), ("short_latest", ctypes.c_int)]
+                ("max_depth", ctypes.c_uint32), ("short_latest", ctypes.c_int), ("deps", ctypes.c_int)]
 
 
 class DecParams(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("timeout_us", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("rans_ctas_per_sm", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("ms_total", ctypes.c_double), ("ms_ans", ctypes.c_double), ("ms_parse", ctypes.c_double),
                 ("ms_copy", ctypes.c_double), ("blocks", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
-                ("pending_spans", ctypes.c_uint64), ("wait_polls", ctypes.c_uint64)]
+                ("pending_spans", ctypes.c_uint64), ("wait_polls", ctypes.c_uint64),
+                ("pending_bytes", ctypes.c_uint64)]
 
 
 class ArchiveInfo(ctypes.Structure):
     _fields_ = [("total_size", ctypes.c_uint64), ("n_blocks", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("min_match", ctypes.c_uint32), ("max_tokens", ctypes.c_uint32),
                 ("archive_bytes", ctypes.c_uint64), ("tokens", ctypes.c_uint64)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("arc", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("out_cap", ctypes.c_uint64),
+                ("status", ctypes.c_int)]
 
 
 class AceapexError(RuntimeError):
@@ -87,6 +96,13 @@ def load(path: str | None = None):
     L.aceapex_decode_all_async.argtypes = [vp, vp, vp, u64, vp]
     L.aceapex_sync.argtypes = [vp, vp]
     L.aceapex_decode_host.argtypes = [vp, vp, vp, u64, vp, u64, vp, c.POINTER(Stats)]
+    L.aceapex_batch_create.argtypes = [vp, c.POINTER(BatchItem), c.c_int, u32, c.POINTER(vp)]
+    L.aceapex_batch_run_async.argtypes = [vp, vp]
+    L.aceapex_batch_wait.argtypes = [vp, vp, c.POINTER(BatchItem), c.POINTER(Stats)]
+    L.aceapex_batch_run.argtypes = [vp, vp, c.POINTER(BatchItem), c.POINTER(Stats)]
+    L.aceapex_batch_destroy.argtypes = [vp]
+    L.aceapex_decode_range.argtypes = [vp, vp, u64, u64, vp, vp, c.POINTER(Stats)]
+    L.aceapex_batch_decode.argtypes = [vp, c.POINTER(BatchItem), c.c_int, vp, c.POINTER(Stats)]
     for name in EXPORTED:
         if name not in ("aceapex_status_string", "aceapex_last_error", "aceapex_free"):
             getattr(L, name).restype = c.c_int
@@ -103,13 +119,14 @@ def _check(rc, ctx=None, what=""):
 
 
 def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, threads: int = 0,
-           latest_source: bool = False, max_depth: int = 0, short_latest: bool = False) -> bytes:
+           latest_source: bool = False, max_depth: int = 0, short_latest: bool = False, deps: bool = False) -> bytes:
     """aceapex_encode on host bytes (numpy uint8 array or bytes)."""
     import numpy as np
     L = load()
     a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data,
                              dtype=np.uint8)
-    p = EncParams(int(no_rep), min_match, max_lanes, threads, int(latest_source), max_depth, int(short_latest))
+    p = EncParams(int(no_rep), min_match, max_lanes, threads, int(latest_source), max_depth, int(short_latest),
+                  int(deps))
     ptr = ctypes.c_void_p()
     n = ctypes.c_uint64()
     _check(L.aceapex_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(p), ctypes.byref(ptr),
@@ -123,16 +140,18 @@ def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, 
 class Context:
     """aceapex_ctx on one CUDA device."""
 
-    def __init__(self, device: int = 0, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0):
+    def __init__(self, device: int = 0, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0,
+                 rans_ctas_per_sm: int = 0):
         L = load()
         self._L = L
-        self.params = DecParams(variant, timeout_us, ctas_per_sm, 0)
+        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm)
         h = ctypes.c_void_p()
         _check(L.aceapex_ctx_create(device, ctypes.byref(self.params), ctypes.byref(h)), None, "ctx_create")
         self.h = h
 
-    def set_params(self, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0):
-        self.params = DecParams(variant, timeout_us, ctas_per_sm, 0)
+    def set_params(self, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0,
+                   rans_ctas_per_sm: int = 0):
+        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm)
         _check(self._L.aceapex_ctx_set_params(self.h, ctypes.byref(self.params)), self.h, "set_params")
 
     def close(self):
@@ -206,6 +225,17 @@ def decode_all(ctx: Context, arc: Archive, d_out: int, out_cap: int, stream: int
     return rc
 
 
+def decode_range(ctx: Context, arc: Archive, start: int, length: int, d_out: int, stream: int = 0,
+                 stats: bool = False):
+    """aceapex_decode_range: bytes [start, start+length) into d_out; returns
+    the status (and a Stats dict when stats=True)."""
+    st = Stats() if stats else None
+    rc = ctx._L.aceapex_decode_range(ctx.h, arc.h, start, length, d_out, stream, ctypes.byref(st) if st else None)
+    if stats:
+        return rc, {k: getattr(st, k) for k, _ in Stats._fields_}
+    return rc
+
+
 def decode_all_async(ctx: Context, arc: Archive, d_out: int, out_cap: int, stream: int = 0) -> int:
     return ctx._L.aceapex_decode_all_async(ctx.h, arc.h, d_out, out_cap, stream)
 
@@ -225,3 +255,69 @@ def decode_noalloc(d_arc: int, arc_len: int, d_out: int, out_cap: int, stream: i
     already in device memory, using only the library's static scratch; for
     callers that must not allocate.  Returns the status."""
     return load().aceapex_decode_noalloc(d_arc, arc_len, d_out, out_cap, stream)
+
+
+def _items(entries):
+    arr = (BatchItem * max(len(entries), 1))()
+    for i, (arc, d_out, out_cap) in enumerate(entries):
+        arr[i].arc = arc.h.value if isinstance(arc.h, ctypes.c_void_p) else arc.h
+        arr[i].d_out = d_out
+        arr[i].out_cap = out_cap
+        arr[i].status = 0
+    return arr
+
+
+class Batch:
+    """aceapex_batch: a reusable decode of many archives by one set of
+    launches (captured into a CUDA graph when graph=True).  entries: a list of
+    (Archive, d_out, out_cap)."""
+
+    def __init__(self, ctx: Context, entries, graph: bool = True):
+        self.ctx = ctx
+        self.n = len(entries)
+        self._keep = [e[0] for e in entries]
+        self._items = _items(entries)
+        h = ctypes.c_void_p()
+        _check(ctx._L.aceapex_batch_create(ctx.h, self._items, self.n, BATCH_GRAPH if graph else 0, ctypes.byref(h)),
+               ctx.h, "batch_create")
+        self.h = h
+
+    def run_async(self, stream: int = 0) -> int:
+        return self.ctx._L.aceapex_batch_run_async(self.h, stream)
+
+    def wait(self, stream: int = 0, stats: bool = False):
+        """Returns (status, per-item statuses[, stats dict])."""
+        st = Stats() if stats else None
+        rc = self.ctx._L.aceapex_batch_wait(self.h, stream, self._items, ctypes.byref(st) if st else None)
+        per = [self._items[i].status for i in range(self.n)]
+        if stats:
+            return rc, per, {k: getattr(st, k) for k, _ in Stats._fields_}
+        return rc, per
+
+    def run(self, stream: int = 0, stats: bool = False):
+        rc = self.run_async(stream)
+        if rc != OK:
+            return (rc, [rc] * self.n, None) if stats else (rc, [rc] * self.n)
+        return self.wait(stream, stats)
+
+    def close(self):
+        if self.h:
+            self.ctx._L.aceapex_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_decode(ctx: Context, entries, stream: int = 0, stats: bool = False):
+    """aceapex_batch_decode (one-shot): returns (status, per-item statuses[, stats])."""
+    items = _items(entries)
+    st = Stats() if stats else None
+    rc = ctx._L.aceapex_batch_decode(ctx.h, items, len(entries), stream, ctypes.byref(st) if st else None)
+    per = [items[i].status for i in range(len(entries))]
+    if stats:
+        return rc, per, {k: getattr(st, k) for k, _ in Stats._fields_}
+    return rc, per

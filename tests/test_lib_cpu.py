@@ -97,3 +97,40 @@ def test_host_validation_rejects_structural_corruption(acx):
     a = build_archive(toks)
     acx.archive_check(a)
     assert oracle.decode_status(a, verify=False)[0] == oracle.E_CORRUPT
+
+
+def read_deps(arc):
+    """(off_deps, per-block dependency lists) from the header and index."""
+    import struct
+    nb = struct.unpack_from("<I", arc, 24)[0]
+    off_idx, off_deps = struct.unpack_from("<QQ", arc, 40)
+    lists = []
+    for b in range(nb):
+        dep_off, n_deps = struct.unpack_from("<II", arc, off_idx + 40 * b + 20)
+        lists.append([struct.unpack_from("<I", arc, off_deps + 4 * (dep_off + k))[0] for k in range(n_deps)])
+    return off_deps, lists
+
+
+@pytest.mark.parametrize("kind", ["dna", "text"])
+@pytest.mark.parametrize("no_rep", [False, True])
+def test_library_dependency_lists_are_the_blocks_read(acx, kind, no_rep):
+    """With deps=True each block lists exactly the earlier blocks its matches
+    read (a self-overlapping match reads one period), as found by the oracle's
+    own parse; without, the archive has no dependency section."""
+    data = synth.corpus(kind, 700_000 + 77, 8)
+    arc = acx.encode(data, no_rep=no_rep, deps=True)
+    assert np.array_equal(oracle.decode(arc), data)
+    off, lists = read_deps(arc)
+    assert off != 0
+    for b, got in enumerate(lists):
+        t = oracle.parse_block(arc, b)
+        want = set()
+        for s, m, d in zip(t["src"].tolist(), t["ml"].tolist(), t["dst"].tolist()):
+            if m == 0:
+                continue
+            e = s + min(m, d - s)
+            want.update(a for a in range(s // 16384, (e - 1) // 16384 + 1) if a < b)
+        assert got == sorted(want), b
+    plain = acx.encode(data, no_rep=no_rep)
+    assert read_deps(plain)[0] == 0
+    assert len(plain) < len(arc)
