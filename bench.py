@@ -45,16 +45,22 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="single", choices=["single", "batch"],
-                   help="single: one archive (--corpus); batch: the 96-archive mixed batch")
+    p.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+                   help="single: one archive (--corpus); batch: the 96-archive mixed batch; serve: region server")
     p.add_argument("--corpus", default="dna", choices=["dna", "text"])
     p.add_argument("--size", type=int, default=0)
     p.add_argument("--encoding", default="history", choices=["history", "no_rep"])
     p.add_argument("--variant", default="fast", choices=["fast", "plain"])
     p.add_argument("--lanes", type=int, default=32)
+    p.add_argument("--max-depth", type=int, default=0,
+                   help="encoder chain-depth cap (0: the library default of 16)")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="batch: plain launches instead of a graph replay")
+    p.add_argument("--serve-gib", type=int, default=16, help="serve: genome size in GiB (256 MiB chromosomes)")
+    p.add_argument("--serve-rate", type=float, default=20000.0, help="serve: Poisson arrivals per second")
+    p.add_argument("--serve-seconds", type=float, default=10.0, help="serve: measured seconds (after 2 s warm-up)")
+    p.add_argument("--cache-gib", type=float, default=4.0, help="serve: decoded-block cache in GiB")
     p.add_argument("--cache-dir", default=os.environ.get("ACEAPEX_CACHE", "/tmp/aceapex_bench_cache"))
     return p.parse_args()
 
@@ -79,13 +85,13 @@ def get_archive(args, acx):
     the local disk between runs of the same source version)."""
     size, _ = workload(args)
     data = synth.corpus(args.corpus, size, 0)
-    key = f"{args.corpus}-{size}-s0-{args.encoding}-k{args.lanes}-{encoder_key()}.acx"
+    key = f"{args.corpus}-{size}-s0-{args.encoding}-k{args.lanes}-d{args.max_depth}-{encoder_key()}.acx"
     path = os.path.join(args.cache_dir, key)
     arc = None
     if os.path.exists(path):
         arc = open(path, "rb").read()
     if arc is None:
-        arc = acx.encode(data, no_rep=args.encoding == "no_rep", max_lanes=args.lanes)
+        arc = acx.encode(data, no_rep=args.encoding == "no_rep", max_lanes=args.lanes, max_depth=args.max_depth)
         try:
             os.makedirs(args.cache_dir, exist_ok=True)
             tmp = path + f".{os.getpid()}"
@@ -382,6 +388,127 @@ def run_batch(args, dist):
     ctx.close()
 
 
+def serve_archive(args, acx):
+    """The serving workload's archive: a synthetic genome of serve_gib GiB made
+    of 256 MiB chromosomes (chromosome i from seed 5000+i, generated in
+    parallel), encoded with the 4-entry history, one parse per chromosome."""
+    from concurrent.futures import ThreadPoolExecutor
+    chrom = 256 << 20
+    size = args.serve_gib << 30
+    n_chrom = (size + chrom - 1) // chrom
+    data = np.empty(size, dtype=np.uint8)
+
+    def gen(i):
+        n = min(chrom, size - i * chrom)
+        synth.dna(n, 5000 + i, out=data[i * chrom:i * chrom + n])
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        list(ex.map(gen, range(n_chrom)))
+    key = f"serve-{size}-chrom{chrom}-k{args.lanes}-{encoder_key()}.acx"
+    arc = cached_encode(args, acx, data, key, max_lanes=args.lanes, segment=chrom, threads=os.cpu_count() or 4)
+    return data, arc
+
+
+def run_serve(args, dist):
+    """Region serving under open-loop Poisson load: requests with lognormal
+    lengths (median 16 KiB, sigma 1, clipped to [4 KiB, 1 MiB]) at uniform
+    starts arrive at serve_rate per second for 2 s of warm-up plus
+    serve_seconds measured; each is decoded through its byte-level closure
+    minus the device cache.  Latency = arrival -> completion seen by the
+    server; the line reports p50/p99 of the measured window."""
+    import torch
+
+    import paper_2608_10188_gb300 as acx
+    acx.build.build()
+    dev = dist["local"]
+    torch.cuda.set_device(dev)
+    device = f"cuda:{dev}"
+    t_setup = time.perf_counter()
+    data, arc = serve_archive(args, acx)
+    total = data.size
+    ctx = acx.Context(dev)
+    h_arc = np.frombuffer(arc, dtype=np.uint8).copy()
+    d_arc = torch.from_numpy(h_arc).to(device)
+    A = acx.Archive(ctx, d_arc.data_ptr(), h_arc, h_arc.size)
+    t = time.perf_counter()
+    A.build_index()
+    index_s = time.perf_counter() - t
+    srv = acx.Server(ctx, A, cache_bytes=int(args.cache_gib * (1 << 30)))
+    warm = 2.0
+    rng = np.random.default_rng(55)
+    horizon = warm + args.serve_seconds
+    n_req = int(args.serve_rate * horizon * 1.2) + 16
+    at = np.cumsum(rng.exponential(1.0 / args.serve_rate, n_req))
+    at = at[at < horizon]
+    n_req = at.size
+    lens = np.clip(rng.lognormal(np.log(16384), 1.0, n_req), 4096, 1 << 20).astype(np.int64)
+    starts = (rng.random(n_req) * (total - lens + 1)).astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    arena = torch.empty(int(offs[-1]), dtype=torch.uint8, device=device)
+    ptrs = (arena.data_ptr() + offs[:-1]).astype(np.uint64)
+    setup_s = time.perf_counter() - t_setup
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t0 = srv.now_ns() + 50_000_000
+    at_ns = (t0 + at * 1e9).astype(np.int64)
+    ids = srv.submit_many(starts.astype(np.uint64), lens.astype(np.uint64), ptrs, at_ns)
+    rc = srv.drain(int((horizon + 120) * 1000))
+    clk = clocks.stop()
+    if rc != 0:
+        raise RuntimeError(f"server drain: {rc} {srv.last_error()}")
+    comps = srv.poll(n_req + 16)
+    st_all = srv.stats()
+    by_id = {c["id"]: c for c in comps}
+    idx = {int(i): k for k, i in enumerate(ids)}
+    lat, win_bytes, closure, t_last = [], 0, [], 0.0
+    bad = [c for c in comps if c["status"] != 0]
+    if bad:
+        raise RuntimeError(f"{len(bad)} requests failed, first status {bad[0]['status']}")
+    for c in comps:
+        k = idx[c["id"]]
+        if at[k] >= warm:
+            lat.append(c["latency_us"])
+            win_bytes += int(lens[k])
+            closure.append(c["closure_blocks"])
+            t_last = max(t_last, at[k] + c["latency_us"] / 1e6)
+    lat = np.array(lat)
+    # correctness: a sample of the requests against the generator's bytes
+    smp = rng.choice(n_req, size=min(2000, n_req), replace=False)
+    for k in smp:
+        o, s, l = int(offs[k]), int(starts[k]), int(lens[k])
+        if not np.array_equal(arena[o:o + l].cpu().numpy(), data[s:s + l]):
+            raise RuntimeError(f"request {k} differs from the input")
+    window = t_last - warm
+    gbs = win_bytes / window / 1e9 if window > 0 else 0.0
+    line = {
+        "metric": "p99 region latency under load", "value": round(float(np.percentile(lat, 99)), 1), "unit": "us",
+        "n_gpus": 1, "steps": int(lat.size), "warmup": int(n_req - lat.size),
+        "ms_per_step": round(float(np.mean(lat)) / 1e3, 4), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator; 256 MiB chromosomes)",
+        "config": {"workload": f"region server over a {args.serve_gib} GiB synthetic genome ({total:,} B, "
+                               f"{len(arc):,} B compressed, held on the device), {args.cache_gib:g} GiB decoded-block "
+                               f"cache; Poisson {args.serve_rate:g} requests/s, 2 s warm-up + {args.serve_seconds:g} s",
+                   "request_lengths": "lognormal median 16 KiB, sigma 1, clipped to [4 KiB, 1 MiB]; uniform starts",
+                   "closure": "byte-level (match index built in %.2f s)" % index_s, "setup_s": round(setup_s, 1)},
+        "latency_us": {"p50": round(float(np.percentile(lat, 50)), 1), "p90": round(float(np.percentile(lat, 90)), 1),
+                       "p99": round(float(np.percentile(lat, 99)), 1), "max": round(float(lat.max()), 1),
+                       "mean": round(float(lat.mean()), 1)},
+        "throughput": {"value": round(gbs, 3), "unit": "GB/s", "requests_per_s": round(lat.size / window, 1)},
+        "closure_blocks": {"mean": round(float(np.mean(closure)), 1), "p50": float(np.percentile(closure, 50)),
+                           "p99": float(np.percentile(closure, 99))},
+        "server": {"ticks": st_all["ticks"], "blocks_decoded": st_all["blocks_decoded"],
+                   "blocks_hit": st_all["blocks_hit"],
+                   "hit_rate": round(st_all["blocks_hit"] / max(1, st_all["blocks_hit"] + st_all["blocks_decoded"]), 4),
+                   "refused": st_all["refused"]},
+        "verified": f"{smp.size} sampled requests equal the generator's bytes",
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    srv.close()
+    A.close()
+    ctx.close()
+
+
 def init_dist(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -406,6 +533,10 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, dist)
+        return
+    if args.workload == "serve":
+        if dist["rank"] == 0:
+            run_serve(args, dist)
         return
     import torch
 
@@ -509,6 +640,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded generator; stands in for chr1 hg38)",
             "config": {"workload": wname, "encoding": args.encoding, "variant": args.variant,
+                       "max_depth": args.max_depth or 16,
                        "rans_lanes": args.lanes, "block_size": 16384, "blocks": info["n_blocks"],
                        "tokens": info["tokens"], "archive_bytes": len(arc),
                        "ratio": round(size / len(arc), 4),

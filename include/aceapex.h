@@ -79,6 +79,10 @@ typedef struct {
                             read), so range decodes touch only a block's dependency closure
                             (paper, Random Access at Scale); 0 (default): no lists, a range
                             decode then covers every block up to the range */
+    uint64_t segment;    /* 0 (default): one parse over the whole input.  Else a multiple of
+                            16 KiB: the input is parsed as independent segments of this size
+                            (sources stay inside their segment, like a genome's chromosomes),
+                            in parallel on `threads` threads, into one archive */
 } aceapex_enc_params;
 
 /* Decoder variants. */
@@ -169,12 +173,26 @@ int aceapex_decode_all_async(aceapex_ctx* ctx, aceapex_archive* arc, void* d_out
 int aceapex_sync(aceapex_ctx* ctx, void* stream);
 
 /*
+ * Build the archive's match index: a parse-only pass on the device (entropy
+ * stage without literals, then the token scans) lists every match's
+ * destination, length and absolute source; the index is kept in host memory
+ * with the archive (about 12 bytes per match) until aceapex_archive_close.
+ * With it, range decodes and servers follow the byte-level closure of a
+ * region (paper, Random Access at Scale and "The byte-level refutation": a
+ * byte needs only the bytes it was copied from) instead of whole blocks.
+ * Synchronous; uses the context's stream-independent scratch.
+ */
+int aceapex_archive_index(aceapex_ctx* ctx, aceapex_archive* arc);
+
+/*
  * Decode the original bytes [start, start + len) into d_out (device pointer,
- * len bytes).  Paper, Random Access at Scale: only the blocks the region
- * covers and their block-dependency closure (the earlier blocks their
- * matches read, transitively) are decoded — through the archive's dependency
- * lists when it has them (aceapex_enc_params.deps), else every block up to
- * the region's last — into context scratch, and the region is gathered out.
+ * len bytes).  Paper, Random Access at Scale: only what the region depends on
+ * is decoded, into context scratch, and the region is gathered out.  With a
+ * match index (aceapex_archive_index) that is the byte-level closure: the
+ * matches writing the region's bytes, their source windows, and so on, the
+ * other matches of those blocks being left undone.  Otherwise it is the
+ * block-level closure: through the archive's dependency lists when it has
+ * them (aceapex_enc_params.deps), else every block up to the region's last.
  * A source outside its block's dependency list is ACEAPEX_E_CORRUPT.
  * Returns ACEAPEX_E_RANGE when the region leaves the archive.  Synchronises
  * `stream`; stats (may be NULL): blocks = closure size, bytes = len, ms_copy
@@ -182,6 +200,70 @@ int aceapex_sync(aceapex_ctx* ctx, void* stream);
  */
 int aceapex_decode_range(aceapex_ctx* ctx, aceapex_archive* arc, uint64_t start, uint64_t len, void* d_out,
                          void* stream, aceapex_stats* stats);
+
+/*
+ * Serving: a request loop over one archive held compressed in device memory
+ * with a bounded cache of decoded blocks (paper, Random Access at Scale; the
+ * paper's persistent seek queue).  A worker thread admits the requests that
+ * have arrived, in arrival order, while the cache can hold their byte-level
+ * dependency closure (the match index is built at creation if the archive
+ * has none), and decodes each tick's union of closures, minus the bytes the
+ * cache keeps, with one launch sequence into cache slots followed by one
+ * gather into the requests' buffers.  Requests that arrive while a tick runs
+ * join the next one, which is queued right behind it on the server's stream.
+ * Admission is by memory: a request waits while its closure needs more free
+ * or evictable slots than there are, and completes with ACEAPEX_E_BUSY if it
+ * could never fit.  Blocks read by unfinished ticks are pinned; the others
+ * are evicted least recently used first.  The archive must stay open while
+ * the server exists; the server uses its own context and stream.
+ */
+typedef struct aceapex_server aceapex_server;
+typedef struct {
+    uint64_t cache_bytes;        /* decoded-block cache (device memory; default 4 GiB) */
+    uint32_t max_tick_blocks;    /* blocks one tick decodes at most (default 16384) */
+    uint32_t max_tick_requests;  /* requests one tick gathers at most (default 4096) */
+} aceapex_server_params;
+typedef struct {
+    uint64_t id;
+    int status;               /* ACEAPEX_OK, ACEAPEX_E_BUSY (can never fit), or a decode error */
+    uint32_t closure_blocks;  /* blocks the request read (decoded or kept) */
+    uint32_t decoded_blocks;  /* blocks it added to its tick's decode */
+    double latency_us;        /* arrival -> completion seen by the server */
+    double queue_us;          /* arrival -> admission */
+} aceapex_completion;
+typedef struct {
+    uint64_t completed, failed, refused, bytes, ticks, blocks_decoded, blocks_hit;
+    double p50_us, p99_us, mean_us, max_us;   /* latency of the completed requests */
+    double closure_mean, closure_p50, closure_p99;
+    double seconds;           /* first arrival -> last completion */
+    double gbs;               /* bytes delivered / seconds */
+} aceapex_server_stats;
+
+/* ctx: its device and decoder parameters are used (the server creates its own
+ * context).  arc: opened on that device.  params may be NULL. */
+int aceapex_server_create(aceapex_ctx* ctx, aceapex_archive* arc, const aceapex_server_params* params,
+                          aceapex_server** out);
+/* Nanoseconds since the server was created (its clock for arrivals). */
+int64_t aceapex_server_now_ns(const aceapex_server* server);
+/* Queue n requests: region [start[i], start[i] + len[i]) into d_out[i]
+ * (device pointers, len[i] bytes, valid until the request completes),
+ * arriving at at_ns[i] on the server clock (a later time schedules an
+ * open-loop arrival; negative or at_ns NULL: now).  ids (may be NULL) gets
+ * the request ids.  ACEAPEX_E_RANGE if a region leaves the archive (nothing
+ * is queued then). */
+int aceapex_server_submit_many(aceapex_server* server, int n, const uint64_t* start, const uint64_t* len,
+                               void* const* d_out, const int64_t* at_ns, uint64_t* ids);
+int aceapex_server_submit(aceapex_server* server, uint64_t start, uint64_t len, void* d_out, int64_t at_ns,
+                          uint64_t* id);
+/* Move up to max completions into out, waiting up to wait_ms for the first;
+ * returns how many (or a negative status). */
+int aceapex_server_poll(aceapex_server* server, aceapex_completion* out, int max, int wait_ms);
+/* Wait until every submitted request has completed (ACEAPEX_E_TIMEOUT after timeout_ms). */
+int aceapex_server_drain(aceapex_server* server, int timeout_ms);
+/* Latency percentiles, throughput and cache figures since the last reset. */
+int aceapex_server_get_stats(aceapex_server* server, int reset, aceapex_server_stats* out);
+const char* aceapex_server_last_error(const aceapex_server* server);
+int aceapex_server_destroy(aceapex_server* server);
 
 /*
  * End-to-end decode from host memory: copies the archive (host pointer

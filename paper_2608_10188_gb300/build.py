@@ -28,7 +28,8 @@ def _nvcc() -> str:
 
 def sources():
     return [os.path.join(CSRC, f) for f in ("rans.cu", "assemble.cu", "plain.cu", "noalloc.cu", "gather.cu", "api.cpp",
-                                          "batch.cpp", "subset.cpp", "plan.cpp", "encode.cpp")]
+                                          "batch.cpp", "subset.cpp", "closure.cpp", "serve.cpp", "plan.cpp",
+                                          "encode.cpp")]
 
 
 def _deps():

@@ -76,6 +76,7 @@ int aceapex_ctx_destroy(aceapex_ctx* c) {
     c->out_buf.release();
     c->slot_out.release();
     c->items.release();
+    c->need.release();
     if (c->counters) cudaFree(c->counters);
     if (c->d_err) cudaFree(c->d_err);
     for (auto& ev : c->ev)
@@ -95,7 +96,7 @@ int aceapex_encode(const uint8_t* src, uint64_t n, const aceapex_enc_params* p, 
     aceapex_enc_params d{};
     if (p) d = *p;
     return encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, d.latest_source, d.max_depth,
-                          d.short_latest, d.deps, out, out_len);
+                          d.short_latest, d.deps, d.segment, out, out_len);
 }
 
 void aceapex_free(void* p) { free(p); }
@@ -139,6 +140,7 @@ int aceapex_archive_close(aceapex_archive* A) {
     if (A->d_dtab) cudaFree(A->d_dtab);
     if (A->d_deps) cudaFree(A->d_deps);
     if (A->d_slot) cudaFree(A->d_slot);
+    delete A->midx;
     delete A;
     return ACEAPEX_OK;
 }
@@ -233,14 +235,15 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
 }
 
 int acx::launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_tok, uint32_t max_lenb,
-                     LaunchPlan* lp) {
-    lp->variant = p.variant;
+                     LaunchPlan* lp, uint32_t job_flags) {
+    // parse-only and wanted-byte jobs run the scan decoder (the serial one has neither mode)
+    lp->variant = (job_flags & (kJobIndex | kJobNeed)) ? (uint32_t)ACEAPEX_VARIANT_FAST : p.variant;
     lp->grid_rans = (p.rans_ctas_per_sm ? std::min<int>(c->occ_rans, (int)p.rans_ctas_per_sm) : c->occ_rans) * c->n_sms;
     lp->grid_ext = c->occ_ext * c->n_sms;
     lp->grid_plain = c->occ_plain * c->n_sms;
     lp->grid_local = 0;
-    if (p.variant != ACEAPEX_VARIANT_PLAIN) {
-        const size_t lsm = local_smem_bytes(max_tok, max_lenb);
+    if (lp->variant != ACEAPEX_VARIANT_PLAIN) {
+        const size_t lsm = local_smem_bytes(max_tok, max_lenb, (job_flags & kJobNeed) != 0);
         if (lsm > 227 * 1024) return fail(c, ACEAPEX_E_CORRUPT, "block too large for the local pass");
         int occ = std::max(1, local_occupancy(lsm));
         if (p.ctas_per_sm) occ = std::min<int>(occ, (int)p.ctas_per_sm);
@@ -266,7 +269,8 @@ int acx::enqueue_job(aceapex_ctx* c, const JobDev& job, const LaunchPlan& lp, ui
         if ((e = launch_local(job, lp.grid_local, st)) != cudaSuccess) return cuda_fail(c, e, "local launch");
     }
     if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return cuda_fail(c, e, "event");
-    if ((e = launch_external(job, lp.grid_ext, st)) != cudaSuccess) return cuda_fail(c, e, "external launch");
+    if (!(job.flags & kJobIndex) && (e = launch_external(job, lp.grid_ext, st)) != cudaSuccess)
+        return cuda_fail(c, e, "external launch");
     if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return cuda_fail(c, e, "event");
     return ACEAPEX_OK;
 }

@@ -35,10 +35,10 @@ constexpr int kLocWarps = kLocThreads / 32;
 constexpr uint64_t kRefTag = 1ull << 63;  // history map entry "copy input entry k"
 
 struct LocLayout {
-    uint32_t out, pend, tsrc, tpos, tll, tml, tlit, tcmd, tstat, lenb, soff, slit, scan, bar, misc, total;
+    uint32_t out, pend, tsrc, tpos, tll, tml, tlit, tcmd, tstat, lenb, soff, slit, scan, bar, misc, need, total;
 };
 
-__host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB) {
+__host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB, bool need) {
     LocLayout L;
     uint32_t o = 0;
     auto take = [&](uint32_t bytes, uint32_t align) {
@@ -63,8 +63,16 @@ __host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB) {
     L.scan = take(kLocWarps * 4 * 4 + 64, 16);
     L.bar = take(8, 8);
     L.misc = take(64, 16);
+    L.need = need ? take(kBlock / 8, 16) : 0;  // wanted-byte bitmap (jobs with kJobNeed)
     L.total = (o + 127) & ~127u;
     return L;
+}
+
+// Does the match at [o, o + ml) of a block touch a wanted byte?
+__device__ __forceinline__ bool wanted(const uint32_t* need, uint32_t o, uint32_t ml) {
+    for (uint32_t w = o >> 5; w <= ((o + ml - 1) >> 5); w++)
+        if (need[w] & range_mask(w, o, o + ml)) return true;
+    return false;
 }
 
 // Block-wide exclusive scan of three u32 values per thread.
@@ -172,8 +180,9 @@ __device__ __forceinline__ void copy_run(uint8_t* __restrict__ sout, const uint8
 
 __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
     extern __shared__ __align__(128) uint8_t sm[];
-    const LocLayout L = loc_layout(job.max_tok, job.max_lenb);
+    const LocLayout L = loc_layout(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0);
     uint8_t* sout = sm + L.out;
+    uint32_t* need = reinterpret_cast<uint32_t*>(sm + L.need);  // valid in kJobNeed jobs
     uint32_t* pend = reinterpret_cast<uint32_t*>(sm + L.pend);
     uint64_t* tsrc = reinterpret_cast<uint64_t*>(sm + L.tsrc);
     uint16_t* tpos = reinterpret_cast<uint16_t*>(sm + L.tpos);
@@ -226,6 +235,19 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
         }
         for (uint32_t i = tid; i < kBlock / 32; i += kLocThreads) pend[i] = 0;
         if (tid == 0) misc[1] = 0;
+        // wanted bytes of this item (all when it names none)
+        const bool partial = (job.flags & kJobNeed) && ir.need_n != 0;
+        if (partial) {
+            for (uint32_t i = tid; i < kBlock / 32; i += kLocThreads) need[i] = 0;
+            __syncthreads();
+            for (uint32_t q = 0; q < ir.need_n; q++) {
+                const uint32_t iv = J.need[ir.need_off + q];
+                const uint32_t s0 = iv & 0xffff, e0 = min(iv >> 16, kBlock);
+                if (s0 < e0)
+                    for (uint32_t w = (s0 >> 5) + tid; w <= ((e0 - 1) >> 5); w += kLocThreads)
+                        atomicOr(&need[w], range_mask(w, s0, e0));
+            }
+        }
         bool timed_out = false;
         if (!bad) {
             uint32_t spins = 0;
@@ -378,6 +400,18 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
             mark(misc[1] != 0, kStageSources);
         }
 
+        if (job.flags & kJobIndex) {
+            // parse only: one record per token (source, destination offset,
+            // match length, command)
+            if (!bad)
+                for (uint32_t i = tid; i < n; i += kLocThreads)
+                    J.spans[ir.span_base + i] = SpanRec{(uint32_t)tsrc[i], (uint32_t)(tsrc[i] >> 32),
+                                                        (uint32_t)(tpos[i] + tll[i]) | ((uint32_t)tml[i] << 16), tcmd[i]};
+            if (bad && tid == 0) set_err_arc(job, a, kErrCorrupt, stage << 24, b);
+            __syncthreads();
+            continue;
+        }
+
         uint32_t npend = 0, pbytes = 0;
         if (!bad) {
             // ---- literal placement: one warp per run ----
@@ -432,7 +466,11 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
                 const int any_prog = __syncthreads_or(progress);
                 if (!any_left || !any_prog) break;
             }
-            // ---- whatever is still unresolved becomes pending pieces ----
+            // ---- whatever is still unresolved becomes pending pieces (for a
+            //      partial item: the wanted matches only) ----
+            if (partial)
+                for (uint32_t i = i0; i < i1; i++)
+                    if (tstat[i] && !wanted(need, tpos[i] + tll[i], tml[i])) tstat[i] = 0;
             uint32_t cnt = 0, nbytes = 0;
             for (uint32_t i = i0; i < i1; i++)
                 if (tstat[i]) {
@@ -466,7 +504,15 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
             // lookup and never wait on a corrupt block
             uint4* gp = reinterpret_cast<uint4*>(J.pmap + (uint64_t)ir.slot * (kBlock / 32));
             const uint4* sp = reinterpret_cast<const uint4*>(pend);
-            for (uint32_t i = tid; i < kBlock / 128; i += kLocThreads) gp[i] = npend ? sp[i] : make_uint4(0, 0, 0, 0);
+            const uint4* np4 = reinterpret_cast<const uint4*>(need);
+            for (uint32_t i = tid; i < kBlock / 128; i += kLocThreads) {
+                uint4 v = npend ? sp[i] : make_uint4(0, 0, 0, 0);
+                if (partial) {  // unwanted bytes are never read: leave them out of the bitmap
+                    const uint4 m = np4[i];
+                    v.x &= m.x; v.y &= m.y; v.z &= m.z; v.w &= m.w;
+                }
+                gp[i] = v;
+            }
         }
         if (tid == 0) {
             J.npend[ir.slot] = npend;
@@ -761,10 +807,10 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
     }
 }
 
-size_t local_smem_bytes(uint32_t T, uint32_t LB) { return loc_layout(T, LB).total; }
+size_t local_smem_bytes(uint32_t T, uint32_t LB, bool need) { return loc_layout(T, LB, need).total; }
 
 cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st) {
-    const size_t sm = local_smem_bytes(job.max_tok, job.max_lenb);
+    const size_t sm = local_smem_bytes(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0);
     cudaError_t e = cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_local<<<grid, kLocThreads, sm, st>>>(job);

@@ -1,0 +1,235 @@
+// Byte-level dependency closures: the archive's match index (built by a
+// parse-only pass on the device) and the walk from wanted byte ranges back
+// through the matches that write them.
+//
+// Paper, Random Access at Scale and "The byte-level refutation": what a
+// region needs is not every block its blocks reference but the bytes its
+// bytes were copied from.  With sources anywhere in the output (absolute
+// offsets), a block-level closure grows to a large part of the archive,
+// while the byte-level one stays near the region: each copied byte has one
+// source, and chains end at literals after a few steps (the encoder caps the
+// chain depth).
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "host.h"
+
+using namespace acx;
+
+namespace {
+
+// Is [s, e) inside the union of v?
+bool iv_covers(const Ivs& v, uint32_t s, uint32_t e) {
+    auto it = std::upper_bound(v.begin(), v.end(), std::make_pair(s, 0xffffffffu));
+    if (it == v.begin()) return false;
+    --it;
+    return it->first <= s && it->second >= e;
+}
+
+// The parts of [s, e) outside v.
+void iv_minus(uint32_t s, uint32_t e, const Ivs& v, Ivs* out) {
+    out->clear();
+    auto it = std::upper_bound(v.begin(), v.end(), std::make_pair(s, 0xffffffffu));
+    if (it != v.begin() && std::prev(it)->second > s) s = std::prev(it)->second;
+    for (; s < e && it != v.end() && it->first < e; ++it) {
+        if (it->first > s) out->push_back({s, it->first});
+        s = std::max(s, it->second);
+    }
+    if (s < e) out->push_back({s, e});
+}
+
+// v |= [s, e)
+void iv_add(Ivs& v, uint32_t s, uint32_t e) {
+    auto it = std::lower_bound(v.begin(), v.end(), std::make_pair(s, 0u));
+    if (it != v.begin() && std::prev(it)->second >= s) --it;
+    auto jt = it;
+    while (jt != v.end() && jt->first <= e) {
+        s = std::min(s, jt->first);
+        e = std::max(e, jt->second);
+        ++jt;
+    }
+    it = v.erase(it, jt);
+    v.insert(it, {s, e});
+}
+
+}  // namespace
+
+int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
+    if (A->midx) return ACEAPEX_OK;
+    const Plan& P = A->plan;
+    MatchIndex* M = new (std::nothrow) MatchIndex();
+    if (!M) return fail(c, ACEAPEX_E_NOMEM, "match index: host allocation");
+    M->first.assign((size_t)P.n_blocks + 1, 0);
+    cudaSetDevice(c->device);
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete M;
+        return cuda_fail(c, e, "match index: stream");
+    }
+    DevBuf items, recs, scratch;
+    std::vector<SpanRec> h;
+    std::vector<ItemDev> it;
+    int rc = ACEAPEX_OK;
+    constexpr uint32_t kChunk = 16384;  // blocks per parse-only job
+    for (uint32_t c0 = 0; c0 < P.n_blocks && rc == ACEAPEX_OK; c0 += kChunk) {
+        const uint32_t c1 = std::min(P.n_blocks, c0 + kChunk), k = c1 - c0;
+        it.assign(k, ItemDev{});
+        uint64_t toks = 0, sb = 0;
+        uint32_t max_tok = 1, max_lenb = 1;
+        for (uint32_t i = 0; i < k; i++) {
+            const BlockDev& bd = P.blk[c0 + i];
+            it[i].block = c0 + i;
+            it[i].slot = kNoSlot;
+            it[i].span_base = (uint32_t)toks;  // token records, packed
+            it[i].scratch = sb;
+            toks += bd.n_tok;
+            sb += (bd.s_off[3] + bd.s_raw[3] + 15) & ~15ull;
+            max_tok = std::max(max_tok, bd.n_tok);
+            max_lenb = std::max(max_lenb, bd.s_raw[kLen]);
+        }
+        sb += 64;
+        if ((e = items.ensure(k * sizeof(ItemDev))) != cudaSuccess ||
+            (e = recs.ensure(std::max<uint64_t>(toks, 1) * sizeof(SpanRec))) != cudaSuccess ||
+            (e = scratch.ensure(sb)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(items.p, it.data(), k * sizeof(ItemDev), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+            rc = cuda_fail(c, e, "match index: scratch");
+            break;
+        }
+        JobDev job{};
+        ArcJob& J = job.one;
+        J.arc = (const uint8_t*)A->d_arc;
+        J.blk = A->d_blk;
+        J.dtab = A->d_dtab;
+        J.scratch = (uint8_t*)scratch.p;
+        J.spans = (SpanRec*)recs.p;
+        J.total = P.total;
+        J.n_blocks = P.n_blocks;
+        J.lo = 0;
+        J.hi = k;
+        J.min_match = P.min_match;
+        J.deps = A->d_deps;
+        J.items = (const ItemDev*)items.p;
+        job.n_arcs = 1;
+        job.n_items = k;
+        job.counters = c->counters;
+        job.err = c->d_err;
+        job.timeout_ns = (uint64_t)c->params.timeout_us * 1000ull;
+        job.max_tok = max_tok;
+        job.max_lenb = max_lenb;
+        job.flags = kJobIndex;
+        LaunchPlan lp;
+        if ((rc = launch_plan(c, c->params, max_tok, max_lenb, &lp, kJobIndex))) break;
+        if ((rc = enqueue_job(c, job, lp, 4, nullptr, 0, st, nullptr))) break;
+        if ((rc = ctx_read_status(c, st))) break;
+        h.resize(toks);
+        if (toks && (e = cudaMemcpy(h.data(), recs.p, toks * sizeof(SpanRec), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            rc = cuda_fail(c, e, "match index: records");
+            break;
+        }
+        uint64_t t = 0;
+        for (uint32_t i = 0; i < k; i++) {
+            const uint32_t b = c0 + i, n = P.blk[b].n_tok;
+            M->first[b] = M->o.size();
+            for (uint32_t q = 0; q < n; q++, t++) {
+                const SpanRec& r = h[t];
+                const uint32_t ml = r.z >> 16;
+                if (!ml) continue;
+                M->o.push_back((uint16_t)(r.z & 0xffff));
+                M->ml.push_back((uint16_t)ml);
+                M->src.push_back((uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32));
+            }
+        }
+    }
+    M->first[P.n_blocks] = M->o.size();
+    cudaStreamDestroy(st);
+    items.release();
+    recs.release();
+    scratch.release();
+    if (rc) {
+        delete M;
+        return rc;
+    }
+    A->midx = M;
+    return ACEAPEX_OK;
+}
+
+void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t len, ValidFn valid, void* self,
+                    TickState* T, WalkJournal* J) {
+    struct R {
+        uint32_t b, s, e;
+    };
+    std::vector<R> stack;
+    Ivs parts;
+    auto push_abs = [&](uint64_t s, uint64_t e) {  // absolute [s, e), split by block
+        for (uint64_t a = s / kBlock; a <= (e - 1) / kBlock; a++) {
+            const uint64_t A0 = a * kBlock;
+            stack.push_back({(uint32_t)a, (uint32_t)(std::max(s, A0) - A0), (uint32_t)(std::min(e, A0 + kBlock) - A0)});
+        }
+    };
+    if (len) push_abs(start, start + len);
+    while (!stack.empty()) {
+        const R r = stack.back();
+        stack.pop_back();
+        if (r.s >= r.e) continue;
+        const uint32_t X = r.b;
+        if (T->used.insert(X).second) J->used.push_back(X);
+        auto nit = T->need.find(X);
+        if (nit == T->need.end()) {
+            const Ivs* V = valid(self, X);
+            if (V && iv_covers(*V, r.s, r.e)) continue;  // kept from an earlier decode
+            nit = T->need.emplace(X, Ivs()).first;
+            J->added.push_back(X);
+            // a block decoded again keeps what it held: its kept bytes are wanted too
+            if (V)
+                for (const auto& iv : *V) stack.push_back({X, iv.first, iv.second});
+        }
+        iv_minus(r.s, r.e, nit->second, &parts);
+        if (parts.empty()) continue;
+        if (std::find(J->added.begin(), J->added.end(), X) == J->added.end()) {
+            bool saved = false;
+            for (const auto& sv : J->saved) saved |= sv.first == X;
+            if (!saved) J->saved.push_back({X, nit->second});
+        }
+        const uint64_t lo = M.first[X], hi = M.first[X + 1];
+        for (const auto& p : parts) {
+            iv_add(nit->second, p.first, p.second);
+            // matches of X overlapping p (matches are disjoint and in order)
+            uint64_t a = lo, z = hi;
+            while (a < z) {
+                const uint64_t m = (a + z) / 2;
+                if ((uint32_t)M.o[m] + M.ml[m] <= p.first) a = m + 1; else z = m;
+            }
+            for (uint64_t k = a; k < hi && M.o[k] < p.second; k++) {
+                if (!T->taken.insert(k).second) continue;
+                J->taken.push_back(k);
+                const uint32_t o = M.o[k], ml = M.ml[k];
+                stack.push_back({X, o, o + ml});  // the whole match is decoded
+                const uint64_t dst = (uint64_t)X * kBlock + o, src = M.src[k];
+                const uint64_t d = dst - src;
+                push_abs(src, src + std::min<uint64_t>(d, ml));  // its source window (one period if it overlaps)
+            }
+        }
+    }
+}
+
+void acx::span_undo(TickState* T, const WalkJournal& J) {
+    for (uint32_t b : J.added) T->need.erase(b);
+    for (const auto& sv : J.saved) T->need[sv.first] = sv.second;
+    for (uint64_t k : J.taken) T->taken.erase(k);
+    for (uint32_t b : J.used) T->used.erase(b);
+}
+
+void acx::need_intervals(const Ivs& need, uint32_t raw_len, std::vector<uint32_t>* out) {
+    out->clear();
+    if (need.size() == 1 && need[0].first == 0 && need[0].second >= raw_len) return;
+    for (const auto& iv : need) out->push_back(iv.first | (std::min(iv.second, kBlock) << 16));
+}
+
+extern "C" int aceapex_archive_index(aceapex_ctx* c, aceapex_archive* A) {
+    if (!c || !A) return fail(c, ACEAPEX_E_ARG, "archive_index: null argument");
+    return build_match_index(c, A);
+}

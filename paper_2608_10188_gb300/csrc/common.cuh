@@ -102,7 +102,7 @@ __device__ __forceinline__ ArcJob load_arc(const JobDev& job, int a) { return jo
 // Where a work item's block goes: its block id, output slot, pending-piece
 // base and decoded-stream offset (idx counted from the archive's item_base).
 struct ItemRef {
-    uint32_t blk, slot, span_base;
+    uint32_t blk, slot, span_base, need_off, need_n;
     uint64_t scratch;
 };
 __device__ __forceinline__ ItemRef item_ref(const ArcJob& J, uint32_t idx) {
@@ -113,9 +113,13 @@ __device__ __forceinline__ ItemRef item_ref(const ArcJob& J, uint32_t idx) {
         r.slot = it.slot;
         r.span_base = it.span_base;
         r.scratch = it.scratch;
+        r.need_off = it.need_off;
+        r.need_n = it.need_n;
     } else {
         r.blk = J.lo + idx;
         r.slot = r.blk;
+        r.need_off = 0;
+        r.need_n = 0;
         r.span_base = J.blk[r.blk].span_base;
         r.scratch = J.blk[r.blk].scratch;
     }

@@ -161,6 +161,9 @@ struct Parser {
     };
     std::vector<Emitted> emitted;
     std::vector<uint64_t> block_first;
+    // the parse covers [base, n): sources stay inside it (a segment of a
+    // segmented encode), depth[] and block_first[] are indexed from it
+    uint64_t base = 0;
 
     // Follow a non-periodic source window [s, s + w) back through the
     // non-periodic matches that produced it: their bytes equal their sources,
@@ -168,8 +171,9 @@ struct Parser {
     // the decoder's cross-block dependency chains become short.
     uint64_t forward(uint64_t s, uint32_t w) const {
         for (int hop = 0; hop < 64; hop++) {
-            const uint64_t b = s / kBlock;
-            if (b + 1 >= block_first.size() && b >= block_first.size()) break;
+            if (s < base) break;
+            const uint64_t b = (s - base) / kBlock;
+            if (b >= block_first.size()) break;
             const uint64_t lo = block_first[b];
             const uint64_t hi = b + 1 < block_first.size() ? block_first[b + 1] : emitted.size();
             // last match of the block starting at or before s
@@ -200,8 +204,10 @@ struct Parser {
             if (!oldest || !slot) slot = p + 1;
         }
         if (p + 8 <= n) {
+            // 32-bit entries: position + 1 modulo 2^32 (only distances below
+            // the short window are used, so the high bits are never needed)
             uint32_t& slot = hs[hash_short(s + p, sbits)];
-            if (!short_oldest || !slot || p - (slot - 1) >= kShortWindow) slot = (uint32_t)(p + 1);
+            if (!short_oldest || !slot || (uint32_t)((uint32_t)p - (slot - 1)) >= kShortWindow) slot = (uint32_t)(p + 1);
         }
     }
     static constexpr uint64_t kShortWindow = 1u << 22;
@@ -209,7 +215,8 @@ struct Parser {
     uint32_t window_depth(uint64_t pos, uint64_t d, uint32_t L) const {
         const uint64_t w = d < L ? d : L;
         uint32_t m = 0;
-        for (uint64_t k = 0; k < w; k++) m = m > depth[pos - d + k] ? m : depth[pos - d + k];
+        const uint8_t* dp = &depth[pos - d - base];
+        for (uint64_t k = 0; k < w; k++) m = m > dp[k] ? m : dp[k];
         return m;
     }
     // cost in bits of a NEW token (cmd + two varints + absolute offset)
@@ -236,7 +243,7 @@ struct Parser {
             int bestRep = -1;
             double bestGain = 0.0;
             auto consider = [&](uint64_t d, int rep_idx) {
-                if (d == 0 || d > pos) return;
+                if (d == 0 || d > pos - base) return;
                 const uint32_t L = overlap_len(s, pos, pos - d, limit);
                 if (L < min_match) return;
                 int ri = rep_idx;
@@ -259,8 +266,9 @@ struct Parser {
                 if (q) consider(pos - (q - 1), -1);
             }
             if (pos + 8 <= n) {
-                const uint64_t q = hs[hash_short(s + pos, sbits)];
-                if (q && q - 1 < pos && pos - (q - 1) < kShortWindow) consider(pos - (q - 1), -1);
+                const uint32_t q = hs[hash_short(s + pos, sbits)];
+                const uint64_t back = (uint32_t)((uint32_t)pos - (q - 1));
+                if (q && back > 0 && back < kShortWindow) consider(back, -1);
             }
             if (!bestL) { pos++; continue; }
             if (bestRep < 0 && bestD >= bestL) {
@@ -278,7 +286,7 @@ struct Parser {
                     }
                 }
             }
-            memset(&depth[pos], bestDepth > 255 ? 255 : (int)bestDepth, bestL);
+            memset(&depth[pos - base], bestDepth > 255 ? 255 : (int)bestDepth, bestL);
             emitted.push_back({pos, pos - bestD, bestL});
             const uint32_t LL = (uint32_t)(pos - lit0);
             const bool rep_code = bestRep >= 0 && !no_rep;
@@ -330,7 +338,9 @@ void parallel_for(uint32_t n, int threads, F fn) {
 }  // namespace
 
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   int latest, uint32_t max_depth, int short_latest, int deps, uint8_t** out, uint64_t* out_len) {
+                   int latest, uint32_t max_depth, int short_latest, int deps, uint64_t segment, uint8_t** out,
+                   uint64_t* out_len) {
+    if (segment % kBlock) return -1;
     if (!out || !out_len || (n && !src)) return -1;
     if (min_match == 0) min_match = 4;
     if (max_lanes == 0) max_lanes = 32;
@@ -352,45 +362,67 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
                 const double p = (double)hist[c] / (double)n;
                 H -= p * log2(p);
             }
-        Parser P;
-        P.s = src;
-        P.n = n;
-        P.no_rep = no_rep != 0;
-        P.oldest = latest == 0;
-        P.short_oldest = short_latest == 0;
-        P.max_depth = max_depth == 0 ? kDefaultMaxDepth : max_depth;
-        P.depth.assign(n, 0);
-        P.min_match = min_match;
-        P.lit_bits = std::max(H, 1.0) + 0.1;
-        P.lbits = 16;
-        while (P.lbits < 27 && (1ull << P.lbits) < n) P.lbits++;
-        P.sbits = std::min(P.lbits, 22);
-        P.hl.assign(1ull << P.lbits, 0);
-        P.hs.assign(1ull << P.sbits, 0);
-        uint64_t ins = 0;
-        for (uint32_t b = 0; b < nb; b++) {
-            const uint64_t B = (uint64_t)b * kBlock, E = std::min<uint64_t>(n, B + kBlock);
-            P.parse_block(B, E, blocks[b], ins);
-        }
-        if (deps) {
-            std::vector<uint32_t> ids;
-            for (uint32_t b = 0; b < nb; b++) {
-                const uint64_t lo = P.block_first[b];
-                const uint64_t hi = b + 1 < nb ? P.block_first[b + 1] : P.emitted.size();
-                ids.clear();
-                for (uint64_t m = lo; m < hi; m++) {
-                    const Parser::Emitted& M = P.emitted[m];
-                    const uint64_t d = M.dst - M.src;
-                    const uint64_t end = M.src + (d < M.len ? d : M.len);  // bytes the match reads
-                    for (uint64_t a = M.src / kBlock; a <= (end - 1) / kBlock && a < b; a++) ids.push_back((uint32_t)a);
+        // the parse: one segment, or segments of `segment` bytes parsed in
+        // parallel, each with sources inside itself (a genome's chromosomes)
+        const uint64_t seg = segment ? segment : std::max<uint64_t>(n, 1);
+        const uint32_t n_seg = (uint32_t)((n + seg - 1) / seg);
+        std::vector<std::vector<uint32_t>> seg_deps(deps ? nb : 0);
+        std::atomic<int> failed(0);
+        auto parse_segment = [&](uint32_t g) {
+            try {
+                const uint64_t s0 = (uint64_t)g * seg, s1 = std::min<uint64_t>(n, s0 + seg);
+                Parser P;
+                P.s = src;
+                P.n = s1;
+                P.base = s0;
+                P.no_rep = no_rep != 0;
+                P.oldest = latest == 0;
+                P.short_oldest = short_latest == 0;
+                P.max_depth = max_depth == 0 ? kDefaultMaxDepth : max_depth;
+                P.depth.assign(s1 - s0, 0);
+                P.min_match = min_match;
+                P.lit_bits = std::max(H, 1.0) + 0.1;
+                P.lbits = 16;
+                while (P.lbits < 27 && (1ull << P.lbits) < s1 - s0) P.lbits++;
+                P.sbits = std::min(P.lbits, 22);
+                P.hl.assign(1ull << P.lbits, 0);
+                P.hs.assign(1ull << P.sbits, 0);
+                uint64_t ins = s0;
+                const uint32_t b0 = (uint32_t)(s0 / kBlock), b1 = (uint32_t)((s1 + kBlock - 1) / kBlock);
+                for (uint32_t b = b0; b < b1; b++) {
+                    const uint64_t B = (uint64_t)b * kBlock, E = std::min<uint64_t>(s1, B + kBlock);
+                    P.parse_block(B, E, blocks[b], ins);
                 }
-                std::sort(ids.begin(), ids.end());
-                ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
-                dep_off[b] = (uint32_t)dep_ids.size();
-                dep_n[b] = (uint32_t)ids.size();
-                dep_ids.insert(dep_ids.end(), ids.begin(), ids.end());
+                if (deps) {
+                    std::vector<uint32_t> ids;
+                    for (uint32_t b = b0; b < b1; b++) {
+                        const uint64_t lo = P.block_first[b - b0];
+                        const uint64_t hi = b + 1 < b1 ? P.block_first[b + 1 - b0] : P.emitted.size();
+                        ids.clear();
+                        for (uint64_t m = lo; m < hi; m++) {
+                            const Parser::Emitted& M = P.emitted[m];
+                            const uint64_t d = M.dst - M.src;
+                            const uint64_t end = M.src + (d < M.len ? d : M.len);  // bytes the match reads
+                            for (uint64_t a = M.src / kBlock; a <= (end - 1) / kBlock && a < b; a++)
+                                ids.push_back((uint32_t)a);
+                        }
+                        std::sort(ids.begin(), ids.end());
+                        ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+                        seg_deps[b] = ids;
+                    }
+                }
+            } catch (...) {
+                failed = 1;
             }
-        }
+        };
+        parallel_for(n_seg, std::min<int>(threads, (int)std::max<uint32_t>(n_seg, 1)), parse_segment);
+        if (failed) return -3;
+        if (deps)
+            for (uint32_t b = 0; b < nb; b++) {
+                dep_off[b] = (uint32_t)dep_ids.size();
+                dep_n[b] = (uint32_t)seg_deps[b].size();
+                dep_ids.insert(dep_ids.end(), seg_deps[b].begin(), seg_deps[b].end());
+            }
     } catch (...) {
         return -3;
     }

@@ -4,6 +4,9 @@
 
 #include <algorithm>
 #include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <utility>
 #include <vector>
 
 #include "../../include/aceapex.h"
@@ -42,6 +45,18 @@ struct DevBuf {
     }
 };
 
+// Sorted, disjoint byte intervals [first, second) of one block.
+typedef std::vector<std::pair<uint32_t, uint32_t>> Ivs;
+
+// Every match of an archive, block by block (from a parse-only pass over the
+// archive): match k of block b, for k in [first[b], first[b+1]), writes
+// [o[k], o[k] + ml[k]) of its block from the absolute source src[k].
+struct MatchIndex {
+    std::vector<uint64_t> first;
+    std::vector<uint16_t> o, ml;
+    std::vector<uint64_t> src;
+};
+
 }  // namespace acx
 
 struct aceapex_ctx {
@@ -50,7 +65,7 @@ struct aceapex_ctx {
     std::string err;
     int n_sms = 0;
     acx::DevBuf streams, npend, pmap, spans, lists, arcs, in_arc, out_buf;
-    acx::DevBuf slot_out, items;   // range decodes: decoded closure blocks, work items
+    acx::DevBuf slot_out, items, need;   // range decodes: decoded closure blocks, work items, wanted bytes
     uint32_t* counters = nullptr;  // device
     int* d_err = nullptr;          // device
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -65,6 +80,7 @@ struct aceapex_archive {
     uint32_t* d_dtab = nullptr;
     uint32_t* d_deps = nullptr;    // dependency lists (archives that carry them)
     uint32_t* d_slot = nullptr;    // block -> output slot of subset decodes (allocated on first use)
+    acx::MatchIndex* midx = nullptr;  // match index (aceapex_archive_index), or nullptr
     std::vector<uint32_t> seen;    // closure walk marks (epoch per block)
     uint32_t epoch = 0;
 };
@@ -90,7 +106,8 @@ struct LaunchPlan {
 // Grids for a job whose largest block has max_tok tokens and max_lenb length
 // bytes, under decoder parameters p (fails when a block cannot fit the local
 // pass's shared memory).
-int launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_tok, uint32_t max_lenb, LaunchPlan* lp);
+int launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_tok, uint32_t max_lenb, LaunchPlan* lp,
+                uint32_t job_flags = 0);
 // Synchronise st and return (and clear) the context's device error status.
 int ctx_read_status(aceapex_ctx* c, cudaStream_t st);
 
@@ -108,6 +125,36 @@ struct SubsetPlan {
     uint32_t max_tok = 1, max_lenb = 1;
 };
 void subset_plan(const Plan& P, const uint32_t* blocks, const uint32_t* slots, size_t n, SubsetPlan* S);
+
+// Build the archive's match index with a parse-only pass on the device.
+int build_match_index(aceapex_ctx* c, aceapex_archive* A);
+
+// The span-refined dependency closure of byte ranges (paper, Random Access at
+// Scale; its byte-level view of dependencies): a wanted byte range of a block
+// needs the matches that write it, each match needs its whole source window,
+// and so on back to literals.  `valid(b)` gives the bytes of block b already
+// decoded and kept (nullptr: none); a range inside them needs nothing.  The
+// walk adds to a tick's state (blocks to decode with their wanted intervals,
+// matches taken, blocks read) and journals its changes so that they can be
+// undone when the request is not admitted.
+struct TickState {
+    std::unordered_map<uint32_t, Ivs> need;   // blocks to decode -> wanted intervals
+    std::unordered_set<uint64_t> taken;       // matches already followed
+    std::unordered_set<uint32_t> used;        // every block read (decoded or kept)
+};
+struct WalkJournal {
+    std::vector<std::pair<uint32_t, Ivs>> saved;  // need of a block before its first change (scheduled before)
+    std::vector<uint32_t> added;                  // blocks newly scheduled
+    std::vector<uint64_t> taken;
+    std::vector<uint32_t> used;
+    void clear() { saved.clear(); added.clear(); taken.clear(); used.clear(); }
+};
+typedef const Ivs* (*ValidFn)(void* self, uint32_t block);
+void span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t len, ValidFn valid, void* self,
+               TickState* T, WalkJournal* J);
+void span_undo(TickState* T, const WalkJournal& J);
+// The interval list of a block to decode, or empty when it covers the block.
+void need_intervals(const Ivs& need, uint32_t raw_len, std::vector<uint32_t>* out);
 
 // Make sure the archive's device slot table exists (all kNoSlot at first).
 int ensure_slot_table(aceapex_ctx* c, aceapex_archive* A);

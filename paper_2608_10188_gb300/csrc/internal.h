@@ -58,8 +58,10 @@ struct ItemDev {
     uint32_t block;
     uint32_t slot;            // output slot of the block
     uint32_t span_base;       // first pending-piece slot (n_tok + kSpanSlack slots)
-    uint32_t pad;
+    uint32_t need_n;          // 0: every byte of the block is wanted; else the wanted bytes are the
     uint64_t scratch;         // offset of the block's decoded streams
+    uint32_t need_off;        //   need_n intervals ArcJob::need[need_off ..] (start | end << 16)
+    uint32_t pad;
 };
 constexpr uint32_t kNoSlot = 0xffffffffu;  // slot-table entry of a block not in the output
 
@@ -90,6 +92,7 @@ struct ArcJob {
     // Subset decodes (both nullptr for whole-archive jobs, where item i is
     // block lo + i with the plan's offsets and block b lives at out + b*kBlock):
     const ItemDev* items;     // item i (counted from item_base) of this archive; hi - lo = item count
+    const uint32_t* need;     // wanted-byte intervals of the items (see ItemDev::need_n), or nullptr
     uint32_t* slot;           // block -> output slot: block b's bytes at out + slot[b]*kBlock, its
                               // pending count at npend[slot[b]] and bitmap at pmap + slot[b]*512;
                               // the entropy stage writes the entries of the job's items
@@ -106,6 +109,17 @@ constexpr uint32_t kStatPending = 4093;
 constexpr uint32_t kStatPolls = 4094;    // cross-block rounds
 constexpr uint32_t kCounterWords = 4096;
 
+// Job flags.  kJobIndex: parse only — the entropy stage skips the literal
+// stream and the local pass writes one token record per token (SpanRec: x/y
+// source, z = destination offset | match length << 16, w = command) at the
+// item's span_base instead of decoding the block.
+constexpr uint32_t kJobIndex = 1;
+// kJobNeed: some items want only some of their bytes (ItemDev::need_n): the
+// local pass leaves the matches outside them undone (their bytes are then
+// undefined) and cuts pieces only for wanted matches, so a block's sources
+// outside its wanted bytes' chains are never read.
+constexpr uint32_t kJobNeed = 2;
+
 struct JobDev {
     ArcJob one;               // the archive when arcs == nullptr
     const ArcJob* arcs;       // device array of archives (batched jobs), or nullptr
@@ -118,6 +132,7 @@ struct JobDev {
     uint64_t timeout_ns;
     uint32_t max_tok;         // shared-memory sizing of the assembly kernel
     uint32_t max_lenb;
+    uint32_t flags;           // kJob* bits
     struct alignas(8) ListEnt {
         uint32_t x, y;        // span slot, item
     };

@@ -18,7 +18,7 @@ cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st);
 // node when the stream is being captured into a graph.
 cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st);
 cudaError_t launch_plain(const JobDev& job, int grid, cudaStream_t st);
-size_t local_smem_bytes(uint32_t T, uint32_t LB);
+size_t local_smem_bytes(uint32_t T, uint32_t LB, bool need = false);
 int rans_occupancy();
 int local_occupancy(size_t smem);
 int external_occupancy();

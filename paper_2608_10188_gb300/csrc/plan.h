@@ -26,7 +26,8 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why);
 
 // Library encoder (format v1); out is malloc'ed.
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   int latest, uint32_t max_depth, int short_latest, int deps, uint8_t** out, uint64_t* out_len);
+                   int latest, uint32_t max_depth, int short_latest, int deps, uint64_t segment, uint8_t** out,
+                   uint64_t* out_len);
 
 // FNV-1a 64.
 uint64_t fnv1a64(const uint8_t* p, uint64_t n);

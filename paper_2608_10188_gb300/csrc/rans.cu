@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
             if (it >= n_a) break;
             const ItemRef ir = item_ref(J, it);
             const uint32_t b = ir.blk;
-            if (J.items && lane == 0) J.slot[b] = ir.slot;  // read by the cross-block pass
+            if (J.items && J.slot && lane == 0) J.slot[b] = ir.slot;  // read by the cross-block pass
             const BlockDev& bd = J.blk[b];
             const uint8_t* pay = J.arc + bd.payload;
             uint8_t* scr = J.scratch + ir.scratch;
@@ -342,7 +342,8 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
             const int sh = rans_short3(&S.tab[0][0], bd, pay, scr, &S.ring[warp][0], &S.sbar[warp], sphase, lane,
                                        deadline);
             if (sh < 0) ok = false;
-            for (int s = sh == 0 ? 0 : 0; s < 4 && ok; s++) {
+            const int n_streams = (job.flags & kJobIndex) ? 3 : 4;  // a parse needs no literals
+            for (int s = 0; s < n_streams && ok; s++) {
                 if (sh == 0 && s < 3 && (bd.rans_mask & (1u << s))) continue;  // decoded above
                 fs = s;
                 const uint32_t n = bd.s_raw[s];

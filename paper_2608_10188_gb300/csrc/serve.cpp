@@ -1,0 +1,640 @@
+// Serving (aceapex_server_*): a request loop over one archive held compressed
+// in device memory, with a bounded cache of decoded blocks.
+//
+// Requests (byte regions) arrive at any time.  A worker thread forms ticks:
+// it admits the requests that have arrived, in arrival order, while the
+// cache can hold what they need, walks each one's byte-level dependency
+// closure minus what the cache already holds (paper, Random Access at Scale),
+// and decodes the union with one launch sequence: the block decodes write
+// into cache slots, then one gather copies every admitted region to its
+// destination.  Ticks run back to back on the server's stream, so requests
+// that arrive while a tick is on the GPU join the next one (continuous
+// batching); the host prepares tick k+1 while tick k runs.
+//
+// Cache: slots of 16 KiB (cache_bytes / 16 KiB of them), each with its
+// pending count and bitmap.  A block's kept bytes are the wanted bytes of its
+// last decode; a block decoded again keeps them (they are wanted again).
+// Blocks read by a tick that has not completed are pinned; the others are
+// evicted least recently used first.  Admission is by memory: a request
+// waits while its closure needs more slots (or more blocks per tick) than are
+// free or evictable, and is refused (ACEAPEX_E_BUSY) if it could never fit.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <mutex>
+#include <queue>
+#include <thread>
+#include <vector>
+
+#include "host.h"
+
+using namespace acx;
+
+namespace {
+
+struct Req {
+    uint64_t id = 0, start = 0, len = 0;
+    uint8_t* dst = nullptr;
+    int64_t at_ns = 0, admit_ns = 0;
+    uint32_t closure = 0, decoded = 0;
+};
+struct ReqLater {  // min-heap on (arrival, id)
+    bool operator()(const Req& a, const Req& b) const { return a.at_ns != b.at_ns ? a.at_ns > b.at_ns : a.id > b.id; }
+};
+
+// Host staging and device copies of one tick's tables (two sets: the host
+// fills one while the other's copies may still be pending on the stream).
+struct TickBufs {
+    ItemDev* h_items = nullptr;
+    uint32_t* h_need = nullptr;
+    GatherReq* h_gather = nullptr;
+    int* h_err = nullptr;
+    size_t cap_items = 0, cap_need = 0, cap_gather = 0;
+    DevBuf d_items, d_need, d_gather;
+};
+
+struct Tick {
+    int set = 0;
+    cudaEvent_t done = nullptr;
+    std::vector<Req> reqs;
+    std::vector<uint32_t> used;       // pinned blocks
+    std::vector<uint32_t> decoded;    // blocks written by this tick
+};
+
+cudaError_t host_grow(void** p, size_t* cap, size_t need, size_t elem) {
+    if (need <= *cap) return cudaSuccess;
+    size_t n = std::max(need, *cap * 2 + 64);
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaHostAlloc(p, n * elem, cudaHostAllocDefault);
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+}  // namespace
+
+struct aceapex_server {
+    aceapex_ctx* c = nullptr;  // own context (the worker thread's)
+    aceapex_archive* A = nullptr;
+    aceapex_server_params prm{};
+    uint32_t n_slots = 0;
+    std::chrono::steady_clock::time_point t0;
+    // device
+    uint8_t* cache = nullptr;
+    uint32_t* npend = nullptr;
+    uint32_t* pmap = nullptr;
+    uint32_t* d_slot = nullptr;
+    DevBuf streams, spans, lists;
+    cudaStream_t st = nullptr;
+    TickBufs bufs[2];
+    std::deque<Tick> inflight;
+    std::vector<cudaEvent_t> free_events;
+    // host cache state
+    std::vector<uint32_t> slot_of;   // block -> slot or kNoSlot
+    std::vector<Ivs> valid;          // block -> kept bytes (resident blocks)
+    std::vector<uint32_t> pins;
+    std::list<uint32_t> lru;         // unpinned resident blocks, most recent first
+    std::vector<std::list<uint32_t>::iterator> lru_it;
+    std::vector<uint8_t> in_lru;
+    std::vector<uint32_t> free_slots;
+    // requests
+    std::mutex mu;
+    std::condition_variable cv;
+    std::priority_queue<Req, std::vector<Req>, ReqLater> queue;
+    std::vector<aceapex_completion> done;
+    uint64_t next_id = 1, submitted = 0, finished = 0;
+    std::thread worker;
+    std::atomic<bool> stop{false};
+    int fatal = 0;
+    std::string fatal_msg;
+    // statistics (under mu)
+    std::vector<double> lat_us;
+    std::vector<uint32_t> closures;
+    uint64_t n_ok = 0, n_err = 0, n_busy = 0, bytes = 0, ticks = 0, blk_decoded = 0, blk_hit = 0;
+    int64_t first_arrival = -1, last_done = 0;
+
+    int64_t now() const {
+        return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
+    }
+    void touch(uint32_t b) {  // most recently used
+        if (in_lru[b]) lru.erase(lru_it[b]);
+        lru.push_front(b);
+        lru_it[b] = lru.begin();
+        in_lru[b] = 1;
+    }
+    void pin(uint32_t b) {
+        if (pins[b]++ == 0 && in_lru[b]) {
+            lru.erase(lru_it[b]);
+            in_lru[b] = 0;
+        }
+    }
+    void unpin(uint32_t b) {
+        if (--pins[b] == 0 && slot_of[b] != kNoSlot) touch(b);
+    }
+    void drop(uint32_t b) {  // forget a resident block, free its slot
+        if (slot_of[b] == kNoSlot) return;
+        if (in_lru[b]) {
+            lru.erase(lru_it[b]);
+            in_lru[b] = 0;
+        }
+        free_slots.push_back(slot_of[b]);
+        slot_of[b] = kNoSlot;
+        valid[b].clear();
+    }
+    static const Ivs* valid_fn(void* self, uint32_t b) {
+        aceapex_server* s = (aceapex_server*)self;
+        return s->slot_of[b] != kNoSlot ? &s->valid[b] : nullptr;
+    }
+    void run();
+    bool form_tick();
+    void finish_tick(Tick& t, int status);
+    void complete(const Req& r, int status, int64_t t_done);
+};
+
+void aceapex_server::complete(const Req& r, int status, int64_t t_done) {
+    aceapex_completion cpl{};
+    cpl.id = r.id;
+    cpl.status = status;
+    cpl.closure_blocks = r.closure;
+    cpl.decoded_blocks = r.decoded;
+    cpl.latency_us = (double)(t_done - r.at_ns) / 1e3;
+    cpl.queue_us = r.admit_ns ? (double)(r.admit_ns - r.at_ns) / 1e3 : 0.0;
+    std::lock_guard<std::mutex> g(mu);
+    done.push_back(cpl);
+    finished++;
+    if (status == ACEAPEX_OK) {
+        n_ok++;
+        bytes += r.len;
+        lat_us.push_back(cpl.latency_us);
+        closures.push_back(r.closure);
+        if (first_arrival < 0 || r.at_ns < first_arrival) first_arrival = r.at_ns;
+        last_done = std::max(last_done, t_done);
+    } else if (status == ACEAPEX_E_BUSY) {
+        n_busy++;
+    } else {
+        n_err++;
+    }
+    cv.notify_all();
+}
+
+void aceapex_server::finish_tick(Tick& t, int status) {
+    const int64_t tn = now();
+    for (uint32_t b : t.used) unpin(b);
+    if (status != ACEAPEX_OK)
+        for (uint32_t b : t.decoded)
+            if (pins[b] == 0) drop(b);
+    for (const Req& r : t.reqs) complete(r, status, tn);
+    free_events.push_back(t.done);
+}
+
+// Admit the arrived requests that fit and launch one tick; false if nothing
+// was launched.
+bool aceapex_server::form_tick() {
+    const Plan& P = A->plan;
+    const int set = (int)(ticks & 1);
+    TickBufs& B = bufs[set];
+    TickState T;
+    WalkJournal J;
+    std::vector<Req> admitted;
+    std::vector<uint32_t> new_blocks;  // scheduled and not resident: need a slot
+    const int64_t tn = now();
+    uint32_t avail = (uint32_t)(free_slots.size() + lru.size());
+    for (;;) {
+        Req r;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            if (queue.empty() || queue.top().at_ns > tn) break;
+            if (admitted.size() >= prm.max_tick_requests) break;
+            r = queue.top();
+        }
+        J.clear();
+        span_walk(P, *A->midx, r.start, r.len, &aceapex_server::valid_fn, this, &T, &J);
+        uint32_t need_slots = 0;
+        for (uint32_t b : J.added)
+            if (slot_of[b] == kNoSlot) need_slots++;
+        // blocks kept by the cache that this request reads must stay: they are
+        // pinned below, so they leave the evictable count
+        uint32_t newly_pinned = 0;
+        for (uint32_t b : J.used)
+            if (slot_of[b] != kNoSlot && pins[b] == 0 && in_lru[b]) newly_pinned++;
+        const bool fits = need_slots + newly_pinned <= avail && T.need.size() <= prm.max_tick_blocks;
+        if (!fits) {
+            span_undo(&T, J);
+            const bool never = admitted.empty() && inflight.empty();
+            if (!never) break;  // wait for slots to free up
+            // nothing else holds the cache: this request can never fit
+            {
+                std::lock_guard<std::mutex> g(mu);
+                queue.pop();
+            }
+            complete(r, ACEAPEX_E_BUSY, now());
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> g(mu);
+            queue.pop();
+        }
+        avail -= need_slots + newly_pinned;
+        for (uint32_t b : J.used) pin(b);
+        for (uint32_t b : J.added)
+            if (slot_of[b] == kNoSlot) new_blocks.push_back(b);
+        r.admit_ns = tn;
+        r.closure = (uint32_t)J.used.size();
+        r.decoded = (uint32_t)J.added.size();
+        admitted.push_back(r);
+    }
+    if (admitted.empty()) return false;
+    // slots for the new blocks: free ones first, then the least recently used
+    for (uint32_t b : new_blocks) {
+        uint32_t s;
+        if (!free_slots.empty()) {
+            s = free_slots.back();
+            free_slots.pop_back();
+        } else {
+            const uint32_t victim = lru.back();
+            lru.pop_back();
+            in_lru[victim] = 0;
+            s = slot_of[victim];
+            slot_of[victim] = kNoSlot;
+            valid[victim].clear();
+        }
+        slot_of[b] = s;
+    }
+    // work items: the blocks to decode, in block order, with their wanted bytes
+    std::vector<uint32_t> blocks;
+    blocks.reserve(T.need.size());
+    for (const auto& kv : T.need) blocks.push_back(kv.first);
+    std::sort(blocks.begin(), blocks.end());
+    std::vector<uint32_t> slots(blocks.size());
+    for (size_t i = 0; i < blocks.size(); i++) slots[i] = slot_of[blocks[i]];
+    SubsetPlan S;
+    subset_plan(P, blocks.data(), slots.data(), blocks.size(), &S);
+    std::vector<uint32_t> need, iv;
+    for (size_t i = 0; i < blocks.size(); i++) {
+        Ivs& nb = T.need[blocks[i]];
+        need_intervals(nb, P.blk[blocks[i]].raw_len, &iv);
+        S.items[i].need_off = (uint32_t)need.size();
+        S.items[i].need_n = (uint32_t)iv.size();
+        need.insert(need.end(), iv.begin(), iv.end());
+        valid[blocks[i]] = nb;  // kept once this tick has run (later ticks are ordered after it)
+    }
+    cudaError_t e;
+    int rc = ACEAPEX_OK;
+    const size_t nblk = blocks.size(), nreq = admitted.size();
+    if ((e = host_grow((void**)&B.h_items, &B.cap_items, std::max<size_t>(nblk, 1), sizeof(ItemDev))) != cudaSuccess ||
+        (e = host_grow((void**)&B.h_need, &B.cap_need, std::max<size_t>(need.size(), 1), sizeof(uint32_t))) != cudaSuccess ||
+        (e = host_grow((void**)&B.h_gather, &B.cap_gather, nreq, sizeof(GatherReq))) != cudaSuccess ||
+        (e = B.d_items.ensure(std::max<size_t>(nblk, 1) * sizeof(ItemDev))) != cudaSuccess ||
+        (e = B.d_need.ensure(std::max<size_t>(need.size(), 1) * sizeof(uint32_t))) != cudaSuccess ||
+        (e = B.d_gather.ensure(nreq * sizeof(GatherReq))) != cudaSuccess ||
+        (e = streams.ensure(S.scratch_bytes)) != cudaSuccess ||
+        (e = spans.ensure(std::max<uint64_t>(S.span_slots, 1) * sizeof(SpanRec))) != cudaSuccess ||
+        (e = lists.ensure(2 * std::max<uint64_t>(S.span_slots, 1) * sizeof(JobDev::ListEnt))) != cudaSuccess)
+        rc = cuda_fail(c, e, "server: tick buffers");
+    uint64_t max_len = 0;
+    if (rc == ACEAPEX_OK) {
+        if (nblk) memcpy(B.h_items, S.items.data(), nblk * sizeof(ItemDev));
+        if (!need.empty()) memcpy(B.h_need, need.data(), need.size() * sizeof(uint32_t));
+        for (size_t i = 0; i < nreq; i++) {
+            B.h_gather[i] = GatherReq{admitted[i].dst, admitted[i].start, admitted[i].len};
+            max_len = std::max(max_len, admitted[i].len);
+        }
+        if ((nblk && (e = cudaMemcpyAsync(B.d_items.p, B.h_items, nblk * sizeof(ItemDev), cudaMemcpyHostToDevice, st)) !=
+                         cudaSuccess) ||
+            (!need.empty() && (e = cudaMemcpyAsync(B.d_need.p, B.h_need, need.size() * sizeof(uint32_t),
+                                                   cudaMemcpyHostToDevice, st)) != cudaSuccess) ||
+            (e = cudaMemcpyAsync(B.d_gather.p, B.h_gather, nreq * sizeof(GatherReq), cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess)
+            rc = cuda_fail(c, e, "server: tick upload");
+    }
+    if (rc == ACEAPEX_OK && nblk) {
+        JobDev job{};
+        ArcJob& Jb = job.one;
+        Jb.arc = (const uint8_t*)A->d_arc;
+        Jb.blk = A->d_blk;
+        Jb.dtab = A->d_dtab;
+        Jb.scratch = (uint8_t*)streams.p;
+        Jb.out = cache;
+        Jb.npend = npend;
+        Jb.pmap = pmap;
+        Jb.spans = (SpanRec*)spans.p;
+        Jb.total = P.total;
+        Jb.n_blocks = P.n_blocks;
+        Jb.lo = 0;
+        Jb.hi = (uint32_t)nblk;
+        Jb.min_match = P.min_match;
+        Jb.deps = A->d_deps;
+        Jb.items = (const ItemDev*)B.d_items.p;
+        Jb.need = (const uint32_t*)B.d_need.p;
+        Jb.slot = d_slot;
+        job.n_arcs = 1;
+        job.n_items = (uint32_t)nblk;
+        job.counters = c->counters;
+        job.err = c->d_err;
+        job.timeout_ns = (uint64_t)c->params.timeout_us * 1000ull;
+        job.max_tok = S.max_tok;
+        job.max_lenb = S.max_lenb;
+        job.flags = need.empty() ? 0 : kJobNeed;
+        job.lists[0] = (JobDev::ListEnt*)lists.p;
+        job.lists[1] = job.lists[0] + std::max<uint64_t>(S.span_slots, 1);
+        LaunchPlan lp;
+        rc = launch_plan(c, c->params, S.max_tok, S.max_lenb, &lp, job.flags);
+        if (rc == ACEAPEX_OK) rc = enqueue_job(c, job, lp, 4, c->d_err, 4, st, nullptr);
+    } else if (rc == ACEAPEX_OK) {
+        if ((e = cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), st)) != cudaSuccess) rc = cuda_fail(c, e, "server");
+    }
+    if (rc == ACEAPEX_OK && (e = launch_gather(nullptr, (const GatherReq*)B.d_gather.p, (uint32_t)nreq, max_len, cache,
+                                               d_slot, st)) != cudaSuccess)
+        rc = cuda_fail(c, e, "server: gather launch");
+    if (rc == ACEAPEX_OK &&
+        (e = cudaMemcpyAsync(B.h_err, c->d_err, 4 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        rc = cuda_fail(c, e, "server: status copy");
+    Tick t;
+    t.set = set;
+    t.reqs.swap(admitted);
+    t.used.assign(T.used.begin(), T.used.end());
+    t.decoded = blocks;
+    if (rc == ACEAPEX_OK) {
+        if (free_events.empty()) {
+            cudaEvent_t ev;
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) rc = cuda_fail(c, e, "event");
+            else free_events.push_back(ev);
+        }
+    }
+    if (rc == ACEAPEX_OK) {
+        t.done = free_events.back();
+        free_events.pop_back();
+        if ((e = cudaEventRecord(t.done, st)) != cudaSuccess) {
+            free_events.push_back(t.done);
+            rc = cuda_fail(c, e, "event");
+        }
+    }
+    ticks++;
+    blk_decoded += nblk;
+    blk_hit += T.used.size() - T.need.size();
+    if (rc != ACEAPEX_OK) {
+        // the launch failed: nothing of this tick runs
+        cudaStreamSynchronize(st);
+        t.done = nullptr;
+        const int64_t tn2 = now();
+        for (uint32_t b : t.used) unpin(b);
+        for (uint32_t b : t.decoded)
+            if (pins[b] == 0) drop(b);
+        for (const Req& r : t.reqs) complete(r, rc, tn2);
+        std::lock_guard<std::mutex> g(mu);
+        fatal = rc;
+        fatal_msg = c->err;
+        return true;
+    }
+    inflight.push_back(std::move(t));
+    return true;
+}
+
+void aceapex_server::run() {
+    cudaSetDevice(c->device);
+    while (!stop.load()) {
+        // completed ticks, in order
+        while (!inflight.empty()) {
+            Tick& t = inflight.front();
+            const cudaError_t q = cudaEventQuery(t.done);
+            if (q == cudaErrorNotReady) break;
+            int status = ACEAPEX_OK;
+            if (q != cudaSuccess) {
+                status = ACEAPEX_E_CUDA;
+            } else if (bufs[t.set].h_err[0]) {
+                status = bufs[t.set].h_err[0];
+            }
+            finish_tick(t, status);
+            inflight.pop_front();
+        }
+        bool launched = false;
+        if (inflight.size() < 2 && !fatal) launched = form_tick();
+        if (launched) continue;
+        // nothing to launch: wait briefly for a completion or an arrival
+        int64_t next_at = -1;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            if (!queue.empty()) next_at = queue.top().at_ns;
+        }
+        if (!inflight.empty()) {
+            std::this_thread::yield();
+        } else {
+            std::unique_lock<std::mutex> g(mu);
+            const int64_t tn = now();
+            int64_t wait_ns = 2000000;
+            if (next_at >= 0) wait_ns = std::max<int64_t>(0, std::min<int64_t>(wait_ns, next_at - tn));
+            if (wait_ns > 20000)
+                cv.wait_for(g, std::chrono::nanoseconds(wait_ns - 10000));
+            else if (wait_ns > 0) {
+                g.unlock();
+                std::this_thread::yield();
+            }
+        }
+    }
+    // drain what is on the GPU
+    cudaStreamSynchronize(st);
+    while (!inflight.empty()) {
+        Tick& t = inflight.front();
+        finish_tick(t, cudaEventQuery(t.done) == cudaSuccess ? bufs[t.set].h_err[0] : ACEAPEX_E_CUDA);
+        inflight.pop_front();
+    }
+}
+
+static void server_free(aceapex_server* s) {
+    if (!s) return;
+    if (s->worker.joinable()) {
+        s->stop.store(true);
+        s->cv.notify_all();
+        s->worker.join();
+    }
+    if (s->c) cudaSetDevice(s->c->device);
+    if (s->st) cudaStreamSynchronize(s->st);
+    for (auto& ev : s->free_events) cudaEventDestroy(ev);
+    for (auto& B : s->bufs) {
+        if (B.h_items) cudaFreeHost(B.h_items);
+        if (B.h_need) cudaFreeHost(B.h_need);
+        if (B.h_gather) cudaFreeHost(B.h_gather);
+        if (B.h_err) cudaFreeHost(B.h_err);
+        B.d_items.release();
+        B.d_need.release();
+        B.d_gather.release();
+    }
+    s->streams.release();
+    s->spans.release();
+    s->lists.release();
+    if (s->cache) cudaFree(s->cache);
+    if (s->npend) cudaFree(s->npend);
+    if (s->pmap) cudaFree(s->pmap);
+    if (s->d_slot) cudaFree(s->d_slot);
+    if (s->st) cudaStreamDestroy(s->st);
+    if (s->c) aceapex_ctx_destroy(s->c);
+    delete s;
+}
+
+extern "C" {
+
+int aceapex_server_create(aceapex_ctx* ctx, aceapex_archive* A, const aceapex_server_params* p,
+                          aceapex_server** out) {
+    if (!ctx || !A || !out) return fail(ctx, ACEAPEX_E_ARG, "server_create: null argument");
+    *out = nullptr;
+    aceapex_server* s = new (std::nothrow) aceapex_server();
+    if (!s) return fail(ctx, ACEAPEX_E_NOMEM, "server_create: host allocation");
+    if (p) s->prm = *p;
+    if (!s->prm.cache_bytes) s->prm.cache_bytes = 4ull << 30;
+    if (!s->prm.max_tick_blocks) s->prm.max_tick_blocks = 16384;
+    if (!s->prm.max_tick_requests) s->prm.max_tick_requests = 4096;
+    s->A = A;
+    const uint32_t nb = A->plan.n_blocks;
+    s->n_slots = (uint32_t)std::min<uint64_t>(s->prm.cache_bytes / kBlock, 0xfffffff0u);
+    int rc = aceapex_ctx_create(ctx->device, &ctx->params, &s->c);
+    if (rc) {
+        delete s;
+        return fail(ctx, rc, "server_create: context");
+    }
+    if (s->n_slots == 0) {
+        server_free(s);
+        return fail(ctx, ACEAPEX_E_ARG, "server_create: cache smaller than one block");
+    }
+    // the byte-level closure needs the archive's match index
+    if ((rc = build_match_index(ctx, A))) {
+        server_free(s);
+        return rc;
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->cache, (size_t)s->n_slots * kBlock);
+    if (e == cudaSuccess) e = cudaMalloc(&s->npend, (size_t)s->n_slots * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->pmap, (size_t)s->n_slots * (kBlock / 8));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_slot, (size_t)std::max<uint32_t>(nb, 1) * 4);
+    if (e == cudaSuccess) e = cudaMemset(s->d_slot, 0xff, (size_t)std::max<uint32_t>(nb, 1) * 4);
+    if (e == cudaSuccess) e = cudaMemset(s->pmap, 0, (size_t)s->n_slots * (kBlock / 8));
+    for (auto& B : s->bufs)
+        if (e == cudaSuccess) e = cudaHostAlloc((void**)&B.h_err, 4 * sizeof(int), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        server_free(s);
+        return oom ? fail(ctx, ACEAPEX_E_NOMEM, "server_create: device memory for the cache")
+                   : cuda_fail(ctx, e, "server_create");
+    }
+    s->slot_of.assign(nb, kNoSlot);
+    s->valid.assign(nb, Ivs());
+    s->pins.assign(nb, 0);
+    s->lru_it.resize(nb);
+    s->in_lru.assign(nb, 0);
+    s->free_slots.resize(s->n_slots);
+    for (uint32_t i = 0; i < s->n_slots; i++) s->free_slots[i] = s->n_slots - 1 - i;
+    s->t0 = std::chrono::steady_clock::now();
+    s->worker = std::thread([s] { s->run(); });
+    *out = s;
+    return ACEAPEX_OK;
+}
+
+int64_t aceapex_server_now_ns(const aceapex_server* s) { return s ? s->now() : -1; }
+
+int aceapex_server_submit_many(aceapex_server* s, int n, const uint64_t* start, const uint64_t* len, void* const* d_out,
+                               const int64_t* at_ns, uint64_t* ids) {
+    if (!s || n < 0 || (n && (!start || !len || !d_out))) return ACEAPEX_E_ARG;
+    const uint64_t total = s->A->plan.total;
+    for (int i = 0; i < n; i++)
+        if (start[i] > total || len[i] > total - start[i] || (len[i] && !d_out[i])) return ACEAPEX_E_RANGE;
+    const int64_t tn = s->now();
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (s->fatal) return s->fatal;
+        for (int i = 0; i < n; i++) {
+            Req r;
+            r.id = s->next_id++;
+            r.start = start[i];
+            r.len = len[i];
+            r.dst = (uint8_t*)d_out[i];
+            r.at_ns = at_ns && at_ns[i] >= 0 ? at_ns[i] : tn;
+            if (ids) ids[i] = r.id;
+            s->queue.push(r);
+            s->submitted++;
+        }
+    }
+    s->cv.notify_all();
+    return ACEAPEX_OK;
+}
+
+int aceapex_server_submit(aceapex_server* s, uint64_t start, uint64_t len, void* d_out, int64_t at_ns, uint64_t* id) {
+    return aceapex_server_submit_many(s, 1, &start, &len, &d_out, &at_ns, id);
+}
+
+int aceapex_server_poll(aceapex_server* s, aceapex_completion* out, int max, int wait_ms) {
+    if (!s || max < 0 || (max && !out)) return ACEAPEX_E_ARG;
+    std::unique_lock<std::mutex> g(s->mu);
+    if (s->done.empty() && wait_ms > 0)
+        s->cv.wait_for(g, std::chrono::milliseconds(wait_ms), [s] { return !s->done.empty() || s->fatal; });
+    const int n = (int)std::min<size_t>(s->done.size(), (size_t)max);
+    for (int i = 0; i < n; i++) out[i] = s->done[i];
+    s->done.erase(s->done.begin(), s->done.begin() + n);
+    return n;
+}
+
+int aceapex_server_drain(aceapex_server* s, int timeout_ms) {
+    if (!s) return ACEAPEX_E_ARG;
+    std::unique_lock<std::mutex> g(s->mu);
+    const bool ok = s->cv.wait_for(g, std::chrono::milliseconds(timeout_ms),
+                                   [s] { return s->finished == s->submitted || s->fatal; });
+    if (s->fatal) return s->fatal;
+    return ok ? ACEAPEX_OK : ACEAPEX_E_TIMEOUT;
+}
+
+int aceapex_server_get_stats(aceapex_server* s, int reset, aceapex_server_stats* out) {
+    if (!s || !out) return ACEAPEX_E_ARG;
+    std::lock_guard<std::mutex> g(s->mu);
+    memset(out, 0, sizeof *out);
+    out->completed = s->n_ok;
+    out->failed = s->n_err;
+    out->refused = s->n_busy;
+    out->bytes = s->bytes;
+    out->ticks = s->ticks;
+    out->blocks_decoded = s->blk_decoded;
+    out->blocks_hit = s->blk_hit;
+    if (!s->lat_us.empty()) {
+        std::vector<double> v = s->lat_us;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5))]; };
+        out->p50_us = pct(0.50);
+        out->p99_us = pct(0.99);
+        out->max_us = v.back();
+        double sum = 0;
+        for (double x : v) sum += x;
+        out->mean_us = sum / v.size();
+        std::vector<uint32_t> cl = s->closures;
+        std::sort(cl.begin(), cl.end());
+        double cs = 0;
+        for (uint32_t x : cl) cs += x;
+        out->closure_mean = cs / cl.size();
+        out->closure_p50 = cl[(cl.size() - 1) / 2];
+        out->closure_p99 = cl[std::min(cl.size() - 1, (size_t)(0.99 * (cl.size() - 1) + 0.5))];
+        const double span_s = (double)(s->last_done - s->first_arrival) / 1e9;
+        out->seconds = span_s;
+        out->gbs = span_s > 0 ? (double)s->bytes / span_s / 1e9 : 0.0;
+    }
+    if (reset) {
+        s->lat_us.clear();
+        s->closures.clear();
+        s->n_ok = s->n_err = s->n_busy = s->bytes = s->ticks = s->blk_decoded = s->blk_hit = 0;
+        s->first_arrival = -1;
+        s->last_done = 0;
+    }
+    return ACEAPEX_OK;
+}
+
+const char* aceapex_server_last_error(const aceapex_server* s) { return s ? s->fatal_msg.c_str() : "null server"; }
+
+int aceapex_server_destroy(aceapex_server* s) {
+    if (!s) return ACEAPEX_E_ARG;
+    server_free(s);
+    return ACEAPEX_OK;
+}
+
+}  // extern "C"

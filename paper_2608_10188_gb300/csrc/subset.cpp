@@ -97,13 +97,36 @@ extern "C" int aceapex_decode_range(aceapex_ctx* c, aceapex_archive* A, uint64_t
     cudaSetDevice(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t b0 = (uint32_t)(start / kBlock), b1 = (uint32_t)((start + len - 1) / kBlock);
-    std::vector<uint32_t> blocks, slots;
-    block_closure(A, b0, b1, &blocks);
+    std::vector<uint32_t> blocks, slots, need;
+    std::vector<uint32_t> need_off, need_n;
+    uint32_t flags = 0;
+    if (A->midx) {
+        // byte-level closure through the match index: only the wanted bytes' chains
+        TickState T;
+        WalkJournal Jn;
+        span_walk(P, *A->midx, start, len, [](void*, uint32_t) -> const Ivs* { return nullptr; }, nullptr, &T, &Jn);
+        for (const auto& kv : T.need) blocks.push_back(kv.first);
+        std::sort(blocks.begin(), blocks.end());
+        std::vector<uint32_t> iv;
+        for (uint32_t b : blocks) {
+            need_intervals(T.need[b], P.blk[b].raw_len, &iv);
+            need_off.push_back((uint32_t)need.size());
+            need_n.push_back((uint32_t)iv.size());
+            need.insert(need.end(), iv.begin(), iv.end());
+        }
+        if (!need.empty()) flags = kJobNeed;
+    } else {
+        block_closure(A, b0, b1, &blocks);
+    }
     const size_t k = blocks.size();
     slots.resize(k);
     for (size_t i = 0; i < k; i++) slots[i] = (uint32_t)i;
     SubsetPlan S;
     subset_plan(P, blocks.data(), slots.data(), k, &S);
+    for (size_t i = 0; i < need_off.size(); i++) {
+        S.items[i].need_off = need_off[i];
+        S.items[i].need_n = need_n[i];
+    }
     int rc = ensure_slot_table(c, A);
     if (rc) return rc;
     cudaError_t e;
@@ -111,10 +134,13 @@ extern "C" int aceapex_decode_range(aceapex_ctx* c, aceapex_archive* A, uint64_t
         (e = c->pmap.ensure(k * (kBlock / 8))) != cudaSuccess ||
         (e = c->spans.ensure(S.span_slots * sizeof(SpanRec))) != cudaSuccess ||
         (e = c->lists.ensure(2 * S.span_slots * sizeof(JobDev::ListEnt))) != cudaSuccess ||
-        (e = c->slot_out.ensure(k * kBlock)) != cudaSuccess || (e = c->items.ensure(k * sizeof(ItemDev))) != cudaSuccess)
+        (e = c->slot_out.ensure(k * kBlock)) != cudaSuccess || (e = c->items.ensure(k * sizeof(ItemDev))) != cudaSuccess ||
+        (e = c->need.ensure(std::max<size_t>(need.size(), 1) * sizeof(uint32_t))) != cudaSuccess)
         return cuda_fail(c, e, "decode_range: scratch");
     if ((e = cudaMemcpyAsync(c->items.p, S.items.data(), k * sizeof(ItemDev), cudaMemcpyHostToDevice, st)) !=
-        cudaSuccess)
+            cudaSuccess ||
+        (!need.empty() && (e = cudaMemcpyAsync(c->need.p, need.data(), need.size() * sizeof(uint32_t),
+                                               cudaMemcpyHostToDevice, st)) != cudaSuccess))
         return cuda_fail(c, e, "decode_range: work items");
     JobDev job{};
     ArcJob& J = job.one;
@@ -134,6 +160,7 @@ extern "C" int aceapex_decode_range(aceapex_ctx* c, aceapex_archive* A, uint64_t
     J.item_base = 0;
     J.deps = A->d_deps;
     J.items = (const ItemDev*)c->items.p;
+    J.need = (const uint32_t*)c->need.p;
     J.slot = A->d_slot;
     job.n_arcs = 1;
     job.n_items = (uint32_t)k;
@@ -144,8 +171,9 @@ extern "C" int aceapex_decode_range(aceapex_ctx* c, aceapex_archive* A, uint64_t
     job.max_lenb = S.max_lenb;
     job.lists[0] = (JobDev::ListEnt*)c->lists.p;
     job.lists[1] = job.lists[0] + S.span_slots;
+    job.flags = flags;
     LaunchPlan lp;
-    if ((rc = launch_plan(c, c->params, S.max_tok, S.max_lenb, &lp))) return rc;
+    if ((rc = launch_plan(c, c->params, S.max_tok, S.max_lenb, &lp, flags))) return rc;
     if ((rc = enqueue_job(c, job, lp, 4, nullptr, 0, st, stats ? c->ev : nullptr))) return rc;
     const GatherReq req{(uint8_t*)d_out, start, len};
     if ((e = launch_gather(&req, nullptr, 1, len, J.out, A->d_slot, st)) != cudaSuccess)

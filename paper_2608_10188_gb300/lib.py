@@ -23,7 +23,9 @@ EXPORTED = [
     "aceapex_archive_get_info", "aceapex_decode_all", "aceapex_decode_all_async", "aceapex_sync",
     "aceapex_decode_host", "aceapex_archive_check", "aceapex_decode_noalloc", "aceapex_batch_create",
     "aceapex_batch_run_async", "aceapex_batch_wait", "aceapex_batch_run", "aceapex_batch_destroy",
-    "aceapex_batch_decode", "aceapex_decode_range",
+    "aceapex_batch_decode", "aceapex_decode_range", "aceapex_archive_index", "aceapex_server_create",
+    "aceapex_server_now_ns", "aceapex_server_submit_many", "aceapex_server_submit", "aceapex_server_poll",
+    "aceapex_server_drain", "aceapex_server_get_stats", "aceapex_server_last_error", "aceapex_server_destroy",
 ]
 BATCH_GRAPH = 1
 
@@ -31,7 +33,8 @@ BATCH_GRAPH = 1
 class EncParams(ctypes.Structure):
     _fields_ = [("no_rep", ctypes.c_int), ("min_match", ctypes.c_uint32), ("max_lanes", ctypes.c_uint32),
                 ("threads", ctypes.c_int), ("latest_source", ctypes.c_int),
-                ("max_depth", ctypes.c_uint32), ("short_latest", ctypes.c_int), ("deps", ctypes.c_int)]
+                ("max_depth", ctypes.c_uint32), ("short_latest", ctypes.c_int), ("deps", ctypes.c_int),
+                ("segment", ctypes.c_uint64)]
 
 
 class DecParams(ctypes.Structure):
@@ -55,6 +58,23 @@ class ArchiveInfo(ctypes.Structure):
 class BatchItem(ctypes.Structure):
     _fields_ = [("arc", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("out_cap", ctypes.c_uint64),
                 ("status", ctypes.c_int)]
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("cache_bytes", ctypes.c_uint64), ("max_tick_blocks", ctypes.c_uint32),
+                ("max_tick_requests", ctypes.c_uint32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("closure_blocks", ctypes.c_uint32),
+                ("decoded_blocks", ctypes.c_uint32), ("latency_us", ctypes.c_double), ("queue_us", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("completed", "failed", "refused", "bytes", "ticks", "blocks_decoded",
+                                               "blocks_hit")] + \
+               [(k, ctypes.c_double) for k in ("p50_us", "p99_us", "mean_us", "max_us", "closure_mean", "closure_p50",
+                                               "closure_p99", "seconds", "gbs")]
 
 
 class AceapexError(RuntimeError):
@@ -102,9 +122,22 @@ def load(path: str | None = None):
     L.aceapex_batch_run.argtypes = [vp, vp, c.POINTER(BatchItem), c.POINTER(Stats)]
     L.aceapex_batch_destroy.argtypes = [vp]
     L.aceapex_decode_range.argtypes = [vp, vp, u64, u64, vp, vp, c.POINTER(Stats)]
+    L.aceapex_archive_index.argtypes = [vp, vp]
+    L.aceapex_server_create.argtypes = [vp, vp, c.POINTER(ServerParams), c.POINTER(vp)]
+    L.aceapex_server_now_ns.argtypes = [vp]
+    L.aceapex_server_now_ns.restype = c.c_int64
+    L.aceapex_server_submit_many.argtypes = [vp, c.c_int, vp, vp, vp, vp, vp]
+    L.aceapex_server_submit.argtypes = [vp, u64, u64, vp, c.c_int64, c.POINTER(u64)]
+    L.aceapex_server_poll.argtypes = [vp, c.POINTER(Completion), c.c_int, c.c_int]
+    L.aceapex_server_drain.argtypes = [vp, c.c_int]
+    L.aceapex_server_get_stats.argtypes = [vp, c.c_int, c.POINTER(ServerStats)]
+    L.aceapex_server_last_error.argtypes = [vp]
+    L.aceapex_server_last_error.restype = c.c_char_p
+    L.aceapex_server_destroy.argtypes = [vp]
     L.aceapex_batch_decode.argtypes = [vp, c.POINTER(BatchItem), c.c_int, vp, c.POINTER(Stats)]
     for name in EXPORTED:
-        if name not in ("aceapex_status_string", "aceapex_last_error", "aceapex_free"):
+        if name not in ("aceapex_status_string", "aceapex_last_error", "aceapex_free", "aceapex_server_now_ns",
+                        "aceapex_server_last_error"):
             getattr(L, name).restype = c.c_int
     _lib = L
     return L
@@ -119,14 +152,15 @@ def _check(rc, ctx=None, what=""):
 
 
 def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, threads: int = 0,
-           latest_source: bool = False, max_depth: int = 0, short_latest: bool = False, deps: bool = False) -> bytes:
+           latest_source: bool = False, max_depth: int = 0, short_latest: bool = False, deps: bool = False,
+           segment: int = 0) -> bytes:
     """aceapex_encode on host bytes (numpy uint8 array or bytes)."""
     import numpy as np
     L = load()
     a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data,
                              dtype=np.uint8)
     p = EncParams(int(no_rep), min_match, max_lanes, threads, int(latest_source), max_depth, int(short_latest),
-                  int(deps))
+                  int(deps), segment)
     ptr = ctypes.c_void_p()
     n = ctypes.c_uint64()
     _check(L.aceapex_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(p), ctypes.byref(ptr),
@@ -186,6 +220,10 @@ class Archive:
         _check(ctx._L.aceapex_archive_get_info(self.h, ctypes.byref(info)), ctx.h, "archive_info")
         self.info = {k: getattr(info, k) for k, _ in ArchiveInfo._fields_}
         self._hbuf = None
+
+    def build_index(self):
+        """aceapex_archive_index: the match index for byte-level closures."""
+        _check(self.ctx._L.aceapex_archive_index(self.ctx.h, self.h), self.ctx.h, "archive_index")
 
     @property
     def total(self) -> int:
@@ -321,3 +359,74 @@ def batch_decode(ctx: Context, entries, stream: int = 0, stats: bool = False):
     if stats:
         return rc, per, {k: getattr(st, k) for k, _ in Stats._fields_}
     return rc, per
+
+
+class Server:
+    """aceapex_server: continuous-batching region server over one opened
+    archive with a bounded device cache of decoded blocks."""
+
+    def __init__(self, ctx: Context, arc: Archive, cache_bytes: int = 0, max_tick_blocks: int = 0,
+                 max_tick_requests: int = 0):
+        self.ctx = ctx
+        self.arc = arc
+        self._L = ctx._L
+        p = ServerParams(cache_bytes, max_tick_blocks, max_tick_requests)
+        h = ctypes.c_void_p()
+        _check(self._L.aceapex_server_create(ctx.h, arc.h, ctypes.byref(p), ctypes.byref(h)), ctx.h, "server_create")
+        self.h = h
+
+    def now_ns(self) -> int:
+        return self._L.aceapex_server_now_ns(self.h)
+
+    def submit_many(self, starts, lens, d_outs, at_ns=None):
+        """Queue regions (numpy arrays of uint64 starts/lengths, device
+        pointers, optional int64 arrival times on the server clock); returns
+        the request ids."""
+        import numpy as np
+        n = len(starts)
+        st = np.ascontiguousarray(starts, dtype=np.uint64)
+        ln = np.ascontiguousarray(lens, dtype=np.uint64)
+        dp = np.ascontiguousarray(d_outs, dtype=np.uint64)
+        at = None if at_ns is None else np.ascontiguousarray(at_ns, dtype=np.int64)
+        ids = np.zeros(n, dtype=np.uint64)
+        rc = self._L.aceapex_server_submit_many(self.h, n, st.ctypes.data, ln.ctypes.data, dp.ctypes.data,
+                                                at.ctypes.data if at is not None else None, ids.ctypes.data)
+        if rc != OK:
+            raise AceapexError(rc, "server_submit")
+        return ids
+
+    def submit(self, start: int, length: int, d_out: int, at_ns: int = -1) -> int:
+        i = ctypes.c_uint64()
+        rc = self._L.aceapex_server_submit(self.h, start, length, d_out, at_ns, ctypes.byref(i))
+        if rc != OK:
+            raise AceapexError(rc, "server_submit")
+        return i.value
+
+    def poll(self, max_n: int = 4096, wait_ms: int = 0):
+        buf = (Completion * max(max_n, 1))()
+        n = self._L.aceapex_server_poll(self.h, buf, max_n, wait_ms)
+        if n < 0:
+            raise AceapexError(n, "server_poll")
+        return [{k: getattr(buf[i], k) for k, _ in Completion._fields_} for i in range(n)]
+
+    def drain(self, timeout_ms: int = 60000) -> int:
+        return self._L.aceapex_server_drain(self.h, timeout_ms)
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        _check(self._L.aceapex_server_get_stats(self.h, int(reset), ctypes.byref(st)), None, "server_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def last_error(self) -> str:
+        return self._L.aceapex_server_last_error(self.h).decode()
+
+    def close(self):
+        if self.h:
+            self._L.aceapex_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

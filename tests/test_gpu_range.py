@@ -79,6 +79,37 @@ def ranges(total, seed, n=24):
     return [(s, l) for s, l in out if l > 0]
 
 
+@pytest.mark.parametrize("kind,no_rep", [("dna", False), ("dna", True), ("text", False)])
+def test_byte_level_closure_ranges_match_oracle(acx, ctx, kind, no_rep):
+    """With a match index the range decode follows byte-level chains only:
+    every region still equals the oracle's bytes, never touches more blocks
+    than its block-level closure, and on the genome far fewer (on Zipf text,
+    whose words are copied from anywhere in the short window, the two are
+    close)."""
+    data = synth.corpus(kind, (6 << 20) + 999, 13)
+    arc = acx.encode(data, no_rep=no_rep, deps=True)
+    ref = oracle.decode(arc)
+    op = Opened(acx, ctx, arc)
+    op.A.build_index()
+    torch = op.torch
+    stream = torch.cuda.current_stream().cuda_stream
+    touched, block_level = [], []
+    for s, ln in ranges(len(data), 9, n=40):
+        out = torch.full((ln + 32,), 0x5A, dtype=torch.uint8, device="cuda")
+        rc, st = acx.decode_range(ctx, op.A, s, ln, out.data_ptr(), stream, stats=True)
+        assert rc == 0, (s, ln, ctx.last_error())
+        o = out.cpu().numpy()
+        assert np.array_equal(o[:ln], ref[s:s + ln]), (s, ln)
+        assert np.all(o[ln:] == 0x5A)
+        if ln <= 32768 and s > len(data) // 2:
+            touched.append(st["blocks"])
+            block_level.append(closure_size(arc, s // BLOCK, (s + ln - 1) // BLOCK))
+    assert touched and all(t <= b for t, b in zip(touched, block_level))
+    if kind == "dna":  # copies of a few bytes each: chains stay narrow
+        assert np.mean(touched) < 0.5 * np.mean(block_level), (touched, block_level)
+    op.close()
+
+
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("deps", [True, False])
 @pytest.mark.parametrize("kind,no_rep", [("dna", False), ("dna", True), ("text", False)])

@@ -134,3 +134,23 @@ def test_library_dependency_lists_are_the_blocks_read(acx, kind, no_rep):
     plain = acx.encode(data, no_rep=no_rep)
     assert read_deps(plain)[0] == 0
     assert len(plain) < len(arc)
+
+
+def test_segmented_encode_keeps_sources_inside_segments(acx):
+    """Segmented parallel parse: every match reads inside its own segment
+    (checked on the oracle's parse), the archive decodes exactly, and the
+    size stays close to the single-parse archive."""
+    data = synth.dna((6 << 20) + 5000, 4)
+    seg = 1 << 20
+    arc = acx.encode(data, segment=seg, threads=4, deps=True)
+    assert np.array_equal(oracle.decode(arc), data)
+    nb = (len(data) + 16383) // 16384
+    for b in range(0, nb, 7):
+        t = oracle.parse_block(arc, b)
+        for s, m, d in zip(t["src"].tolist(), t["ml"].tolist(), t["dst"].tolist()):
+            if m:
+                assert s // seg == d // seg
+    whole = acx.encode(data)
+    assert len(arc) < 1.02 * len(whole) + 64 * 1024
+    with pytest.raises(acx.AceapexError):
+        acx.encode(data, segment=1000)  # not a multiple of the block size
