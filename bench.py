@@ -57,6 +57,8 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="batch: plain launches instead of a graph replay")
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="batch: keep the default lane cap and launch shapes")
     p.add_argument("--serve-gib", type=int, default=16, help="serve: genome size in GiB (256 MiB chromosomes)")
     p.add_argument("--serve-rate", type=float, default=20000.0, help="serve: Poisson arrivals per second")
     p.add_argument("--serve-seconds", type=float, default=10.0, help="serve: measured seconds (after 2 s warm-up)")
@@ -117,6 +119,42 @@ def cached_encode(args, acx, data, key, **kw):
     except OSError:
         pass
     return arc
+
+
+def tune_lanes(args, acx, torch, ctx, device):
+    """The encode-side tuning lever: the rANS lane cap.  Samples of both
+    corpora (8 MiB each, seeds 4000/4001) are encoded with every cap and
+    decoded as one batch; the cap with the fastest decode is used."""
+    from concurrent.futures import ThreadPoolExecutor
+    samples = [synth.dna(8 << 20, 4000), synth.text(8 << 20, 4001)]
+    flush = torch.empty(L2_FLUSH, dtype=torch.uint8, device=device)
+    sh = torch.cuda.current_stream().cuda_stream
+    res = {}
+    for K in (8, 16, 32, 64, 128):
+        with ThreadPoolExecutor(max_workers=2) as ex:
+            arcs = list(ex.map(lambda d: acx.encode(d, max_lanes=K, threads=1), samples))
+        keep, archives, outs = [], [], []
+        for a in arcs:
+            h = np.frombuffer(a, np.uint8).copy()
+            d = torch.from_numpy(h).to(device)
+            keep.append(d)
+            A = acx.Archive(ctx, d.data_ptr(), h, h.size)
+            archives.append(A)
+            outs.append(torch.empty(A.total, dtype=torch.uint8, device=device))
+        b = acx.Batch(ctx, [(A, o.data_ptr(), A.total) for A, o in zip(archives, outs)], graph=False)
+        ms = []
+        for r in range(6):
+            flush.fill_(1)
+            rc, _, st = b.run(sh, stats=True)
+            if rc != 0:
+                raise RuntimeError(f"lane tuning decode failed: {rc}")
+            if r:
+                ms.append(st["ms_total"])
+        b.close()
+        for A in archives:
+            A.close()
+        res[K] = statistics.median(ms)
+    return min(res, key=res.get), res
 
 
 def batch_archives(args, acx):
@@ -263,9 +301,12 @@ def run_batch(args, dist):
     dev = dist["local"]
     torch.cuda.set_device(dev)
     device = f"cuda:{dev}"
-    specs, pairs = batch_archives(args, acx)
     variant = acx.lib.VARIANT_PLAIN if args.variant == "plain" else acx.lib.VARIANT_FAST
     ctx = acx.Context(dev, variant=variant)
+    lanes_ms = None
+    if args.autotune:
+        args.lanes, lanes_ms = tune_lanes(args, acx, torch, ctx, device)
+    specs, pairs = batch_archives(args, acx)
     d_arcs, archives, outs = [], [], []
     for data, arc in pairs:
         h = np.frombuffer(arc, dtype=np.uint8).copy()
@@ -277,6 +318,10 @@ def run_batch(args, dist):
     total = sum(A.total for A in archives)
     arc_total = sum(len(a) for _, a in pairs)
     entries = [(A, o.data_ptr(), A.total) for A, o in zip(archives, outs)]
+    tuned = None
+    if args.autotune:
+        tuned = acx.tune.tuned_params(ctx, entries, f"batch96-k{args.lanes}-{encoder_key()}",
+                                      os.path.join(args.cache_dir, "autotune.json"), reps=3, device=dev)
     graph = not args.no_graph
     B = acx.Batch(ctx, entries, graph=graph)
     flush = torch.empty(L2_FLUSH, dtype=torch.uint8, device=device)
@@ -368,6 +413,10 @@ def run_batch(args, dist):
             "config": {"workload": f"batch of {len(specs)} archives, {total:,} B (log-uniform 64 KiB-64 MiB; "
                                    f"{kinds['dna']} DNA, {kinds['text']} text; history-free for i mod 4 in {{2,3}})",
                        "launch": "one CUDA graph replay per step" if graph else "one launch sequence per step",
+                       "autotuned": None if tuned is None else {
+                           "rans_lanes_ms": {str(k): round(v, 4) for k, v in lanes_ms.items()},
+                           "ctas_per_sm": tuned["ctas_per_sm"], "rans_ctas_per_sm": tuned["rans_ctas_per_sm"],
+                           "queue_chunk": tuned["queue_chunk"], "cached": tuned["cached"]},
                        "variant": args.variant, "rans_lanes": args.lanes, "blocks": n_blocks,
                        "archive_bytes": arc_total, "ratio": round(total / arc_total, 4),
                        "l2": "256 MiB buffer written between steps; per-step CUDA events exclude it"},

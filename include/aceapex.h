@@ -94,6 +94,7 @@ typedef struct {
     uint32_t timeout_us;  /* limit of every device-side dependency wait (default 2,000,000) */
     uint32_t ctas_per_sm; /* persistent CTAs per SM for the local pass (0 = occupancy maximum) */
     uint32_t rans_ctas_per_sm; /* persistent CTAs per SM for the entropy stage (0 = occupancy maximum) */
+    uint32_t queue_chunk; /* blocks a warp (entropy stage) or CTA (local pass) takes per queue ticket (0 = 1) */
 } aceapex_dec_params;
 
 /* Timing of the last call, measured with CUDA events on the call's stream
@@ -320,6 +321,25 @@ int aceapex_batch_run(aceapex_batch* batch, void* stream, aceapex_batch_item* it
 int aceapex_batch_destroy(aceapex_batch* batch);
 /* One-shot batch: create (no graph), run, destroy. */
 int aceapex_batch_decode(aceapex_ctx* ctx, aceapex_batch_item* items, int n, void* stream, aceapex_stats* stats);
+
+/*
+ * Autotuner (the paper has none; its decoders fix their launch shapes).
+ * Decodes the items as one batch under every point of the launch space —
+ * persistent CTAs per SM of the local pass (1..its occupancy) and of the
+ * entropy stage (1..its occupancy), blocks per queue ticket (1, 4, 16) — with
+ * the L2 flushed before each timed run (median of `reps` after one warm-up),
+ * writes up to max_points measured points, sets the context's parameters to
+ * the fastest (variant and timeout unchanged) and copies them to *best.
+ * The items' outputs are overwritten.  The encode-side lever of the same
+ * tuning, the rANS lane count, is a property of the archive (encoder
+ * max_lanes).
+ */
+typedef struct {
+    uint32_t ctas_per_sm, rans_ctas_per_sm, queue_chunk;
+    double ms;
+} aceapex_tune_point;
+int aceapex_autotune(aceapex_ctx* ctx, const aceapex_batch_item* items, int n, int reps, aceapex_tune_point* points,
+                     int max_points, int* n_points, aceapex_dec_params* best);
 
 /*
  * Decode without allocating anything (the paper has no counterpart: this is a

@@ -203,11 +203,18 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
     uint32_t phase = 0;
+    const uint32_t chunk = job.chunk ? job.chunk : 1u;
+    uint32_t cnext = 0, cleft = 0;  // the CTA's current run of `chunk` tickets
 
     for (;;) {
-        if (tid == 0) misc[0] = atomicAdd(&job.counters[1], 1u);
-        __syncthreads();
-        const uint32_t item = misc[0];
+        if (cleft == 0) {
+            if (tid == 0) misc[0] = atomicAdd(&job.counters[1], chunk);
+            __syncthreads();
+            cnext = misc[0];
+            cleft = chunk;
+        }
+        const uint32_t item = cnext++;
+        cleft--;
         if (item >= job.n_items) return;
         const int a = find_arc(job, item);
         const ArcJob J = load_arc(job, a);
@@ -651,6 +658,89 @@ __device__ __forceinline__ void append(bool keep, ListEnt e, ListEnt* list, uint
     if (keep) list[base + __popc(m & ((1u << lane) - 1))] = e;
 }
 
+// Round trace (diagnostics): work-list size and start time (ns) of every round.
+__device__ __forceinline__ void trace_round(const JobDev& job, uint32_t round, uint32_t n) {
+    if (round >= kTraceRounds) return;
+    job.counters[kTrace + 3 * round] = n;
+    const uint64_t t = gtimer();
+    job.counters[kTrace + 3 * round + 1] = (uint32_t)t;
+    job.counters[kTrace + 3 * round + 2] = (uint32_t)(t >> 32);
+}
+
+// A round that finished no piece.  In a valid archive the lowest pending
+// piece always has final sources (every source precedes its destination), so
+// the pieces left wait on bytes that no piece writes: their archives are
+// corrupt.
+__device__ void report_stalled(const JobDev& job, uint32_t in, uint32_t n, uint32_t w0, uint32_t nw, int lane) {
+    for (uint32_t i = w0 * 32 + lane; i < n; i += nw * 32) {
+        const ListEnt e = job.lists[in][i];
+        const int a = find_arc(job, e.y);
+        const ArcJob J = load_arc(job, a);
+        set_err_arc(job, a, kErrCorrupt, kStageSources << 24, item_ref(J, e.y - J.item_base).blk);
+    }
+}
+
+// One pass over work list `in` (n entries) by warps w0, w0 + nw, ...: every
+// piece is attempted once; the unfinished ones go to list `out`.
+__device__ void round_pass(const JobDev& job, uint32_t in, uint32_t out, uint32_t n, uint32_t w0, uint32_t nw,
+                           SpanRec* wrec, uint64_t* wdst, int lane) {
+    for (uint32_t i0 = w0 * 32; i0 < n; i0 += nw * 32) {
+        const uint32_t i = i0 + lane;
+        const bool has = i < n;
+        ListEnt e{0, 0};
+        if (has) e = job.lists[in][i];
+        // (the lanes' pieces may come from several archives: one archive at a time)
+        const int arc_i = has ? find_arc(job, e.y) : -1;
+        bool done = false;
+        uint32_t todo = __ballot_sync(ACX_FULL, has);
+        while (todo) {
+            const int a0 = __shfl_sync(ACX_FULL, arc_i, __ffs(todo) - 1);
+            const bool mine = has && arc_i == a0;
+            const ArcJob J = load_arc(job, a0);
+            SpanRec r{0, 0, 0, 0};
+            if (mine) r = J.spans[e.x];
+            const bool d2 = try_pieces(mine, J, mine ? item_ref(J, e.y - J.item_base).slot : 0, r, wrec, wdst, lane);
+            if (mine) done = d2;
+            todo &= ~__ballot_sync(ACX_FULL, mine);
+        }
+        append(has && !done, e, job.lists[out], &job.counters[kListCnt + out], lane);
+    }
+}
+
+// The last rounds on one CTA (the other CTAs have left): list `in` holds n
+// entries and the count of the other list is zero.  Rounds are separated by
+// CTA barriers; the same progress argument as the grid rounds ends them.
+constexpr uint32_t kSoloMax = 4 * kExtThreads;  // lists up to four CTA-wide passes
+__device__ void solo_rounds(const JobDev& job, uint32_t in, uint32_t n, uint32_t round, uint64_t deadline,
+                            SpanRec* wrec, uint64_t* wdst, int lane) {
+    __shared__ uint32_t n_next;
+    const uint32_t warp = threadIdx.x >> 5, nw = kExtThreads / 32;
+    for (;;) {
+        const uint32_t out = in ^ 1u;
+        round_pass(job, in, out, n, warp, nw, wrec, wdst, lane);
+        __syncthreads();  // every append of this round is visible to the CTA
+        if (threadIdx.x == 0) {
+            n_next = *((volatile uint32_t*)&job.counters[kListCnt + out]);
+            job.counters[kListCnt + in] = 0;  // list `in` becomes the next output
+            trace_round(job, ++round, n_next);
+            if (n_next) atomicAdd(&job.counters[kStatPolls], 1u);
+        }
+        __syncthreads();
+        const uint32_t m = n_next;
+        if (m == 0) return;
+        if (m == n) {
+            report_stalled(job, out, m, warp, nw, lane);
+            return;
+        }
+        if (__syncthreads_or(gtimer() > deadline)) {
+            if (threadIdx.x == 0) set_err(job.err, kErrTimeout, kStageWait << 24, 0);
+            return;
+        }
+        in = out;
+        n = m;
+    }
+}
+
 // Cross-block pass in rounds.  Round 0 walks every block's pending spans (in
 // ascending order); each later round walks the spans the previous round could
 // not finish.  A span is attempted once per round and never waited on, so
@@ -756,54 +846,21 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             return;
         }
         const uint32_t n = *((volatile uint32_t*)&job.counters[kListCnt + in]);
-        if (blockIdx.x == 0 && threadIdx.x == 0 && round < kTraceRounds) {
-            // round trace: work-list size and start time (ns) of every round
-            job.counters[kTrace + 3 * round] = n;
-            const uint64_t t = gtimer();
-            job.counters[kTrace + 3 * round + 1] = (uint32_t)t;
-            job.counters[kTrace + 3 * round + 2] = (uint32_t)(t >> 32);
-        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) trace_round(job, round, n);
         if (n == 0) return;
         if (n == n_prev) {
-            // the last round finished no piece.  In a valid archive the lowest
-            // pending piece always has final sources (every source precedes its
-            // destination), so the pieces left wait on bytes that no piece
-            // writes: their archives are corrupt.
-            for (uint32_t i = gwarp * 32 + lane; i < n; i += nwarps * 32) {
-                const ListEnt e = job.lists[in][i];
-                const int a = find_arc(job, e.y);
-                const ArcJob J = load_arc(job, a);
-                set_err_arc(job, a, kErrCorrupt, kStageSources << 24, item_ref(J, e.y - J.item_base).blk);
-            }
+            report_stalled(job, in, n, gwarp, nwarps, lane);
             return;
         }
         n_prev = n;
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&job.counters[kStatPolls], 1u);
-        if (round > (1u << 20)) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) set_err(job.err, kErrTimeout, kStageWait << 24, 0);
+        if (n <= kSoloMax) {
+            // a short list: one CTA finishes the remaining rounds with CTA
+            // barriers instead of grid barriers
+            if (blockIdx.x == 0) solo_rounds(job, in, n, round, deadline, wrec, wdst, lane);
             return;
         }
-        for (uint32_t i0 = gwarp * 32; i0 < n; i0 += nwarps * 32) {
-            const uint32_t i = i0 + lane;
-            const bool has = i < n;
-            ListEnt e{0, 0};
-            if (has) e = job.lists[in][i];
-            // (the lanes' pieces may come from several archives: one archive at a time)
-            const int arc_i = has ? find_arc(job, e.y) : -1;
-            bool done = false;
-            uint32_t todo = __ballot_sync(ACX_FULL, has);
-            while (todo) {
-                const int a0 = __shfl_sync(ACX_FULL, arc_i, __ffs(todo) - 1);
-                const bool mine = has && arc_i == a0;
-                const ArcJob J = load_arc(job, a0);
-                SpanRec r{0, 0, 0, 0};
-                if (mine) r = J.spans[e.x];
-                const bool d2 = try_pieces(mine, J, mine ? item_ref(J, e.y - J.item_base).slot : 0, r, wrec, wdst, lane);
-                if (mine) done = d2;
-                todo &= ~__ballot_sync(ACX_FULL, mine);
-            }
-            append(has && !done, e, job.lists[out], &job.counters[kListCnt + out], lane);
-        }
+        round_pass(job, in, out, n, gwarp, nwarps, wrec, wdst, lane);
     }
 }
 

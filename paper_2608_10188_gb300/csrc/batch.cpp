@@ -281,3 +281,81 @@ int aceapex_batch_decode(aceapex_ctx* c, aceapex_batch_item* items, int n, void*
 }
 
 }  // extern "C"
+
+// ---- autotuner ----------------------------------------------------------------------------
+// Times one batch under every point of the decoder's launch space — CTAs per
+// SM of the local pass and of the entropy stage, blocks per queue ticket —
+// with the L2 flushed before each run, and keeps the fastest.
+extern "C" int aceapex_autotune(aceapex_ctx* c, const aceapex_batch_item* items, int n, int reps,
+                                aceapex_tune_point* points, int max_points, int* n_points, aceapex_dec_params* best) {
+    if (!c || n <= 0 || !items || max_points < 0 || (max_points && !points))
+        return fail(c, ACEAPEX_E_ARG, "autotune: bad argument");
+    if (reps <= 0) reps = 3;
+    cudaSetDevice(c->device);
+    const aceapex_dec_params base = c->params;
+    aceapex_batch* B = nullptr;
+    int rc = aceapex_batch_create(c, items, n, 0, &B);
+    if (rc) return rc;
+    void* flush = nullptr;
+    const size_t flush_bytes = 256u << 20;  // larger than L2
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaMalloc(&flush, flush_bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        aceapex_batch_destroy(B);
+        if (flush) cudaFree(flush);
+        return cuda_fail(c, e, "autotune");
+    }
+    const size_t lsm = local_smem_bytes(B->job.max_tok, B->job.max_lenb);
+    const int occ_local = base.variant == ACEAPEX_VARIANT_PLAIN ? 1 : std::max(1, local_occupancy(lsm));
+    std::vector<uint32_t> locals, ranss;
+    for (int v : {1, 2, 3, 4, 6, 8, 12, 16})
+        if (v <= occ_local) locals.push_back((uint32_t)v);
+    for (int v = 1; v <= c->occ_rans; v++) ranss.push_back((uint32_t)v);
+    const uint32_t chunks[] = {1, 4, 16};
+    double best_ms = 1e30;
+    aceapex_dec_params best_p = base;
+    int np = 0;
+    std::vector<float> t;
+    for (uint32_t lc : locals)
+        for (uint32_t rcn : ranss)
+            for (uint32_t ch : chunks) {
+                aceapex_dec_params p = base;
+                p.ctas_per_sm = lc;
+                p.rans_ctas_per_sm = rcn;
+                p.queue_chunk = ch;
+                LaunchPlan lp;
+                if ((rc = launch_plan(c, p, B->job.max_tok, B->job.max_lenb, &lp))) break;
+                B->lp = lp;
+                t.clear();
+                for (int r = 0; r <= reps && rc == ACEAPEX_OK; r++) {
+                    cudaMemsetAsync(flush, r & 0xff, flush_bytes, st);
+                    if ((rc = aceapex_batch_run_async(B, st))) break;
+                    aceapex_stats s;
+                    if ((rc = aceapex_batch_wait(B, st, nullptr, &s))) break;
+                    if (r) t.push_back((float)s.ms_total);  // the first run warms up
+                }
+                if (rc) break;
+                std::sort(t.begin(), t.end());
+                const double ms = t[t.size() / 2];
+                if (np < max_points) {
+                    points[np].ctas_per_sm = lc;
+                    points[np].rans_ctas_per_sm = rcn;
+                    points[np].queue_chunk = ch;
+                    points[np].ms = ms;
+                }
+                np++;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_p = p;
+                }
+            }
+    cudaStreamDestroy(st);
+    cudaFree(flush);
+    aceapex_batch_destroy(B);
+    if (n_points) *n_points = std::min(np, max_points);
+    if (rc) return rc;
+    c->params = best_p;
+    if (best) *best = best_p;
+    return ACEAPEX_OK;
+}

@@ -100,7 +100,7 @@ std::string device_error_text(const int h[3]);
 
 // Grid sizes and variant of one decode job.
 struct LaunchPlan {
-    uint32_t variant = 0;
+    uint32_t variant = 0, chunk = 1;
     int grid_rans = 0, grid_local = 0, grid_plain = 0, grid_ext = 0;
 };
 // Grids for a job whose largest block has max_tok tokens and max_lenb length

@@ -133,6 +133,7 @@ struct JobDev {
     uint32_t max_tok;         // shared-memory sizing of the assembly kernel
     uint32_t max_lenb;
     uint32_t flags;           // kJob* bits
+    uint32_t chunk;           // work items per ticket of the entropy stage and the local pass (0 = 1)
     struct alignas(8) ListEnt {
         uint32_t x, y;        // span slot, item
     };

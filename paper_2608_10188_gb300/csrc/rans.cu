@@ -325,10 +325,17 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
             if (threadIdx.x == 0) S.arc = a;
         }
         const uint32_t n_a = J.hi - J.lo;
+        const uint32_t chunk = job.chunk ? job.chunk : 1u;
+        uint32_t cnext = 0, cleft = 0;  // this warp's current run of `chunk` tickets
         for (;;) {
-            uint32_t it = 0;
-            if (lane == 0) it = atomicAdd(&tickets[a], 1u);
-            it = __shfl_sync(ACX_FULL, it, 0);
+            if (cleft == 0) {
+                uint32_t t0 = 0;
+                if (lane == 0) t0 = atomicAdd(&tickets[a], chunk);
+                cnext = __shfl_sync(ACX_FULL, t0, 0);
+                cleft = chunk;
+            }
+            const uint32_t it = cnext++;
+            cleft--;
             if (it >= n_a) break;
             const ItemRef ir = item_ref(J, it);
             const uint32_t b = ir.blk;

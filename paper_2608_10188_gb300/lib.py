@@ -26,6 +26,7 @@ EXPORTED = [
     "aceapex_batch_decode", "aceapex_decode_range", "aceapex_archive_index", "aceapex_server_create",
     "aceapex_server_now_ns", "aceapex_server_submit_many", "aceapex_server_submit", "aceapex_server_poll",
     "aceapex_server_drain", "aceapex_server_get_stats", "aceapex_server_last_error", "aceapex_server_destroy",
+    "aceapex_autotune",
 ]
 BATCH_GRAPH = 1
 
@@ -39,7 +40,7 @@ class EncParams(ctypes.Structure):
 
 class DecParams(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("timeout_us", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("rans_ctas_per_sm", ctypes.c_uint32)]
+                ("rans_ctas_per_sm", ctypes.c_uint32), ("queue_chunk", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -75,6 +76,11 @@ class ServerStats(ctypes.Structure):
                                                "blocks_hit")] + \
                [(k, ctypes.c_double) for k in ("p50_us", "p99_us", "mean_us", "max_us", "closure_mean", "closure_p50",
                                                "closure_p99", "seconds", "gbs")]
+
+
+class TunePoint(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_uint32), ("rans_ctas_per_sm", ctypes.c_uint32),
+                ("queue_chunk", ctypes.c_uint32), ("ms", ctypes.c_double)]
 
 
 class AceapexError(RuntimeError):
@@ -134,6 +140,8 @@ def load(path: str | None = None):
     L.aceapex_server_last_error.argtypes = [vp]
     L.aceapex_server_last_error.restype = c.c_char_p
     L.aceapex_server_destroy.argtypes = [vp]
+    L.aceapex_autotune.argtypes = [vp, c.POINTER(BatchItem), c.c_int, c.c_int, c.POINTER(TunePoint), c.c_int,
+                                   c.POINTER(c.c_int), c.POINTER(DecParams)]
     L.aceapex_batch_decode.argtypes = [vp, c.POINTER(BatchItem), c.c_int, vp, c.POINTER(Stats)]
     for name in EXPORTED:
         if name not in ("aceapex_status_string", "aceapex_last_error", "aceapex_free", "aceapex_server_now_ns",
@@ -166,7 +174,12 @@ def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, 
     _check(L.aceapex_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(p), ctypes.byref(ptr),
                             ctypes.byref(n)), None, "encode")
     try:
-        return ctypes.string_at(ptr.value, n.value)
+        if n.value < (1 << 31):
+            return ctypes.string_at(ptr.value, n.value)
+        # ctypes.string_at takes a C int size: copy larger archives by memmove
+        buf = bytearray(n.value)
+        ctypes.memmove((ctypes.c_char * n.value).from_buffer(buf), ptr.value, n.value)
+        return bytes(buf)
     finally:
         L.aceapex_free(ptr)
 
@@ -175,17 +188,17 @@ class Context:
     """aceapex_ctx on one CUDA device."""
 
     def __init__(self, device: int = 0, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0,
-                 rans_ctas_per_sm: int = 0):
+                 rans_ctas_per_sm: int = 0, queue_chunk: int = 0):
         L = load()
         self._L = L
-        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm)
+        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm, queue_chunk)
         h = ctypes.c_void_p()
         _check(L.aceapex_ctx_create(device, ctypes.byref(self.params), ctypes.byref(h)), None, "ctx_create")
         self.h = h
 
     def set_params(self, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0,
-                   rans_ctas_per_sm: int = 0):
-        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm)
+                   rans_ctas_per_sm: int = 0, queue_chunk: int = 0):
+        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm, queue_chunk)
         _check(self._L.aceapex_ctx_set_params(self.h, ctypes.byref(self.params)), self.h, "set_params")
 
     def close(self):
@@ -430,3 +443,17 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def autotune(ctx: Context, entries, reps: int = 3, max_points: int = 512):
+    """aceapex_autotune over a list of (Archive, d_out, out_cap): returns
+    (best params dict, measured points).  The context keeps the best params."""
+    items = _items(entries)
+    pts = (TunePoint * max_points)()
+    npts = ctypes.c_int()
+    best = DecParams()
+    _check(ctx._L.aceapex_autotune(ctx.h, items, len(entries), reps, pts, max_points, ctypes.byref(npts),
+                                   ctypes.byref(best)), ctx.h, "autotune")
+    ctx.params = best
+    b = {k: getattr(best, k) for k, _ in DecParams._fields_}
+    return b, [{k: getattr(pts[i], k) for k, _ in TunePoint._fields_} for i in range(npts.value)]

@@ -210,3 +210,29 @@ def test_full_batch_workload(acx, ctx):
         assert np.array_equal(op.result(i)[0], oracle.decode(arcs[i]))
     b.close()
     op.close()
+
+
+def test_autotune_picks_a_measured_point_and_keeps_parity(acx, ctx, mixed, tmp_path):
+    """aceapex_autotune times the batch over the launch space and leaves the
+    context on the fastest measured point; decoding with it stays exact, and
+    the JSON cache returns the same point without measuring again."""
+    op = Opened(acx, ctx, [a for _, a in mixed])
+    best, points = acx.autotune(ctx, op.entries(), reps=2)
+    assert points and min(p["ms"] for p in points) == min(
+        p["ms"] for p in points if (p["ctas_per_sm"], p["rans_ctas_per_sm"], p["queue_chunk"]) ==
+        (best["ctas_per_sm"], best["rans_ctas_per_sm"], best["queue_chunk"]))
+    assert {p["queue_chunk"] for p in points} == {1, 4, 16}
+    op.poison()
+    b = acx.Batch(ctx, op.entries(), graph=True)
+    rc, per = b.run(op.torch.cuda.current_stream().cuda_stream)
+    assert rc == 0 and per == [0] * len(mixed)
+    for i, (data, _) in enumerate(mixed):
+        assert np.array_equal(op.result(i)[0], data)
+    b.close()
+    path = str(tmp_path / "tune.json")
+    first = acx.tune.tuned_params(ctx, op.entries(), "mixed-small", path, reps=1)
+    again = acx.tune.tuned_params(ctx, op.entries(), "mixed-small", path)
+    assert again["cached"] and not first["cached"]
+    assert all(first[k] == again[k] for k in ("ctas_per_sm", "rans_ctas_per_sm", "queue_chunk"))
+    ctx.set_params(variant=FAST, timeout_us=2_000_000)
+    op.close()
