@@ -52,6 +52,8 @@ def parse_args():
     p.add_argument("--encoding", default="history", choices=["history", "no_rep"])
     p.add_argument("--variant", default="fast", choices=["fast", "plain"])
     p.add_argument("--lanes", type=int, default=32)
+    p.add_argument("--wait-ns", type=int, default=0,
+                   help="decoder: first cross-block round's wait per piece (0: library default)")
     p.add_argument("--max-depth", type=int, default=0,
                    help="encoder chain-depth cap (0: the library default of 16)")
     p.add_argument("--e2e-steps", type=int, default=5)
@@ -596,7 +598,7 @@ def main():
     size, wname = workload(args)
     data, arc = get_archive(args, acx)
     variant = acx.lib.VARIANT_PLAIN if args.variant == "plain" else acx.lib.VARIANT_FAST
-    ctx = acx.Context(dev, variant=variant)
+    ctx = acx.Context(dev, variant=variant, wait_ns=args.wait_ns)
     h_arc = np.frombuffer(arc, dtype=np.uint8).copy()
     d_arc = torch.from_numpy(h_arc).to(f"cuda:{dev}")
     A = acx.Archive(ctx, d_arc.data_ptr(), h_arc, h_arc.size)

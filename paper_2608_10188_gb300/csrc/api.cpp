@@ -239,6 +239,7 @@ int acx::launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_t
     // parse-only and wanted-byte jobs run the scan decoder (the serial one has neither mode)
     lp->variant = (job_flags & (kJobIndex | kJobNeed)) ? (uint32_t)ACEAPEX_VARIANT_FAST : p.variant;
     lp->chunk = p.queue_chunk ? p.queue_chunk : 1;
+    lp->wait_ns = p.wait_ns;
     lp->grid_rans = (p.rans_ctas_per_sm ? std::min<int>(c->occ_rans, (int)p.rans_ctas_per_sm) : c->occ_rans) * c->n_sms;
     lp->grid_ext = c->occ_ext * c->n_sms;
     lp->grid_plain = c->occ_plain * c->n_sms;
@@ -260,6 +261,7 @@ int acx::enqueue_job(aceapex_ctx* c, const JobDev& job_in, const LaunchPlan& lp,
                      uint32_t n_errs, cudaStream_t st, cudaEvent_t* ev) {
     JobDev job = job_in;
     job.chunk = lp.chunk;
+    job.wait_ns = lp.wait_ns;
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return cuda_fail(c, e, "event");
     if ((e = launch_prologue(job.counters, n_counters, st, errs, n_errs)) != cudaSuccess)

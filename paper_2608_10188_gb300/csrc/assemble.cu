@@ -550,7 +550,7 @@ __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t 
 }
 
 constexpr int kExtThreads = 1024;  // one CTA per SM: grid barriers stay cheap
-constexpr uint64_t kRound0WaitNs = 4000;  // how long a round-0 lane waits for its sources
+constexpr uint32_t kRound0WaitNs = 4000;  // default wait of a round-0 piece for its sources
 
 // Are the bytes a piece reads final?  (period 0: [src, src+len); otherwise the
 // residues phase.. of the period window [src, src+period), one or two ranges.)
@@ -769,6 +769,7 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
     // short while for sources that are about to be finished by lower pieces,
     // then defers its piece to the rounds below.
     {
+        const uint64_t wait_ns = job.wait_ns == 0xffffffffu ? ~0ull : (job.wait_ns ? job.wait_ns : kRound0WaitNs);
         uint32_t blk = 0, dsl = 0, cnt = 0, next = 0, base = 0, item = 0;
         int arc = 0;
         bool exhausted = false;
@@ -824,7 +825,7 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
                 todo &= ~__ballot_sync(ACX_FULL, mine);
             }
             // give up on pieces that waited too long: the rounds finish them
-            const bool giveup = has && gtimer() - t0 > kRound0WaitNs;
+            const bool giveup = has && gtimer() - t0 > wait_ns;
             append(giveup, ListEnt{l_span, l_item}, job.lists[0], &job.counters[kListCnt], lane);
             if (giveup) has = false;
             if (__any_sync(ACX_FULL, progressed || giveup)) {

@@ -157,13 +157,44 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
     return ACEAPEX_OK;
 }
 
+void acx::TickState::begin(uint32_t n_blocks, uint64_t n_match) {
+    if (sched_mark.size() != n_blocks) {
+        sched_mark.assign(n_blocks, 0);
+        used_mark.assign(n_blocks, 0);
+        touch_req.assign(n_blocks, 0);
+        need.assign(n_blocks, Ivs());
+        epoch = 0;
+    }
+    if (match_mark.size() != n_match) {
+        match_mark.assign(n_match, 0);
+        epoch = 0;
+    }
+    if (++epoch == 0) {  // the stamps wrapped: clear them once
+        std::fill(sched_mark.begin(), sched_mark.end(), 0);
+        std::fill(used_mark.begin(), used_mark.end(), 0);
+        std::fill(match_mark.begin(), match_mark.end(), 0);
+        epoch = 1;
+    }
+    sched.clear();
+    used.clear();
+}
+
 void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t len, ValidFn valid, void* self,
                     TickState* T, WalkJournal* J) {
-    struct R {
-        uint32_t b, s, e;
-    };
-    std::vector<R> stack;
-    Ivs parts;
+    (void)P;
+    const uint32_t ep = T->epoch;
+    if (++T->req == 0) {
+        std::fill(T->touch_req.begin(), T->touch_req.end(), 0);
+        T->req = 1;
+    }
+    const uint32_t rq = T->req;
+    J->saved.clear();
+    J->taken.clear();
+    J->sched0 = T->sched.size();
+    J->used0 = T->used.size();
+    auto& stack = T->stack;
+    Ivs& parts = T->parts;
+    stack.clear();
     auto push_abs = [&](uint64_t s, uint64_t e) {  // absolute [s, e), split by block
         for (uint64_t a = s / kBlock; a <= (e - 1) / kBlock; a++) {
             const uint64_t A0 = a * kBlock;
@@ -172,31 +203,35 @@ void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t
     };
     if (len) push_abs(start, start + len);
     while (!stack.empty()) {
-        const R r = stack.back();
+        const TickState::R r = stack.back();
         stack.pop_back();
         if (r.s >= r.e) continue;
         const uint32_t X = r.b;
-        if (T->used.insert(X).second) J->used.push_back(X);
-        auto nit = T->need.find(X);
-        if (nit == T->need.end()) {
+        if (T->used_mark[X] != ep) {
+            T->used_mark[X] = ep;
+            T->used.push_back(X);
+        }
+        Ivs& nX = T->need[X];
+        if (T->sched_mark[X] != ep) {
             const Ivs* V = valid(self, X);
             if (V && iv_covers(*V, r.s, r.e)) continue;  // kept from an earlier decode
-            nit = T->need.emplace(X, Ivs()).first;
-            J->added.push_back(X);
+            T->sched_mark[X] = ep;
+            T->touch_req[X] = rq;
+            T->sched.push_back(X);
+            nX.clear();
             // a block decoded again keeps what it held: its kept bytes are wanted too
             if (V)
                 for (const auto& iv : *V) stack.push_back({X, iv.first, iv.second});
         }
-        iv_minus(r.s, r.e, nit->second, &parts);
+        iv_minus(r.s, r.e, nX, &parts);
         if (parts.empty()) continue;
-        if (std::find(J->added.begin(), J->added.end(), X) == J->added.end()) {
-            bool saved = false;
-            for (const auto& sv : J->saved) saved |= sv.first == X;
-            if (!saved) J->saved.push_back({X, nit->second});
+        if (T->touch_req[X] != rq) {  // scheduled by an earlier request: keep its need for an undo
+            T->touch_req[X] = rq;
+            J->saved.push_back({X, nX});
         }
         const uint64_t lo = M.first[X], hi = M.first[X + 1];
         for (const auto& p : parts) {
-            iv_add(nit->second, p.first, p.second);
+            iv_add(nX, p.first, p.second);
             // matches of X overlapping p (matches are disjoint and in order)
             uint64_t a = lo, z = hi;
             while (a < z) {
@@ -204,7 +239,8 @@ void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t
                 if ((uint32_t)M.o[m] + M.ml[m] <= p.first) a = m + 1; else z = m;
             }
             for (uint64_t k = a; k < hi && M.o[k] < p.second; k++) {
-                if (!T->taken.insert(k).second) continue;
+                if (T->match_mark[k] == ep) continue;
+                T->match_mark[k] = ep;
                 J->taken.push_back(k);
                 const uint32_t o = M.o[k], ml = M.ml[k];
                 stack.push_back({X, o, o + ml});  // the whole match is decoded
@@ -217,10 +253,15 @@ void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t
 }
 
 void acx::span_undo(TickState* T, const WalkJournal& J) {
-    for (uint32_t b : J.added) T->need.erase(b);
+    for (size_t i = J.sched0; i < T->sched.size(); i++) {
+        T->sched_mark[T->sched[i]] = 0;
+        T->need[T->sched[i]].clear();
+    }
+    T->sched.resize(J.sched0);
     for (const auto& sv : J.saved) T->need[sv.first] = sv.second;
-    for (uint64_t k : J.taken) T->taken.erase(k);
-    for (uint32_t b : J.used) T->used.erase(b);
+    for (size_t i = J.used0; i < T->used.size(); i++) T->used_mark[T->used[i]] = 0;
+    T->used.resize(J.used0);
+    for (uint64_t k : J.taken) T->match_mark[k] = 0;
 }
 
 void acx::need_intervals(const Ivs& need, uint32_t raw_len, std::vector<uint32_t>* out) {
@@ -232,4 +273,45 @@ void acx::need_intervals(const Ivs& need, uint32_t raw_len, std::vector<uint32_t
 extern "C" int aceapex_archive_index(aceapex_ctx* c, aceapex_archive* A) {
     if (!c || !A) return fail(c, ACEAPEX_E_ARG, "archive_index: null argument");
     return build_match_index(c, A);
+}
+
+// Diagnostics (not part of the documented ABI; host only): the byte-level
+// closure of [start, start + len) of an archive given as host bytes, under a
+// match index given as arrays (first[n_blocks + 1], o/ml/src[n_match]).
+// Writes the closure's blocks in ascending order to blocks[], each block's
+// interval count to iv_count[] and its wanted intervals (start | end << 16)
+// to ivs[]; *n_blocks gets the block count.  Returns 0, -1 when a capacity is
+// too small, -2 for a corrupt archive.
+extern "C" int acx_debug_closure(const uint8_t* h_arc, uint64_t arc_len, const uint64_t* first, uint64_t n_match,
+                                 const uint16_t* o, const uint16_t* ml, const uint64_t* src, uint64_t start,
+                                 uint64_t len, uint32_t* blocks, uint32_t* iv_count, uint32_t* ivs,
+                                 uint32_t cap_blocks, uint32_t cap_ivs, uint32_t* n_blocks) {
+    Plan P;
+    std::string why;
+    if (build_plan(h_arc, arc_len, &P, &why) != 0) return -2;
+    if (start > P.total || len > P.total - start) return -1;
+    MatchIndex M;
+    M.first.assign(first, first + P.n_blocks + 1);
+    M.o.assign(o, o + n_match);
+    M.ml.assign(ml, ml + n_match);
+    M.src.assign(src, src + n_match);
+    TickState T;
+    WalkJournal J;
+    T.begin(P.n_blocks, n_match);
+    span_walk(P, M, start, len, [](void*, uint32_t) -> const Ivs* { return nullptr; }, nullptr, &T, &J);
+    std::vector<uint32_t> bl(T.sched.begin(), T.sched.end());
+    std::sort(bl.begin(), bl.end());
+    if (bl.size() > cap_blocks) return -1;
+    uint32_t k = 0;
+    for (size_t i = 0; i < bl.size(); i++) {
+        blocks[i] = bl[i];
+        const Ivs& v = T.need[bl[i]];
+        iv_count[i] = (uint32_t)v.size();
+        for (const auto& iv : v) {
+            if (k >= cap_ivs) return -1;
+            ivs[k++] = iv.first | (iv.second << 16);
+        }
+    }
+    *n_blocks = (uint32_t)bl.size();
+    return 0;
 }

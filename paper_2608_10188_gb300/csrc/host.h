@@ -100,7 +100,7 @@ std::string device_error_text(const int h[3]);
 
 // Grid sizes and variant of one decode job.
 struct LaunchPlan {
-    uint32_t variant = 0, chunk = 1;
+    uint32_t variant = 0, chunk = 1, wait_ns = 0;
     int grid_rans = 0, grid_local = 0, grid_plain = 0, grid_ext = 0;
 };
 // Grids for a job whose largest block has max_tok tokens and max_lenb length
@@ -138,18 +138,32 @@ int build_match_index(aceapex_ctx* c, aceapex_archive* A);
 // matches taken, blocks read) and journals its changes so that they can be
 // undone when the request is not admitted.
 struct TickState {
-    std::unordered_map<uint32_t, Ivs> need;   // blocks to decode -> wanted intervals
-    std::unordered_set<uint64_t> taken;       // matches already followed
-    std::unordered_set<uint32_t> used;        // every block read (decoded or kept)
+    // Per block and per match, marks stamped with the tick's epoch (no
+    // clearing between ticks), and the tick's lists.
+    uint32_t epoch = 0, req = 0;
+    std::vector<uint32_t> sched_mark, used_mark, touch_req;  // per block
+    std::vector<Ivs> need;                                    // per block: wanted intervals (when scheduled)
+    std::vector<uint32_t> match_mark;                         // per match: followed this tick
+    std::vector<uint32_t> sched;                              // blocks to decode, in scheduling order
+    std::vector<uint32_t> used;                               // every block read (decoded or kept)
+    struct R {
+        uint32_t b, s, e;
+    };
+    std::vector<R> stack;
+    Ivs parts;
+    // Start a tick over an archive of n_blocks blocks and n_match matches.
+    void begin(uint32_t n_blocks, uint64_t n_match);
+    bool scheduled(uint32_t b) const { return sched_mark[b] == epoch; }
 };
 struct WalkJournal {
-    std::vector<std::pair<uint32_t, Ivs>> saved;  // need of a block before its first change (scheduled before)
-    std::vector<uint32_t> added;                  // blocks newly scheduled
+    std::vector<std::pair<uint32_t, Ivs>> saved;  // need of a block scheduled by an earlier request, before this one
+    size_t sched0 = 0, used0 = 0;                 // list lengths before the request
     std::vector<uint64_t> taken;
-    std::vector<uint32_t> used;
-    void clear() { saved.clear(); added.clear(); taken.clear(); used.clear(); }
 };
 typedef const Ivs* (*ValidFn)(void* self, uint32_t block);
+// Walk one request's region; returns nothing, the tick state grows.  The
+// blocks the request scheduled are T->sched[J->sched0 ..], the blocks it read
+// first are T->used[J->used0 ..].
 void span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t len, ValidFn valid, void* self,
                TickState* T, WalkJournal* J);
 void span_undo(TickState* T, const WalkJournal& J);

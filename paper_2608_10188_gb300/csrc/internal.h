@@ -134,6 +134,8 @@ struct JobDev {
     uint32_t max_lenb;
     uint32_t flags;           // kJob* bits
     uint32_t chunk;           // work items per ticket of the entropy stage and the local pass (0 = 1)
+    uint32_t wait_ns;         // cross-block round 0: how long a piece may wait for its sources before it
+                              // is left to the later rounds (0xffffffff: until the deadline)
     struct alignas(8) ListEnt {
         uint32_t x, y;        // span slot, item
     };

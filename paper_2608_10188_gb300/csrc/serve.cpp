@@ -104,6 +104,8 @@ struct aceapex_server {
     std::vector<std::list<uint32_t>::iterator> lru_it;
     std::vector<uint8_t> in_lru;
     std::vector<uint32_t> free_slots;
+    TickState walk;                  // closure walk state, reused by every tick
+    WalkJournal journal;
     // requests
     std::mutex mu;
     std::condition_variable cv;
@@ -200,8 +202,9 @@ bool aceapex_server::form_tick() {
     const Plan& P = A->plan;
     const int set = (int)(ticks & 1);
     TickBufs& B = bufs[set];
-    TickState T;
-    WalkJournal J;
+    TickState& T = walk;
+    WalkJournal& J = journal;
+    T.begin(P.n_blocks, A->midx->o.size());
     std::vector<Req> admitted;
     std::vector<uint32_t> new_blocks;  // scheduled and not resident: need a slot
     const int64_t tn = now();
@@ -214,17 +217,19 @@ bool aceapex_server::form_tick() {
             if (admitted.size() >= prm.max_tick_requests) break;
             r = queue.top();
         }
-        J.clear();
+
         span_walk(P, *A->midx, r.start, r.len, &aceapex_server::valid_fn, this, &T, &J);
         uint32_t need_slots = 0;
-        for (uint32_t b : J.added)
-            if (slot_of[b] == kNoSlot) need_slots++;
+        for (size_t i = J.sched0; i < T.sched.size(); i++)
+            if (slot_of[T.sched[i]] == kNoSlot) need_slots++;
         // blocks kept by the cache that this request reads must stay: they are
         // pinned below, so they leave the evictable count
         uint32_t newly_pinned = 0;
-        for (uint32_t b : J.used)
+        for (size_t i = J.used0; i < T.used.size(); i++) {
+            const uint32_t b = T.used[i];
             if (slot_of[b] != kNoSlot && pins[b] == 0 && in_lru[b]) newly_pinned++;
-        const bool fits = need_slots + newly_pinned <= avail && T.need.size() <= prm.max_tick_blocks;
+        }
+        const bool fits = need_slots + newly_pinned <= avail && T.sched.size() <= prm.max_tick_blocks;
         if (!fits) {
             span_undo(&T, J);
             const bool never = admitted.empty() && inflight.empty();
@@ -242,12 +247,12 @@ bool aceapex_server::form_tick() {
             queue.pop();
         }
         avail -= need_slots + newly_pinned;
-        for (uint32_t b : J.used) pin(b);
-        for (uint32_t b : J.added)
-            if (slot_of[b] == kNoSlot) new_blocks.push_back(b);
+        for (size_t i = J.used0; i < T.used.size(); i++) pin(T.used[i]);
+        for (size_t i = J.sched0; i < T.sched.size(); i++)
+            if (slot_of[T.sched[i]] == kNoSlot) new_blocks.push_back(T.sched[i]);
         r.admit_ns = tn;
-        r.closure = (uint32_t)J.used.size();
-        r.decoded = (uint32_t)J.added.size();
+        r.closure = (uint32_t)(T.used.size() - J.used0);
+        r.decoded = (uint32_t)(T.sched.size() - J.sched0);
         admitted.push_back(r);
     }
     if (admitted.empty()) return false;
@@ -268,9 +273,7 @@ bool aceapex_server::form_tick() {
         slot_of[b] = s;
     }
     // work items: the blocks to decode, in block order, with their wanted bytes
-    std::vector<uint32_t> blocks;
-    blocks.reserve(T.need.size());
-    for (const auto& kv : T.need) blocks.push_back(kv.first);
+    std::vector<uint32_t> blocks(T.sched.begin(), T.sched.end());
     std::sort(blocks.begin(), blocks.end());
     std::vector<uint32_t> slots(blocks.size());
     for (size_t i = 0; i < blocks.size(); i++) slots[i] = slot_of[blocks[i]];
@@ -378,7 +381,7 @@ bool aceapex_server::form_tick() {
     }
     ticks++;
     blk_decoded += nblk;
-    blk_hit += T.used.size() - T.need.size();
+    blk_hit += T.used.size() - T.sched.size();
     if (rc != ACEAPEX_OK) {
         // the launch failed: nothing of this tick runs
         cudaStreamSynchronize(st);

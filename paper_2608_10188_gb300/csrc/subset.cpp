@@ -104,8 +104,9 @@ extern "C" int aceapex_decode_range(aceapex_ctx* c, aceapex_archive* A, uint64_t
         // byte-level closure through the match index: only the wanted bytes' chains
         TickState T;
         WalkJournal Jn;
+        T.begin(P.n_blocks, A->midx->o.size());
         span_walk(P, *A->midx, start, len, [](void*, uint32_t) -> const Ivs* { return nullptr; }, nullptr, &T, &Jn);
-        for (const auto& kv : T.need) blocks.push_back(kv.first);
+        blocks.assign(T.sched.begin(), T.sched.end());
         std::sort(blocks.begin(), blocks.end());
         std::vector<uint32_t> iv;
         for (uint32_t b : blocks) {

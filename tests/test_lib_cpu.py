@@ -154,3 +154,76 @@ def test_segmented_encode_keeps_sources_inside_segments(acx):
     assert len(arc) < 1.02 * len(whole) + 64 * 1024
     with pytest.raises(acx.AceapexError):
         acx.encode(data, segment=1000)  # not a multiple of the block size
+
+
+def _match_index(arc, nb):
+    """The archive's matches block by block, from the oracle's parse."""
+    first, o, ml, src = [0], [], [], []
+    for b in range(nb):
+        t = oracle.parse_block(arc, b)
+        for m, d, s in zip(t["ml"].tolist(), t["dst"].tolist(), t["src"].tolist()):
+            if m:
+                o.append(d - 16384 * b)
+                ml.append(m)
+                src.append(s)
+        first.append(len(o))
+    return (np.array(first, np.uint64), np.array(o, np.uint16), np.array(ml, np.uint16), np.array(src, np.uint64))
+
+
+def _closure(acx, arc, idx, start, length):
+    import ctypes
+    L = acx.load()
+    f = L.acx_debug_closure
+    vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+    f.argtypes = [vp, u64, vp, u64, vp, vp, vp, u64, u64, vp, vp, vp, u32, u32, vp]
+    f.restype = ctypes.c_int
+    first, o, ml, src = idx
+    a = np.frombuffer(arc, np.uint8)
+    cap = 1 << 16
+    blocks, cnt, ivs = np.zeros(cap, np.uint32), np.zeros(cap, np.uint32), np.zeros(cap * 4, np.uint32)
+    n = np.zeros(1, np.uint32)
+    rc = f(a.ctypes.data, a.size, first.ctypes.data, o.size, o.ctypes.data, ml.ctypes.data, src.ctypes.data,
+           start, length, blocks.ctypes.data, cnt.ctypes.data, ivs.ctypes.data, cap, cap * 4, n.ctypes.data)
+    assert rc == 0
+    out, k = {}, 0
+    for i in range(int(n[0])):
+        out[int(blocks[i])] = [(int(v) & 0xffff, int(v) >> 16) for v in ivs[k:k + int(cnt[i])]]
+        k += int(cnt[i])
+    return out
+
+
+@pytest.mark.parametrize("kind,no_rep", [("dna", False), ("dna", True), ("text", False)])
+def test_byte_level_closure_is_sufficient(acx, kind, no_rep):
+    """The byte-level closure walk (Random Access at Scale): decoding only the
+    closure's blocks, and in them only the matches touching their wanted
+    bytes (byte-serially, in output order, everything else left at zero),
+    reproduces the requested region exactly; the wanted bytes cover the
+    region and every wanted match lies inside them."""
+    data = synth.corpus(kind, (1 << 20) + 333, 21)
+    arc = acx.encode(data, no_rep=no_rep)
+    nb = (data.size + 16383) // 16384
+    idx = _match_index(arc, nb)
+    toks = [oracle.parse_block(arc, b) for b in range(nb)]
+    lits = [oracle.block_stream(arc, b, 3) for b in range(nb)]
+    rng = np.random.default_rng(3)
+    regions = [(0, 1), (data.size - 1, 1), (16380, 10)]
+    regions += [(int(s), int(l)) for l in rng.integers(1, 40000, 12)
+                for s in [rng.integers(0, data.size - l)]]
+    for start, length in regions:
+        need = _closure(acx, arc, idx, start, length)
+        # the region's bytes are wanted
+        for p in range(start // 16384, (start + length - 1) // 16384 + 1):
+            s0, e0 = max(start, 16384 * p) - 16384 * p, min(start + length, 16384 * (p + 1)) - 16384 * p
+            assert any(s <= s0 and e0 <= e for s, e in need[p]), (start, length, p)
+        out = np.zeros(data.size, np.uint8)
+        for b in sorted(need):
+            t, lit, B = toks[b], lits[b], 16384 * b
+            ivs = need[b]
+            for ll, m, d, s, li in zip(t["ll"].tolist(), t["ml"].tolist(), t["dst"].tolist(), t["src"].tolist(),
+                                       t["lit"].tolist()):
+                out[d - ll:d] = lit[li:li + ll]
+                if m and any(s0 < d - B + m and d - B < e0 for s0, e0 in ivs):
+                    assert any(s0 <= d - B and d - B + m <= e0 for s0, e0 in ivs)  # the whole match is wanted
+                    for j in range(m):
+                        out[d + j] = out[s + j]
+        assert np.array_equal(out[start:start + length], data[start:start + length]), (start, length)
