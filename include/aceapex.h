@@ -95,10 +95,12 @@ typedef struct {
     uint32_t ctas_per_sm; /* persistent CTAs per SM for the local pass (0 = occupancy maximum) */
     uint32_t rans_ctas_per_sm; /* persistent CTAs per SM for the entropy stage (0 = occupancy maximum) */
     uint32_t queue_chunk; /* blocks a warp (entropy stage) or CTA (local pass) takes per queue ticket (0 = 1) */
-    uint32_t wait_ns;     /* cross-block pass, first round: how long a match piece waits for its sources before
-                             it is left to the later, barrier-separated rounds (0 = 4000; 0xFFFFFFFF = no
-                             limit short of timeout_us: pieces are handed out in output order, so the lowest
-                             unfinished one always has final sources and the first round finishes them all) */
+    uint32_t wait_ns;     /* cross-block pass, first round: how long a match piece may wait for its sources
+                             before it is left to the later, barrier-separated rounds; 0xFFFFFFFF = no limit
+                             short of timeout_us (pieces are handed out in output order, so the lowest
+                             unfinished one always has final sources and the first round finishes them all);
+                             0 = automatic: no limit while the pending pieces are at most 16 per thread of the
+                             pass's grid, else 4000 (many pieces with long chains would clog the hand-out) */
 } aceapex_dec_params;
 
 /* Timing of the last call, measured with CUDA events on the call's stream

@@ -123,7 +123,13 @@ __device__ __forceinline__ HMap hmap_compose(const HMap& f, const HMap& g) {
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const uint64_t x = g.e[k];
-        r.e[k] = (x & kRefTag) ? f.e[x & 3] : x;
+        const uint32_t j = (uint32_t)x & 3;
+        // f.e[j] by selects, so that the maps stay in registers
+        uint64_t v = f.e[0];
+        v = j == 1 ? f.e[1] : v;
+        v = j == 2 ? f.e[2] : v;
+        v = j == 3 ? f.e[3] : v;
+        r.e[k] = (x & kRefTag) ? v : x;
     }
     return r;
 }
@@ -178,7 +184,7 @@ __device__ __forceinline__ void copy_run(uint8_t* __restrict__ sout, const uint8
     }
 }
 
-__global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
+__global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
     extern __shared__ __align__(128) uint8_t sm[];
     const LocLayout L = loc_layout(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0);
     uint8_t* sout = sm + L.out;
@@ -356,16 +362,24 @@ __global__ void __launch_bounds__(kLocThreads, 8) k_local(JobDev job) {
             HMap agg = hmap_identity();
             for (uint32_t i = i0; i < i1; i++)
                 agg = hmap_compose(agg, hmap_token(tcmd[i], B + tpos[i] + tll[i] - tsrc[i]));
-            hbuf[tid] = agg;
-            __syncthreads();
-            for (int o = 1; o < kLocThreads; o <<= 1) {  // inclusive Hillis-Steele scan of the maps
-                const HMap mine = hbuf[tid];
-                const HMap prev = tid >= o ? hbuf[tid - o] : hmap_identity();
-                __syncthreads();
-                if (tid >= o) hbuf[tid] = hmap_compose(prev, mine);
-                __syncthreads();
+            // inclusive scan of the maps: shuffles inside each warp, then the
+            // warps' totals (earlier maps act first)
+            HMap inc = agg;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                HMap prev;
+#pragma unroll
+                for (int k = 0; k < 4; k++) prev.e[k] = __shfl_up_sync(ACX_FULL, inc.e[k], o);
+                if (lane >= o) inc = hmap_compose(prev, inc);
             }
-            const HMap pre = tid > 0 ? hbuf[tid - 1] : hmap_identity();
+            if (lane == 31) hbuf[warp] = inc;
+            __syncthreads();
+            HMap pre = hmap_identity();
+            for (int w = 0; w < warp; w++) pre = hmap_compose(pre, hbuf[w]);
+            HMap ex;
+#pragma unroll
+            for (int k = 0; k < 4; k++) ex.e[k] = __shfl_up_sync(ACX_FULL, inc.e[k], 1);
+            if (lane > 0) pre = hmap_compose(pre, ex);
             uint64_t h[4];
             const uint64_t h0[4] = {1, 2, 3, 4};  // initial history, reset per block
 #pragma unroll
@@ -550,7 +564,8 @@ __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t 
 }
 
 constexpr int kExtThreads = 1024;  // one CTA per SM: grid barriers stay cheap
-constexpr uint32_t kRound0WaitNs = 4000;  // default wait of a round-0 piece for its sources
+constexpr uint32_t kRound0WaitNs = 4000;  // wait of a round-0 piece for its sources when they are many
+constexpr uint32_t kWaitAllPerLane = 16;   // pieces per grid lane up to which round 0 waits without limit
 
 // Are the bytes a piece reads final?  (period 0: [src, src+len); otherwise the
 // residues phase.. of the period window [src, src+period), one or two ranges.)
@@ -769,7 +784,17 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
     // short while for sources that are about to be finished by lower pieces,
     // then defers its piece to the rounds below.
     {
-        const uint64_t wait_ns = job.wait_ns == 0xffffffffu ? ~0ull : (job.wait_ns ? job.wait_ns : kRound0WaitNs);
+        // wait_ns 0 (automatic): in output order, waiting pieces cost little
+        // while pieces are few per lane of the grid; with many (long, wide
+        // chains, e.g. text) waiting lanes would clog the hand-out, so a piece
+        // that waited kRound0WaitNs goes to the rounds
+        uint64_t wait_ns;
+        if (job.wait_ns == 0) {
+            const uint64_t pieces = *((volatile uint32_t*)&job.counters[kStatPending]);
+            wait_ns = pieces <= kWaitAllPerLane * (uint64_t)gridDim.x * blockDim.x ? ~0ull : kRound0WaitNs;
+        } else {
+            wait_ns = job.wait_ns == 0xffffffffu ? ~0ull : job.wait_ns;
+        }
         uint32_t blk = 0, dsl = 0, cnt = 0, next = 0, base = 0, item = 0;
         int arc = 0;
         bool exhausted = false;
@@ -779,7 +804,7 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
         uint32_t l_blk = 0, l_dsl = 0, l_span = 0, l_item = 0;
         int l_arc = 0;
         uint64_t t0 = 0;
-        uint32_t spins = 0;
+        uint32_t spins = 0, nap = 64;
         const uint32_t lt_mask = (1u << lane) - 1;
         for (;;) {
             uint32_t idle = __ballot_sync(ACX_FULL, !has);
@@ -830,8 +855,10 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             if (giveup) has = false;
             if (__any_sync(ACX_FULL, progressed || giveup)) {
                 spins = 0;
+                nap = 64;
             } else {
-                __nanosleep(64);
+                __nanosleep(nap);
+                if (wait_ns == ~0ull) nap = min(2 * nap, 1024u);  // long waits: fewer polls of the bitmaps
                 if ((++spins & 255) == 0 && __any_sync(ACX_FULL, gtimer() > deadline)) {
                     if (lane == 0) set_err_arc(job, l_arc, kErrTimeout, kStageWait << 24, l_blk);
                     break;

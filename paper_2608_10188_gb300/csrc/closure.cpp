@@ -41,6 +41,13 @@ void iv_minus(uint32_t s, uint32_t e, const Ivs& v, Ivs* out) {
     if (s < e) out->push_back({s, e});
 }
 
+// Does [s, e) meet the union of v?
+bool iv_meets(const Ivs& v, uint32_t s, uint32_t e) {
+    auto it = std::upper_bound(v.begin(), v.end(), std::make_pair(s, 0xffffffffu));
+    if (it != v.begin() && std::prev(it)->second > s) return true;
+    return it != v.end() && it->first < e;
+}
+
 // v |= [s, e)
 void iv_add(Ivs& v, uint32_t s, uint32_t e) {
     auto it = std::lower_bound(v.begin(), v.end(), std::make_pair(s, 0u));
@@ -157,7 +164,7 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
     return ACEAPEX_OK;
 }
 
-void acx::TickState::begin(uint32_t n_blocks, uint64_t n_match) {
+void acx::TickState::begin(uint32_t n_blocks) {
     if (sched_mark.size() != n_blocks) {
         sched_mark.assign(n_blocks, 0);
         used_mark.assign(n_blocks, 0);
@@ -165,14 +172,9 @@ void acx::TickState::begin(uint32_t n_blocks, uint64_t n_match) {
         need.assign(n_blocks, Ivs());
         epoch = 0;
     }
-    if (match_mark.size() != n_match) {
-        match_mark.assign(n_match, 0);
-        epoch = 0;
-    }
     if (++epoch == 0) {  // the stamps wrapped: clear them once
         std::fill(sched_mark.begin(), sched_mark.end(), 0);
         std::fill(used_mark.begin(), used_mark.end(), 0);
-        std::fill(match_mark.begin(), match_mark.end(), 0);
         epoch = 1;
     }
     sched.clear();
@@ -189,7 +191,6 @@ void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t
     }
     const uint32_t rq = T->req;
     J->saved.clear();
-    J->taken.clear();
     J->sched0 = T->sched.size();
     J->used0 = T->used.size();
     auto& stack = T->stack;
@@ -230,8 +231,9 @@ void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t
             J->saved.push_back({X, nX});
         }
         const uint64_t lo = M.first[X], hi = M.first[X + 1];
+        // Every byte enters the wanted set together with all matches that
+        // touch it, so a match touching the wanted set is already followed.
         for (const auto& p : parts) {
-            iv_add(nX, p.first, p.second);
             // matches of X overlapping p (matches are disjoint and in order)
             uint64_t a = lo, z = hi;
             while (a < z) {
@@ -239,15 +241,14 @@ void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t
                 if ((uint32_t)M.o[m] + M.ml[m] <= p.first) a = m + 1; else z = m;
             }
             for (uint64_t k = a; k < hi && M.o[k] < p.second; k++) {
-                if (T->match_mark[k] == ep) continue;
-                T->match_mark[k] = ep;
-                J->taken.push_back(k);
                 const uint32_t o = M.o[k], ml = M.ml[k];
+                if (iv_meets(nX, o, o + ml)) continue;
                 stack.push_back({X, o, o + ml});  // the whole match is decoded
                 const uint64_t dst = (uint64_t)X * kBlock + o, src = M.src[k];
                 const uint64_t d = dst - src;
                 push_abs(src, src + std::min<uint64_t>(d, ml));  // its source window (one period if it overlaps)
             }
+            iv_add(nX, p.first, p.second);
         }
     }
 }
@@ -261,8 +262,9 @@ void acx::span_undo(TickState* T, const WalkJournal& J) {
     for (const auto& sv : J.saved) T->need[sv.first] = sv.second;
     for (size_t i = J.used0; i < T->used.size(); i++) T->used_mark[T->used[i]] = 0;
     T->used.resize(J.used0);
-    for (uint64_t k : J.taken) T->match_mark[k] = 0;
 }
+
+void acx::iv_union(Ivs& v, uint32_t s, uint32_t e) { iv_add(v, s, e); }
 
 void acx::need_intervals(const Ivs& need, uint32_t raw_len, std::vector<uint32_t>* out) {
     out->clear();
@@ -297,7 +299,7 @@ extern "C" int acx_debug_closure(const uint8_t* h_arc, uint64_t arc_len, const u
     M.src.assign(src, src + n_match);
     TickState T;
     WalkJournal J;
-    T.begin(P.n_blocks, n_match);
+    T.begin(P.n_blocks);
     span_walk(P, M, start, len, [](void*, uint32_t) -> const Ivs* { return nullptr; }, nullptr, &T, &J);
     std::vector<uint32_t> bl(T.sched.begin(), T.sched.end());
     std::sort(bl.begin(), bl.end());

@@ -143,7 +143,6 @@ struct TickState {
     uint32_t epoch = 0, req = 0;
     std::vector<uint32_t> sched_mark, used_mark, touch_req;  // per block
     std::vector<Ivs> need;                                    // per block: wanted intervals (when scheduled)
-    std::vector<uint32_t> match_mark;                         // per match: followed this tick
     std::vector<uint32_t> sched;                              // blocks to decode, in scheduling order
     std::vector<uint32_t> used;                               // every block read (decoded or kept)
     struct R {
@@ -151,14 +150,13 @@ struct TickState {
     };
     std::vector<R> stack;
     Ivs parts;
-    // Start a tick over an archive of n_blocks blocks and n_match matches.
-    void begin(uint32_t n_blocks, uint64_t n_match);
+    // Start a tick over an archive of n_blocks blocks.
+    void begin(uint32_t n_blocks);
     bool scheduled(uint32_t b) const { return sched_mark[b] == epoch; }
 };
 struct WalkJournal {
     std::vector<std::pair<uint32_t, Ivs>> saved;  // need of a block scheduled by an earlier request, before this one
     size_t sched0 = 0, used0 = 0;                 // list lengths before the request
-    std::vector<uint64_t> taken;
 };
 typedef const Ivs* (*ValidFn)(void* self, uint32_t block);
 // Walk one request's region; returns nothing, the tick state grows.  The
@@ -167,6 +165,8 @@ typedef const Ivs* (*ValidFn)(void* self, uint32_t block);
 void span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t len, ValidFn valid, void* self,
                TickState* T, WalkJournal* J);
 void span_undo(TickState* T, const WalkJournal& J);
+// v |= [s, e) for a sorted disjoint interval list.
+void iv_union(Ivs& v, uint32_t s, uint32_t e);
 // The interval list of a block to decode, or empty when it covers the block.
 void need_intervals(const Ivs& need, uint32_t raw_len, std::vector<uint32_t>* out);
 

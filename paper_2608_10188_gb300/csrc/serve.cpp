@@ -104,8 +104,26 @@ struct aceapex_server {
     std::vector<std::list<uint32_t>::iterator> lru_it;
     std::vector<uint8_t> in_lru;
     std::vector<uint32_t> free_slots;
-    TickState walk;                  // closure walk state, reused by every tick
-    WalkJournal journal;
+    TickState walk;                  // the tick being formed: blocks to decode, wanted bytes, blocks read
+    // closure walks of a tick's candidate requests run in parallel on these
+    // threads (plus the worker); each walk sees the cache, not the tick
+    struct WalkOut {
+        std::vector<uint32_t> sched, used;
+        std::vector<Ivs> need;  // wanted bytes of sched[i]
+    };
+    std::vector<std::thread> pool;
+    std::vector<TickState> pool_ts;
+    std::mutex pool_mu;
+    std::condition_variable pool_cv, pool_done_cv;
+    uint64_t pool_gen = 0;
+    int pool_busy = 0;
+    bool pool_stop = false;
+    std::atomic<size_t> pool_next{0};
+    size_t pool_n = 0;
+    const std::vector<Req>* pool_reqs = nullptr;
+    std::vector<WalkOut>* pool_outs = nullptr;
+    void walk_items(int ti);
+    void walk_all(const std::vector<Req>& reqs, std::vector<WalkOut>& outs);
     // requests
     std::mutex mu;
     std::condition_variable cv;
@@ -196,6 +214,42 @@ void aceapex_server::finish_tick(Tick& t, int status) {
     free_events.push_back(t.done);
 }
 
+// One closure walk per request, against the cache only (thread ti's state).
+void aceapex_server::walk_items(int ti) {
+    TickState& ts = pool_ts[ti];
+    WalkJournal j;
+    const Plan& P = A->plan;
+    for (;;) {
+        const size_t i = pool_next.fetch_add(1);
+        if (i >= pool_n) break;
+        const Req& r = (*pool_reqs)[i];
+        WalkOut& o = (*pool_outs)[i];
+        ts.begin(P.n_blocks);
+        span_walk(P, *A->midx, r.start, r.len, &aceapex_server::valid_fn, this, &ts, &j);
+        o.sched.assign(ts.sched.begin(), ts.sched.end());
+        o.used.assign(ts.used.begin(), ts.used.end());
+        o.need.resize(o.sched.size());
+        for (size_t k = 0; k < o.sched.size(); k++) o.need[k].swap(ts.need[o.sched[k]]);
+    }
+}
+
+void aceapex_server::walk_all(const std::vector<Req>& reqs, std::vector<WalkOut>& outs) {
+    outs.resize(reqs.size());
+    pool_reqs = &reqs;
+    pool_outs = &outs;
+    pool_n = reqs.size();
+    pool_next.store(0);
+    {
+        std::lock_guard<std::mutex> g(pool_mu);
+        pool_busy = (int)pool.size();
+        pool_gen++;
+    }
+    pool_cv.notify_all();
+    walk_items(0);
+    std::unique_lock<std::mutex> g(pool_mu);
+    pool_done_cv.wait(g, [this] { return pool_busy == 0; });
+}
+
 // Admit the arrived requests that fit and launch one tick; false if nothing
 // was launched.
 bool aceapex_server::form_tick() {
@@ -203,57 +257,71 @@ bool aceapex_server::form_tick() {
     const int set = (int)(ticks & 1);
     TickBufs& B = bufs[set];
     TickState& T = walk;
-    WalkJournal& J = journal;
-    T.begin(P.n_blocks, A->midx->o.size());
-    std::vector<Req> admitted;
+    T.begin(P.n_blocks);
+    std::vector<Req> admitted, cand;
     std::vector<uint32_t> new_blocks;  // scheduled and not resident: need a slot
     const int64_t tn = now();
-    uint32_t avail = (uint32_t)(free_slots.size() + lru.size());
-    for (;;) {
-        Req r;
-        {
-            std::lock_guard<std::mutex> g(mu);
-            if (queue.empty() || queue.top().at_ns > tn) break;
-            if (admitted.size() >= prm.max_tick_requests) break;
-            r = queue.top();
+    {
+        std::lock_guard<std::mutex> g(mu);
+        while (!queue.empty() && queue.top().at_ns <= tn && cand.size() < prm.max_tick_requests) {
+            cand.push_back(queue.top());
+            queue.pop();
         }
-
-        span_walk(P, *A->midx, r.start, r.len, &aceapex_server::valid_fn, this, &T, &J);
-        uint32_t need_slots = 0;
-        for (size_t i = J.sched0; i < T.sched.size(); i++)
-            if (slot_of[T.sched[i]] == kNoSlot) need_slots++;
+    }
+    if (cand.empty()) return false;
+    std::vector<WalkOut> outs;
+    walk_all(cand, outs);
+    // admission in arrival order: a request joins while the cache can hold its
+    // closure next to those admitted before it
+    uint32_t avail = (uint32_t)(free_slots.size() + lru.size());
+    size_t k = 0;
+    for (; k < cand.size(); k++) {
+        Req& r = cand[k];
+        const WalkOut& o = outs[k];
+        uint32_t need_slots = 0, new_sched = 0;
+        for (uint32_t b : o.sched)
+            if (!T.scheduled(b)) {
+                new_sched++;
+                if (slot_of[b] == kNoSlot) need_slots++;
+            }
         // blocks kept by the cache that this request reads must stay: they are
         // pinned below, so they leave the evictable count
         uint32_t newly_pinned = 0;
-        for (size_t i = J.used0; i < T.used.size(); i++) {
-            const uint32_t b = T.used[i];
-            if (slot_of[b] != kNoSlot && pins[b] == 0 && in_lru[b]) newly_pinned++;
-        }
-        const bool fits = need_slots + newly_pinned <= avail && T.sched.size() <= prm.max_tick_blocks;
+        for (uint32_t b : o.used)
+            if (T.used_mark[b] != T.epoch && slot_of[b] != kNoSlot && pins[b] == 0 && in_lru[b]) newly_pinned++;
+        const bool fits = need_slots + newly_pinned <= avail && T.sched.size() + new_sched <= prm.max_tick_blocks;
         if (!fits) {
-            span_undo(&T, J);
-            const bool never = admitted.empty() && inflight.empty();
-            if (!never) break;  // wait for slots to free up
+            if (!admitted.empty() || !inflight.empty()) break;  // wait for slots to free up
             // nothing else holds the cache: this request can never fit
-            {
-                std::lock_guard<std::mutex> g(mu);
-                queue.pop();
-            }
             complete(r, ACEAPEX_E_BUSY, now());
             continue;
         }
-        {
-            std::lock_guard<std::mutex> g(mu);
-            queue.pop();
-        }
         avail -= need_slots + newly_pinned;
-        for (size_t i = J.used0; i < T.used.size(); i++) pin(T.used[i]);
-        for (size_t i = J.sched0; i < T.sched.size(); i++)
-            if (slot_of[T.sched[i]] == kNoSlot) new_blocks.push_back(T.sched[i]);
+        for (size_t q = 0; q < o.sched.size(); q++) {
+            const uint32_t b = o.sched[q];
+            if (!T.scheduled(b)) {
+                T.sched_mark[b] = T.epoch;
+                T.sched.push_back(b);
+                T.need[b] = o.need[q];
+                if (slot_of[b] == kNoSlot) new_blocks.push_back(b);
+            } else {
+                for (const auto& iv : o.need[q]) iv_union(T.need[b], iv.first, iv.second);
+            }
+        }
+        for (uint32_t b : o.used)
+            if (T.used_mark[b] != T.epoch) {
+                T.used_mark[b] = T.epoch;
+                T.used.push_back(b);
+                pin(b);
+            }
         r.admit_ns = tn;
-        r.closure = (uint32_t)(T.used.size() - J.used0);
-        r.decoded = (uint32_t)(T.sched.size() - J.sched0);
+        r.closure = (uint32_t)o.used.size();
+        r.decoded = (uint32_t)o.sched.size();
         admitted.push_back(r);
+    }
+    if (k < cand.size()) {  // not admitted now: back to the queue (arrival order is kept)
+        std::lock_guard<std::mutex> g(mu);
+        for (; k < cand.size(); k++) queue.push(cand[k]);
     }
     if (admitted.empty()) return false;
     // slots for the new blocks: free ones first, then the least recently used
@@ -457,6 +525,12 @@ static void server_free(aceapex_server* s) {
         s->cv.notify_all();
         s->worker.join();
     }
+    {
+        std::lock_guard<std::mutex> g(s->pool_mu);
+        s->pool_stop = true;
+    }
+    s->pool_cv.notify_all();
+    for (auto& t : s->pool) t.join();
     if (s->c) cudaSetDevice(s->c->device);
     if (s->st) cudaStreamSynchronize(s->st);
     for (auto& ev : s->free_events) cudaEventDestroy(ev);
@@ -533,6 +607,24 @@ int aceapex_server_create(aceapex_ctx* ctx, aceapex_archive* A, const aceapex_se
     s->free_slots.resize(s->n_slots);
     for (uint32_t i = 0; i < s->n_slots; i++) s->free_slots[i] = s->n_slots - 1 - i;
     s->t0 = std::chrono::steady_clock::now();
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int n_walk = (int)std::min(8u, std::max(1u, hw / 2));  // walkers, the worker included
+    s->pool_ts.resize(n_walk);
+    for (int t = 1; t < n_walk; t++)
+        s->pool.emplace_back([s, t] {
+            uint64_t seen = 0;
+            for (;;) {
+                {
+                    std::unique_lock<std::mutex> g(s->pool_mu);
+                    s->pool_cv.wait(g, [s, seen] { return s->pool_stop || s->pool_gen != seen; });
+                    if (s->pool_stop) return;
+                    seen = s->pool_gen;
+                }
+                s->walk_items(t);
+                std::lock_guard<std::mutex> g(s->pool_mu);
+                if (--s->pool_busy == 0) s->pool_done_cv.notify_all();
+            }
+        });
     s->worker = std::thread([s] { s->run(); });
     *out = s;
     return ACEAPEX_OK;

@@ -104,7 +104,7 @@ extern "C" int aceapex_decode_range(aceapex_ctx* c, aceapex_archive* A, uint64_t
         // byte-level closure through the match index: only the wanted bytes' chains
         TickState T;
         WalkJournal Jn;
-        T.begin(P.n_blocks, A->midx->o.size());
+        T.begin(P.n_blocks);
         span_walk(P, *A->midx, start, len, [](void*, uint32_t) -> const Ivs* { return nullptr; }, nullptr, &T, &Jn);
         blocks.assign(T.sched.begin(), T.sched.end());
         std::sort(blocks.begin(), blocks.end());
