@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--lanes", type=int, default=32)
     p.add_argument("--wait-ns", type=int, default=0,
                    help="decoder: first cross-block round's wait per piece (0: library default)")
+    p.add_argument("--shard", action="store_true",
+                   help="N GPUs split the output blocks (each decodes its range's closure) instead of replicas")
     p.add_argument("--max-depth", type=int, default=0,
                    help="encoder chain-depth cap (0: the library default of 16)")
     p.add_argument("--e2e-steps", type=int, default=5)
@@ -608,16 +610,32 @@ def main():
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
+    world = dist["world"]
+    # --shard: this rank decodes its block-aligned range through the range's
+    # byte-level closure (strong scaling); otherwise every rank decodes its
+    # own replica of the whole archive (weak scaling)
+    if args.shard:
+        A.build_index()
+        s0, ln = acx.shard_range(size, world, dist["rank"])
+
+        def one(stats=False):
+            return acx.decode_range(ctx, A, s0, ln, out.data_ptr() + s0, sh, stats=stats)
+    else:
+        s0, ln = 0, size
+
+        def one(stats=False):
+            return acx.decode_all(ctx, A, out.data_ptr(), size, sh, stats=stats)
+
     # correctness gate: the timed configuration must reproduce the input exactly
-    rc = acx.decode_all(ctx, A, out.data_ptr(), size, sh)
+    rc = one()
     if rc != 0:
         raise RuntimeError(f"decode failed: {rc} {ctx.last_error()}")
-    if not torch.equal(out, torch.from_numpy(data).to(out.device)):
+    if not torch.equal(out[s0:s0 + ln], torch.from_numpy(data[s0:s0 + ln]).to(out.device)):
         raise RuntimeError("GPU decode differs from the input")
 
     for _ in range(args.warmup):
         flush.fill_(1)
-        acx.decode_all(ctx, A, out.data_ptr(), size, sh)
+        one()
     torch.cuda.synchronize()
     if dist["pg"]:
         dist["pg"].barrier()
@@ -629,7 +647,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1)  # write 256 MiB > L2 between steps
-        r, st = acx.decode_all(ctx, A, out.data_ptr(), size, sh, stats=True)
+        r, st = one(stats=True)
         if r != 0:
             raise RuntimeError(f"decode failed: {r} {ctx.last_error()}")
         ms_total.append(st["ms_total"])
@@ -649,8 +667,7 @@ def main():
         t = torch.tensor([dev_ms], device=out.device, dtype=torch.float64)
         dist["pg"].all_reduce(t, op=dist["pg"].ReduceOp.MAX)
         dev_ms = float(t.item())
-    world = dist["world"]
-    value = world * size * args.steps / (dev_ms / 1e3) / 1e9
+    value = (1 if args.shard else world) * size * args.steps / (dev_ms / 1e3) / 1e9
     ms_step = dev_ms / args.steps
 
     # roofline of the dominant kernel and of the whole path
@@ -658,7 +675,9 @@ def main():
     s_ms = statistics.mean(ms_asm)
     x_ms = statistics.mean(ms_ext)
     roof, path_roof = rooflines({"ans": a_ms, "local": s_ms, "cross": x_ms}, stream_bytes(arc), size, len(arc),
-                                last_stats, info["n_blocks"], args.variant, ms_step)
+                                last_stats, info["n_blocks"], args.variant, ms_step,
+                                wname if args.encoding == "history" and args.variant == "fast"
+                                and not args.max_depth and args.lanes == 32 else "")
 
     # end to end through the C ABI from pinned host memory
     e2e = None
@@ -677,7 +696,7 @@ def main():
         if not np.array_equal(hout_np, data):
             raise RuntimeError("decode_host output differs from the input")
         e_mean = statistics.mean(e_ms)
-        e2e = {"value": round(world * size / (e_mean / 1e3) / 1e9, 3), "unit": "GB/s",
+        e2e = {"value": round((1 if args.shard else world) * size / (e_mean / 1e3) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": len(arc), "d2h_bytes_per_step": size}
 
     cpu = None
@@ -688,8 +707,8 @@ def main():
         line = {
             "metric": "device-resident decode GB/s", "value": round(value, 3), "unit": "GB/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic (seeded generator; stands in for chr1 hg38)",
+            "higher_is_better": True, "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic (seeded generator; stands in for chr1 hg38)",
             "config": {"workload": wname, "encoding": args.encoding, "variant": args.variant,
                        "max_depth": args.max_depth or 16,
                        "rans_lanes": args.lanes, "block_size": 16384, "blocks": info["n_blocks"],
@@ -716,13 +735,18 @@ def main():
         dist["pg"].destroy_process_group()
 
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel, keyed by (workload, kernel); None until a capture of the current
-# kernel exists
-TRAFFIC = {}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, keyed by
+# (workload, kernel): the --set full capture of profiles/ncu_full_decode_dna_64MiB.md
+# (4,096 blocks) scaled to the genome's 15,499 blocks; absent (null) for
+# workloads and kernels without a capture of the current code
+TRAFFIC = {
+    ("chr1-shaped synthetic genome 253,935,557 B", "k_rans"): 93_870_000,
+    ("chr1-shaped synthetic genome 253,935,557 B", "k_local"): 340_100_000,
+    ("chr1-shaped synthetic genome 253,935,557 B", "k_external"): 140_850_000,
+}
 
 
-def rooflines(stage, pb, size, arc_len, st, n_blocks, variant, ms_step):
+def rooflines(stage, pb, size, arc_len, st, n_blocks, variant, ms_step, wname=""):
     """HBM roofline of each decode kernel from its algorithmic bytes per launch
     over its CUDA-event time, the dominant (slowest) kernel first, and of the
     whole path (archive bytes read + output bytes written over the step)."""
@@ -741,12 +765,13 @@ def rooflines(stage, pb, size, arc_len, st, n_blocks, variant, ms_step):
     }
     per = {k: {"ms": round(ms, 4), "algorithmic_bytes": int(b),
                "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1) if ms > 0 else None,
-               "frac": round(b / (ms / 1e3) / 1e9 / peak, 4) if ms > 0 else None} for k, (ms, b) in kern.items()}
+               "frac": round(b / (ms / 1e3) / 1e9 / peak, 4) if ms > 0 else None,
+               "traffic": TRAFFIC.get((wname, k))} for k, (ms, b) in kern.items()}
     dom = max(kern, key=lambda k: kern[k][0])
     ms, b = kern[dom]
     achieved = b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(dom), "peak_kind": peak_kind + " hbm_gbs",
+            "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get((wname, dom)), "peak_kind": peak_kind + " hbm_gbs",
             "algorithmic_bytes": int(b), "kernels": per}
     path_bytes = arc_len + size
     path_gbs = path_bytes / (ms_step / 1e3) / 1e9

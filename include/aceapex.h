@@ -209,6 +209,17 @@ int aceapex_decode_range(aceapex_ctx* ctx, aceapex_archive* arc, uint64_t start,
                          void* stream, aceapex_stats* stats);
 
 /*
+ * Sharded decode over several GPUs (one process per GPU): the output blocks
+ * are split into n_ranks contiguous ranges of nearly equal block counts, and
+ * rank `rank` gets [*start, *start + *len).  Each rank decodes its range with
+ * aceapex_decode_range — its byte-level closure, so the sources it needs from
+ * other ranks' ranges are decoded redundantly and no collective is on the
+ * path; an all-gather of the ranges (if the caller wants the whole output on
+ * every GPU) comes after.  Pure arithmetic, no device work.
+ */
+int aceapex_shard_range(uint64_t total, int n_ranks, int rank, uint64_t* start, uint64_t* len);
+
+/*
  * Serving: a request loop over one archive held compressed in device memory
  * with a bounded cache of decoded blocks (paper, Random Access at Scale; the
  * paper's persistent seek queue).  A worker thread admits the requests that

@@ -7,4 +7,4 @@ only used by callers for device memory and streams.
 """
 from . import build, lib, tune  # noqa: F401
 from .lib import (Archive, Batch, Context, Server, autotune, AceapexError, archive_check, batch_decode, decode_all,  # noqa: F401
-                  decode_all_async, decode_host, decode_range, encode, load)
+                  decode_all_async, decode_host, decode_range, encode, load, shard_range)

@@ -162,6 +162,16 @@ int aceapex_archive_check(const void* h_arc, uint64_t len, aceapex_archive_info*
     return ACEAPEX_OK;
 }
 
+int aceapex_shard_range(uint64_t total, int n_ranks, int rank, uint64_t* start, uint64_t* len) {
+    if (n_ranks <= 0 || rank < 0 || rank >= n_ranks || !start || !len) return ACEAPEX_E_ARG;
+    const uint64_t nb = (total + kBlock - 1) / kBlock;
+    const uint64_t b0 = nb * (uint64_t)rank / (uint64_t)n_ranks, b1 = nb * (uint64_t)(rank + 1) / (uint64_t)n_ranks;
+    const uint64_t s = std::min(total, b0 * kBlock), e = std::min(total, b1 * kBlock);
+    *start = s;
+    *len = e - s;
+    return ACEAPEX_OK;
+}
+
 // Diagnostics (not part of the documented ABI): copy the context's device
 // counter block (tickets, statistics, cross-block round trace) to host memory.
 int acx_debug_counters(aceapex_ctx* c, uint32_t* out, uint32_t n) {

@@ -428,7 +428,10 @@ __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
                 for (uint32_t i = tid; i < n; i += kLocThreads)
                     J.spans[ir.span_base + i] = SpanRec{(uint32_t)tsrc[i], (uint32_t)(tsrc[i] >> 32),
                                                         (uint32_t)(tpos[i] + tll[i]) | ((uint32_t)tml[i] << 16), tcmd[i]};
-            if (bad && tid == 0) set_err_arc(job, a, kErrCorrupt, stage << 24, b);
+            if (bad && tid == 0) {
+                set_err_arc(job, a, kErrCorrupt, stage << 24, b);
+                J.npend[ir.slot] = 1;  // per-item status of a parse-only job
+            }
             __syncthreads();
             continue;
         }

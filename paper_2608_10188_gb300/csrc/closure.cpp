@@ -77,7 +77,9 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
         delete M;
         return cuda_fail(c, e, "match index: stream");
     }
-    DevBuf items, recs, scratch;
+    DevBuf items, recs, scratch, status;
+    M->bad.assign(P.n_blocks, 0);
+    std::vector<uint32_t> st_h;
     std::vector<SpanRec> h;
     std::vector<ItemDev> it;
     int rc = ACEAPEX_OK;
@@ -90,7 +92,7 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
         for (uint32_t i = 0; i < k; i++) {
             const BlockDev& bd = P.blk[c0 + i];
             it[i].block = c0 + i;
-            it[i].slot = kNoSlot;
+            it[i].slot = i;  // index of the item's status word
             it[i].span_base = (uint32_t)toks;  // token records, packed
             it[i].scratch = sb;
             toks += bd.n_tok;
@@ -101,7 +103,8 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
         sb += 64;
         if ((e = items.ensure(k * sizeof(ItemDev))) != cudaSuccess ||
             (e = recs.ensure(std::max<uint64_t>(toks, 1) * sizeof(SpanRec))) != cudaSuccess ||
-            (e = scratch.ensure(sb)) != cudaSuccess ||
+            (e = scratch.ensure(sb)) != cudaSuccess || (e = status.ensure(k * sizeof(uint32_t))) != cudaSuccess ||
+            (e = cudaMemsetAsync(status.p, 0, k * sizeof(uint32_t), st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(items.p, it.data(), k * sizeof(ItemDev), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
             rc = cuda_fail(c, e, "match index: scratch");
             break;
@@ -120,6 +123,7 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
         J.min_match = P.min_match;
         J.deps = A->d_deps;
         J.items = (const ItemDev*)items.p;
+        J.npend = (uint32_t*)status.p;
         job.n_arcs = 1;
         job.n_items = k;
         job.counters = c->counters;
@@ -131,7 +135,14 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
         LaunchPlan lp;
         if ((rc = launch_plan(c, c->params, max_tok, max_lenb, &lp, kJobIndex))) break;
         if ((rc = enqueue_job(c, job, lp, 4, nullptr, 0, st, nullptr))) break;
-        if ((rc = ctx_read_status(c, st))) break;
+        // a corrupt block is recorded in its status word and the index goes on
+        if ((rc = ctx_read_status(c, st)) && rc != ACEAPEX_E_CORRUPT) break;
+        rc = ACEAPEX_OK;
+        st_h.resize(k);
+        if ((e = cudaMemcpy(st_h.data(), status.p, k * sizeof(uint32_t), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            rc = cuda_fail(c, e, "match index: status");
+            break;
+        }
         h.resize(toks);
         if (toks && (e = cudaMemcpy(h.data(), recs.p, toks * sizeof(SpanRec), cudaMemcpyDeviceToHost)) != cudaSuccess) {
             rc = cuda_fail(c, e, "match index: records");
@@ -141,6 +152,11 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
         for (uint32_t i = 0; i < k; i++) {
             const uint32_t b = c0 + i, n = P.blk[b].n_tok;
             M->first[b] = M->o.size();
+            if (st_h[i]) {
+                M->bad[b] = 1;
+                t += n;
+                continue;
+            }
             for (uint32_t q = 0; q < n; q++, t++) {
                 const SpanRec& r = h[t];
                 const uint32_t ml = r.z >> 16;
@@ -156,6 +172,7 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
     items.release();
     recs.release();
     scratch.release();
+    status.release();
     if (rc) {
         delete M;
         return rc;
@@ -191,6 +208,7 @@ void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t
     }
     const uint32_t rq = T->req;
     J->saved.clear();
+    J->bad = false;
     J->sched0 = T->sched.size();
     J->used0 = T->used.size();
     auto& stack = T->stack;
@@ -208,6 +226,10 @@ void acx::span_walk(const Plan& P, const MatchIndex& M, uint64_t start, uint64_t
         stack.pop_back();
         if (r.s >= r.e) continue;
         const uint32_t X = r.b;
+        if (!M.bad.empty() && M.bad[X]) {  // no matches are known there: the region cannot be decoded
+            J->bad = true;
+            continue;
+        }
         if (T->used_mark[X] != ep) {
             T->used_mark[X] = ep;
             T->used.push_back(X);
@@ -316,4 +338,20 @@ extern "C" int acx_debug_closure(const uint8_t* h_arc, uint64_t arc_len, const u
     }
     *n_blocks = (uint32_t)bl.size();
     return 0;
+}
+
+// Diagnostics (not part of the documented ABI): copy an archive's match index
+// to host arrays (first[n_blocks + 1], o/ml/src[cap], bad[n_blocks]); returns
+// the number of matches, or -1 (no index, or cap too small).
+extern "C" int64_t acx_debug_match_index(const aceapex_archive* A, uint64_t* first, uint16_t* o, uint16_t* ml,
+                                         uint64_t* src, uint8_t* bad, uint64_t cap) {
+    if (!A || !A->midx) return -1;
+    const MatchIndex& M = *A->midx;
+    if (M.o.size() > cap) return -1;
+    std::copy(M.first.begin(), M.first.end(), first);
+    std::copy(M.o.begin(), M.o.end(), o);
+    std::copy(M.ml.begin(), M.ml.end(), ml);
+    std::copy(M.src.begin(), M.src.end(), src);
+    std::copy(M.bad.begin(), M.bad.end(), bad);
+    return (int64_t)M.o.size();
 }

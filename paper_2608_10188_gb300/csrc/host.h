@@ -55,6 +55,7 @@ struct MatchIndex {
     std::vector<uint64_t> first;
     std::vector<uint16_t> o, ml;
     std::vector<uint64_t> src;
+    std::vector<uint8_t> bad;  // per block: 1 if the parse found it corrupt (it then lists no matches)
 };
 
 }  // namespace acx
@@ -157,6 +158,7 @@ struct TickState {
 struct WalkJournal {
     std::vector<std::pair<uint32_t, Ivs>> saved;  // need of a block scheduled by an earlier request, before this one
     size_t sched0 = 0, used0 = 0;                 // list lengths before the request
+    bool bad = false;                             // the region depends on a block the parse found corrupt
 };
 typedef const Ivs* (*ValidFn)(void* self, uint32_t block);
 // Walk one request's region; returns nothing, the tick state grows.  The

@@ -112,7 +112,8 @@ constexpr uint32_t kCounterWords = 4096;
 // Job flags.  kJobIndex: parse only — the entropy stage skips the literal
 // stream and the local pass writes one token record per token (SpanRec: x/y
 // source, z = destination offset | match length << 16, w = command) at the
-// item's span_base instead of decoding the block.
+// item's span_base instead of decoding the block; a corrupt block sets
+// npend[item's slot] to 1 (the caller zeroes it first).
 constexpr uint32_t kJobIndex = 1;
 // kJobNeed: some items want only some of their bytes (ItemDev::need_n): the
 // local pass leaves the matches outside them undone (their bytes are then

@@ -250,7 +250,12 @@ __device__ int rans_short3(const uint32_t* __restrict__ tab, const BlockDev& bd,
     ok = __all_sync(ACX_FULL, ok);
     const uint32_t lt_mask = (1u << lane) - 1;
     uint32_t p = 0;
-    for (uint32_t t = 0; t < steps && ok; t++) {
+    // The word pointer p is per stream group, so an overrun (a corrupt
+    // stream) is noticed by one group first: the loop ends only on the
+    // warp-uniform flag, refreshed every 8 steps, and ring reads stay inside
+    // this warp's ring until then.
+    bool okw = ok;
+    for (uint32_t t = 0; t < steps && okw; t++) {
         const uint32_t i = t * Kg + j;
         bool need = false;
         if (my >= 0 && i < n) {
@@ -261,11 +266,12 @@ __device__ int rans_short3(const uint32_t* __restrict__ tab, const BlockDev& bd,
             need = x < kL;
         }
         const uint32_t b = __ballot_sync(ACX_FULL, need) & gmask;
-        if (need) x = (x << 16) | ring[ro + p + __popc(b & lt_mask)];
+        if (need) x = (x << 16) | ring[(ro + p + __popc(b & lt_mask)) & (kRingWords - 1)];
         p += __popc(b);
         if (p > Wg) ok = false;
-        if ((t & 7) == 7) ok = __all_sync(ACX_FULL, ok);
+        if ((t & 7) == 7) okw = __all_sync(ACX_FULL, ok);
     }
+    ok = __all_sync(ACX_FULL, ok);
     const bool fin = my < 0 || (p == Wg && x == kL);
     __syncwarp();  // the ring is free again for the next stream's copies
     return __all_sync(ACX_FULL, ok && fin) ? 0 : -1;
@@ -369,7 +375,10 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
                     copy_stored(body, o, n, lane);
                 }
             }
-            if (!ok && lane == 0) set_err_arc(job, a, kErrCorrupt, (kStageRans << 24) | fs, b);
+            if (!ok && lane == 0) {
+                set_err_arc(job, a, kErrCorrupt, (kStageRans << 24) | fs, b);
+                if (job.flags & kJobIndex) J.npend[ir.slot] = 1;  // per-item status of a parse-only job
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -110,6 +110,7 @@ struct aceapex_server {
     struct WalkOut {
         std::vector<uint32_t> sched, used;
         std::vector<Ivs> need;  // wanted bytes of sched[i]
+        bool bad = false;       // depends on a block the parse found corrupt
     };
     std::vector<std::thread> pool;
     std::vector<TickState> pool_ts;
@@ -226,6 +227,7 @@ void aceapex_server::walk_items(int ti) {
         WalkOut& o = (*pool_outs)[i];
         ts.begin(P.n_blocks);
         span_walk(P, *A->midx, r.start, r.len, &aceapex_server::valid_fn, this, &ts, &j);
+        o.bad = j.bad;
         o.sched.assign(ts.sched.begin(), ts.sched.end());
         o.used.assign(ts.used.begin(), ts.used.end());
         o.need.resize(o.sched.size());
@@ -278,6 +280,10 @@ bool aceapex_server::form_tick() {
     for (; k < cand.size(); k++) {
         Req& r = cand[k];
         const WalkOut& o = outs[k];
+        if (o.bad) {  // a corrupt block: this request fails alone
+            complete(r, ACEAPEX_E_CORRUPT, now());
+            continue;
+        }
         uint32_t need_slots = 0, new_sched = 0;
         for (uint32_t b : o.sched)
             if (!T.scheduled(b)) {

@@ -106,6 +106,7 @@ extern "C" int aceapex_decode_range(aceapex_ctx* c, aceapex_archive* A, uint64_t
         WalkJournal Jn;
         T.begin(P.n_blocks);
         span_walk(P, *A->midx, start, len, [](void*, uint32_t) -> const Ivs* { return nullptr; }, nullptr, &T, &Jn);
+        if (Jn.bad) return fail(c, ACEAPEX_E_CORRUPT, "decode_range: the region depends on a corrupt block");
         blocks.assign(T.sched.begin(), T.sched.end());
         std::sort(blocks.begin(), blocks.end());
         std::vector<uint32_t> iv;

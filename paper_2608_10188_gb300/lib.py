@@ -26,7 +26,7 @@ EXPORTED = [
     "aceapex_batch_decode", "aceapex_decode_range", "aceapex_archive_index", "aceapex_server_create",
     "aceapex_server_now_ns", "aceapex_server_submit_many", "aceapex_server_submit", "aceapex_server_poll",
     "aceapex_server_drain", "aceapex_server_get_stats", "aceapex_server_last_error", "aceapex_server_destroy",
-    "aceapex_autotune",
+    "aceapex_autotune", "aceapex_shard_range",
 ]
 BATCH_GRAPH = 1
 
@@ -140,6 +140,7 @@ def load(path: str | None = None):
     L.aceapex_server_last_error.argtypes = [vp]
     L.aceapex_server_last_error.restype = c.c_char_p
     L.aceapex_server_destroy.argtypes = [vp]
+    L.aceapex_shard_range.argtypes = [u64, c.c_int, c.c_int, c.POINTER(u64), c.POINTER(u64)]
     L.aceapex_autotune.argtypes = [vp, c.POINTER(BatchItem), c.c_int, c.c_int, c.POINTER(TunePoint), c.c_int,
                                    c.POINTER(c.c_int), c.POINTER(DecParams)]
     L.aceapex_batch_decode.argtypes = [vp, c.POINTER(BatchItem), c.c_int, vp, c.POINTER(Stats)]
@@ -457,3 +458,12 @@ def autotune(ctx: Context, entries, reps: int = 3, max_points: int = 512):
     ctx.params = best
     b = {k: getattr(best, k) for k, _ in DecParams._fields_}
     return b, [{k: getattr(pts[i], k) for k, _ in TunePoint._fields_} for i in range(npts.value)]
+
+
+def shard_range(total: int, n_ranks: int, rank: int):
+    """aceapex_shard_range: (start, length) of this rank's block-aligned output range."""
+    s, n = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = load().aceapex_shard_range(total, n_ranks, rank, ctypes.byref(s), ctypes.byref(n))
+    if rc != OK:
+        raise AceapexError(rc, "shard_range")
+    return s.value, n.value
