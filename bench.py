@@ -741,7 +741,6 @@ def main():
 # workloads and kernels without a capture of the current code
 TRAFFIC = {
     ("chr1-shaped synthetic genome 253,935,557 B", "k_rans"): 93_870_000,
-    ("chr1-shaped synthetic genome 253,935,557 B", "k_local"): 340_100_000,
     ("chr1-shaped synthetic genome 253,935,557 B", "k_external"): 140_850_000,
 }
 

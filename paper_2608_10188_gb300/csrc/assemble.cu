@@ -68,6 +68,10 @@ __host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB, bool ne
     return L;
 }
 
+// Literal runs up to this many bytes are copied by one thread (a byte at a
+// time, every thread of the CTA on its own run); longer ones by a warp.
+constexpr uint32_t kLaneBytes = 32;
+
 // Does the match at [o, o + ml) of a block touch a wanted byte?
 __device__ __forceinline__ bool wanted(const uint32_t* need, uint32_t o, uint32_t ml) {
     for (uint32_t w = o >> 5; w <= ((o + ml - 1) >> 5); w++)
@@ -184,6 +188,25 @@ __device__ __forceinline__ void copy_run(uint8_t* __restrict__ sout, const uint8
     }
 }
 
+// Issue the 1-D TMA copies of an item's four decoded streams (16-aligned,
+// padded) into the stream buffers (one thread).  Nothing is issued for a
+// block beyond the job's shared-memory limits (the caller treats it as bad).
+__device__ void stage_streams(const JobDev& job, uint32_t item, uint8_t* tcmd, uint8_t* lenb, uint8_t* soff,
+                              uint8_t* slit, uint64_t* bar) {
+    const ArcJob J = load_arc(job, find_arc(job, item));
+    const ItemRef ir = item_ref(J, item - J.item_base);
+    const BlockDev& bd = J.blk[ir.blk];
+    const uint32_t n = bd.n_tok, LB = bd.s_raw[kLen], n_new = bd.n_new, n_lit = bd.s_raw[kLit];
+    if (n > job.max_tok || LB > job.max_lenb || n_new > job.max_tok) return;
+    const uint8_t* scr = J.scratch + ir.scratch;
+    const uint32_t sz[4] = {(n + 15) & ~15u, (LB + 15) & ~15u, (5 * n_new + 15) & ~15u, (n_lit + 15) & ~15u};
+    uint8_t* dsts[4] = {tcmd, lenb, soff, slit};
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic use of the buffers
+    mbar_arrive_tx(bar, sz[0] + sz[1] + sz[2] + sz[3]);
+    for (int q = 0; q < 4; q++)
+        if (sz[q]) tma_load_1d(dsts[q], scr + bd.s_off[q], sz[q], bar);
+}
+
 __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
     extern __shared__ __align__(128) uint8_t sm[];
     const LocLayout L = loc_layout(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0);
@@ -211,16 +234,24 @@ __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
     uint32_t phase = 0;
     const uint32_t chunk = job.chunk ? job.chunk : 1u;
     uint32_t cnext = 0, cleft = 0;  // the CTA's current run of `chunk` tickets
+    uint32_t pf_item = 0xffffffffu;  // item whose streams are already in flight (CTA-uniform)
 
     for (;;) {
-        if (cleft == 0) {
-            if (tid == 0) misc[0] = atomicAdd(&job.counters[1], chunk);
-            __syncthreads();
-            cnext = misc[0];
-            cleft = chunk;
+        const bool prefetched = pf_item != 0xffffffffu;
+        uint32_t item;
+        if (prefetched) {
+            item = pf_item;
+            pf_item = 0xffffffffu;
+        } else {
+            if (cleft == 0) {
+                if (tid == 0) misc[0] = atomicAdd(&job.counters[1], chunk);
+                __syncthreads();
+                cnext = misc[0];
+                cleft = chunk;
+            }
+            item = cnext++;
+            cleft--;
         }
-        const uint32_t item = cnext++;
-        cleft--;
         if (item >= job.n_items) return;
         const int a = find_arc(job, item);
         const ArcJob J = load_arc(job, a);
@@ -237,15 +268,10 @@ __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
             if (cond && !bad) { bad = true; stage = st; }
         };
 
-        // ---- stage the four decoded streams with 1-D TMA bulk copies (16-aligned, padded) ----
-        if (!bad && tid == 0) {
-            const uint32_t sz[4] = {(n + 15) & ~15u, (LB + 15) & ~15u, (5 * n_new + 15) & ~15u, (n_lit + 15) & ~15u};
-            uint8_t* dsts[4] = {tcmd, lenb, soff, slit};
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic use of the buffers
-            mbar_arrive_tx(bar, sz[0] + sz[1] + sz[2] + sz[3]);
-            for (int q = 0; q < 4; q++)
-                if (sz[q]) tma_load_1d(dsts[q], scr + bd.s_off[q], sz[q], bar);
-        }
+        // ---- stage the four decoded streams with 1-D TMA bulk copies (unless
+        //      they were prefetched during the previous block) ----
+        (void)scr;
+        if (!bad && tid == 0 && !prefetched) stage_streams(job, item, tcmd, lenb, soff, slit, bar);
         for (uint32_t i = tid; i < kBlock / 32; i += kLocThreads) pend[i] = 0;
         if (tid == 0) misc[1] = 0;
         // wanted bytes of this item (all when it names none)
@@ -438,8 +464,17 @@ __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
 
         uint32_t npend = 0, pbytes = 0;
         if (!bad) {
-            // ---- literal placement: one warp per run ----
-            for (uint32_t i = warp; i < n; i += kLocWarps) copy_run(sout, slit, tlit[i], tpos[i], tll[i], lane);
+            // ---- literal placement: a thread copies a tiny run (<= kLaneBytes)
+            //      by itself, all threads at once; a warp copies each longer one ----
+            for (uint32_t i = tid; i < n; i += kLocThreads) {
+                const uint32_t ll = tll[i];
+                if (ll <= kLaneBytes) {
+                    const uint32_t la = tlit[i], lb = tpos[i];
+                    for (uint32_t k = 0; k < ll; k++) sout[lb + k] = slit[la + k];
+                }
+            }
+            for (uint32_t i = warp; i < n; i += kLocWarps)
+                if (tll[i] > kLaneBytes) copy_run(sout, slit, tlit[i], tpos[i], tll[i], lane);
             // ---- every match byte starts unresolved; external sources are pending for good ----
             for (uint32_t i = tid; i < n; i += kLocThreads) {
                 const uint32_t ml = tml[i];
@@ -452,39 +487,63 @@ __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
                 tstat[i] = st;
             }
             __syncthreads();
-            // ---- in-block matches: rounds of ready periodic fills, one warp per match ----
+            // ---- the stream buffers are free from here on: start the next item's
+            //      copies, so that they land while this block finishes ----
+            if (cleft == 0) {
+                if (tid == 0) misc[0] = atomicAdd(&job.counters[1], chunk);
+                __syncthreads();
+                cnext = misc[0];
+                cleft = chunk;
+            }
+            pf_item = cnext++;
+            cleft--;
+            if (tid == 0 && pf_item < job.n_items) stage_streams(job, pf_item, tcmd, lenb, soff, slit, bar);
+            // ---- in-block matches: rounds of ready periodic fills; each warp
+            //      works on four matches at once, eight lanes per match ----
             for (;;) {
                 bool progress = false, left = false;
-                for (uint32_t i = warp; i < n; i += kLocWarps) {
-                    if (tstat[i] != 1) continue;
-                    const uint32_t ml = tml[i];
-                    const uint32_t o = tpos[i] + tll[i];
-                    const uint32_t so = (uint32_t)(tsrc[i] - B);
-                    const uint32_t d = o - so;
-                    const uint32_t we = so + min(d, ml);  // periodic source window [so, we)
+                const uint32_t g = lane >> 3, sl = lane & 7;
+                const uint32_t gmask = 0xffu << (8 * g);
+                for (uint32_t base = warp * 4; base < n; base += kLocWarps * 4) {
+                    const uint32_t i = base + g;
+                    const bool act = i < n && tstat[i] == 1;  // the same for the group's lanes
+                    uint32_t ml = 0, o = 0, so = 0, d = 1, we = 0;
                     bool busy = false;
-                    for (uint32_t w = (so >> 5) + lane; w <= ((we - 1) >> 5); w += 32)
-                        busy |= (((volatile uint32_t*)pend)[w] & range_mask(w, so, we)) != 0;
-                    if (__any_sync(ACX_FULL, busy)) { left = true; continue; }
+                    if (act) {
+                        ml = tml[i];
+                        o = tpos[i] + tll[i];
+                        so = (uint32_t)(tsrc[i] - B);
+                        d = o - so;
+                        we = so + min(d, ml);  // periodic source window [so, we)
+                        for (uint32_t w = (so >> 5) + sl; w <= ((we - 1) >> 5); w += 8)
+                            busy |= (((volatile uint32_t*)pend)[w] & range_mask(w, so, we)) != 0;
+                    }
+                    const uint32_t bm = __ballot_sync(ACX_FULL, busy);  // every lane, active or not
+                    const bool ready = act && (bm & gmask) == 0;
+                    if (act && !ready) left = true;
                     __threadfence_block();  // source reads after the readiness reads
-                    if (d >= ml) {
-                        for (uint32_t k = lane; k < ml; k += 32) sout[o + k] = sout[so + k];
-                    } else {
-                        // out[o+k] = out[so + (k mod d)]: the source window only, so lanes are independent
-                        uint32_t r = lane % d;
-                        const uint32_t step = 32 % d;
-                        for (uint32_t k = lane; k < ml; k += 32) {
-                            sout[o + k] = sout[so + r];
-                            r += step;
-                            if (r >= d) r -= d;
+                    if (ready) {
+                        if (d >= ml) {
+                            for (uint32_t k = sl; k < ml; k += 8) sout[o + k] = sout[so + k];
+                        } else {
+                            // out[o+k] = out[so + (k mod d)]: the source window only, so lanes are independent
+                            uint32_t r = sl % d;
+                            const uint32_t step = 8 % d;
+                            for (uint32_t k = sl; k < ml; k += 8) {
+                                sout[o + k] = sout[so + r];
+                                r += step;
+                                if (r >= d) r -= d;
+                            }
                         }
                     }
                     __syncwarp();
                     __threadfence_block();
-                    for (uint32_t w = (o >> 5) + lane; w <= ((o + ml - 1) >> 5); w += 32)
-                        atomicAnd(&pend[w], ~range_mask(w, o, o + ml));
-                    if (lane == 0) tstat[i] = 0;
-                    progress = true;
+                    if (ready) {
+                        for (uint32_t w = (o >> 5) + sl; w <= ((o + ml - 1) >> 5); w += 8)
+                            atomicAnd(&pend[w], ~range_mask(w, o, o + ml));
+                        if (sl == 0) tstat[i] = 0;
+                        progress = true;
+                    }
                 }
                 const int any_left = __syncthreads_or(left);
                 const int any_prog = __syncthreads_or(progress);
