@@ -699,6 +699,18 @@ def main():
         e2e = {"value": round((1 if args.shard else world) * size / (e_mean / 1e3) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": len(arc), "d2h_bytes_per_step": size}
 
+    # parse statistics of the archive from the device's parse-only pass
+    # (after the timed region): the repeat-coded share and the
+    # dependency-free runs between repeat-coded tokens
+    ps = A.parse_stats()
+    n_rep = sum(ps["rep_matches"])
+    parse = {"tokens": ps["tokens"], "repeat_coded": n_rep,
+             "repeat_coded_share": round(n_rep / max(ps["tokens"], 1), 5),
+             "multibyte_value_share": round(ps["multibyte_values"] / max(ps["values"], 1), 5),
+             "runs": ps["runs"], "median_run": ps["median_run"],
+             "mean_run": round(ps["run_len_sum"] / max(ps["runs"], 1), 2), "max_run": ps["max_run"],
+             "external_matches": ps["external_matches"], "overlap_matches": ps["overlap_matches"]}
+
     cpu = None
     if dist["rank"] == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_baseline(arc, data)
@@ -715,10 +727,14 @@ def main():
                        "tokens": info["tokens"], "archive_bytes": len(arc),
                        "ratio": round(size / len(arc), 4),
                        "l2": "256 MiB buffer written between steps; per-step CUDA events exclude it"},
+            "step_ms": {"median": round(statistics.median(ms_total), 4), "min": round(min(ms_total), 4),
+                        "max": round(max(ms_total), 4),
+                        "spread": round((max(ms_total) - min(ms_total)) / statistics.median(ms_total), 4)},
             "stage_ms": {"ans": round(a_ms, 4), "local_parse_copy": round(s_ms, 4), "cross_block": round(x_ms, 4)},
             "cross_block_stats": {"pending_pieces": last_stats.get("pending_spans"),
                                   "pending_bytes": last_stats.get("pending_bytes"),
                                   "rounds_after_first": last_stats.get("wait_polls")},
+            "parse_stats": parse,
             "roofline": roof,
             "path_roofline": path_roof,
             "e2e": e2e,
@@ -740,8 +756,9 @@ def main():
 # (4,096 blocks) scaled to the genome's 15,499 blocks; absent (null) for
 # workloads and kernels without a capture of the current code
 TRAFFIC = {
-    ("chr1-shaped synthetic genome 253,935,557 B", "k_rans"): 93_870_000,
-    ("chr1-shaped synthetic genome 253,935,557 B", "k_external"): 140_850_000,
+    ("chr1-shaped synthetic genome 253,935,557 B", "k_rans"): 100_760_000,
+    ("chr1-shaped synthetic genome 253,935,557 B", "k_local"): 333_290_000,
+    ("chr1-shaped synthetic genome 253,935,557 B", "k_external"): 140_710_000,
 }
 
 
