@@ -192,6 +192,35 @@ int aceapex_sync(aceapex_ctx* ctx, void* stream);
 int aceapex_archive_index(aceapex_ctx* ctx, aceapex_archive* arc);
 
 /*
+ * Parse statistics of an archive, counted from the device's parse-only pass
+ * (the same pass that builds the match index; it is run if the archive has
+ * no index yet).  Paper, "The Last Sequential Element": the commands that
+ * read the four-entry history (repeat codes) are the parse's only sequential
+ * element; the runs between them are what a scan parse can take at once.
+ *  - runs: each block's tokens are cut at every repeat-coded token; a run is
+ *    the count of non-repeat tokens before a repeat-coded token, back to the
+ *    previous one or the block start, plus one trailing run per block (the
+ *    history resets per block, so a block boundary ends a run).  Runs of
+ *    length 0 count.  median_run is the element of rank floor(runs / 2) of
+ *    the sorted run lengths.
+ *  - multibyte_values: length values of 128 or more (two or more LEB128
+ *    bytes in a canonical encoding).
+ *  - overlap_matches: matches with distance < length (periodic fills);
+ *    external_matches: matches whose source starts before their block.
+ * Blocks the parse finds corrupt are left out and counted in bad_blocks.
+ * Synchronous; stats must not be NULL.
+ */
+typedef struct {
+    uint64_t blocks, tokens, new_matches, rep_matches[4], lit_only;
+    uint64_t values, multibyte_values;
+    uint64_t literal_bytes, match_bytes, overlap_matches, external_matches;
+    uint64_t max_tokens_block;
+    uint64_t runs, run_len_sum, median_run, max_run;
+    uint64_t bad_blocks;
+} aceapex_parse_stats;
+int aceapex_archive_parse_stats(aceapex_ctx* ctx, aceapex_archive* arc, aceapex_parse_stats* stats);
+
+/*
  * Decode the original bytes [start, start + len) into d_out (device pointer,
  * len bytes).  Paper, Random Access at Scale: only what the region depends on
  * is decoded, into context scratch, and the region is gathered out.  With a

@@ -82,6 +82,8 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
     std::vector<uint32_t> st_h;
     std::vector<SpanRec> h;
     std::vector<ItemDev> it;
+    std::vector<uint32_t> runs;
+    aceapex_parse_stats S{};
     int rc = ACEAPEX_OK;
     constexpr uint32_t kChunk = 16384;  // blocks per parse-only job
     for (uint32_t c0 = 0; c0 < P.n_blocks && rc == ACEAPEX_OK; c0 += kChunk) {
@@ -154,20 +156,60 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
             M->first[b] = M->o.size();
             if (st_h[i]) {
                 M->bad[b] = 1;
+                S.bad_blocks++;
                 t += n;
                 continue;
             }
+            // token records in token order: LL = this match's destination
+            // minus the previous token's end; a repeat-coded token ends a run
+            S.blocks++;
+            S.tokens += n;
+            S.values += 2ull * n;
+            S.max_tokens_block = std::max<uint64_t>(S.max_tokens_block, n);
+            const uint64_t B = (uint64_t)b * kBlock;
+            uint32_t end = 0, run = 0;
             for (uint32_t q = 0; q < n; q++, t++) {
                 const SpanRec& r = h[t];
-                const uint32_t ml = r.z >> 16;
+                const uint32_t ml = r.z >> 16, o = r.z & 0xffff, ll = o - end;
+                const uint64_t src = (uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32);
+                end = o + ml;
+                S.literal_bytes += ll;
+                S.match_bytes += ml;
+                S.multibyte_values += (ll >= 128) + (ml >= 128);
+                if (r.w == kLitOnly) {
+                    S.lit_only++;
+                    run++;
+                } else {
+                    if (B + o - src < ml) S.overlap_matches++;
+                    if (src < B) S.external_matches++;
+                    if (r.w == kNew) {
+                        S.new_matches++;
+                        run++;
+                    } else {
+                        S.rep_matches[r.w - kRep0]++;
+                        runs.push_back(run);
+                        run = 0;
+                    }
+                }
                 if (!ml) continue;
-                M->o.push_back((uint16_t)(r.z & 0xffff));
+                M->o.push_back((uint16_t)o);
                 M->ml.push_back((uint16_t)ml);
-                M->src.push_back((uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32));
+                M->src.push_back(src);
             }
+            runs.push_back(run);
         }
     }
     M->first[P.n_blocks] = M->o.size();
+    if (!runs.empty()) {
+        for (uint32_t v : runs) {
+            S.run_len_sum += v;
+            S.max_run = std::max<uint64_t>(S.max_run, v);
+        }
+        S.runs = runs.size();
+        std::nth_element(runs.begin(), runs.begin() + runs.size() / 2, runs.end());
+        S.median_run = runs[runs.size() / 2];
+    }
+    M->stats = S;
     cudaStreamDestroy(st);
     items.release();
     recs.release();
@@ -297,6 +339,14 @@ void acx::need_intervals(const Ivs& need, uint32_t raw_len, std::vector<uint32_t
 extern "C" int aceapex_archive_index(aceapex_ctx* c, aceapex_archive* A) {
     if (!c || !A) return fail(c, ACEAPEX_E_ARG, "archive_index: null argument");
     return build_match_index(c, A);
+}
+
+extern "C" int aceapex_archive_parse_stats(aceapex_ctx* c, aceapex_archive* A, aceapex_parse_stats* stats) {
+    if (!c || !A || !stats) return fail(c, ACEAPEX_E_ARG, "archive_parse_stats: null argument");
+    const int rc = build_match_index(c, A);
+    if (rc) return rc;
+    *stats = A->midx->stats;
+    return ACEAPEX_OK;
 }
 
 // Diagnostics (not part of the documented ABI; host only): the byte-level

@@ -56,6 +56,7 @@ struct MatchIndex {
     std::vector<uint16_t> o, ml;
     std::vector<uint64_t> src;
     std::vector<uint8_t> bad;  // per block: 1 if the parse found it corrupt (it then lists no matches)
+    aceapex_parse_stats stats{};  // counted from the same pass's token records
 };
 
 }  // namespace acx

@@ -26,7 +26,7 @@ EXPORTED = [
     "aceapex_batch_decode", "aceapex_decode_range", "aceapex_archive_index", "aceapex_server_create",
     "aceapex_server_now_ns", "aceapex_server_submit_many", "aceapex_server_submit", "aceapex_server_poll",
     "aceapex_server_drain", "aceapex_server_get_stats", "aceapex_server_last_error", "aceapex_server_destroy",
-    "aceapex_autotune", "aceapex_shard_range",
+    "aceapex_autotune", "aceapex_shard_range", "aceapex_archive_parse_stats",
 ]
 BATCH_GRAPH = 1
 
@@ -54,6 +54,16 @@ class ArchiveInfo(ctypes.Structure):
     _fields_ = [("total_size", ctypes.c_uint64), ("n_blocks", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("min_match", ctypes.c_uint32), ("max_tokens", ctypes.c_uint32),
                 ("archive_bytes", ctypes.c_uint64), ("tokens", ctypes.c_uint64)]
+
+
+class ParseStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64 * 4 if n == "rep_matches" else ctypes.c_uint64) for n in (
+        "blocks", "tokens", "new_matches", "rep_matches", "lit_only", "values", "multibyte_values",
+        "literal_bytes", "match_bytes", "overlap_matches", "external_matches", "max_tokens_block",
+        "runs", "run_len_sum", "median_run", "max_run", "bad_blocks")]
+
+    def as_dict(self):
+        return {n: (list(getattr(self, n)) if n == "rep_matches" else getattr(self, n)) for n, _ in self._fields_}
 
 
 class BatchItem(ctypes.Structure):
@@ -129,6 +139,7 @@ def load(path: str | None = None):
     L.aceapex_batch_destroy.argtypes = [vp]
     L.aceapex_decode_range.argtypes = [vp, vp, u64, u64, vp, vp, c.POINTER(Stats)]
     L.aceapex_archive_index.argtypes = [vp, vp]
+    L.aceapex_archive_parse_stats.argtypes = [vp, vp, c.POINTER(ParseStats)]
     L.aceapex_server_create.argtypes = [vp, vp, c.POINTER(ServerParams), c.POINTER(vp)]
     L.aceapex_server_now_ns.argtypes = [vp]
     L.aceapex_server_now_ns.restype = c.c_int64
@@ -238,6 +249,14 @@ class Archive:
     def build_index(self):
         """aceapex_archive_index: the match index for byte-level closures."""
         _check(self.ctx._L.aceapex_archive_index(self.ctx.h, self.h), self.ctx.h, "archive_index")
+
+    def parse_stats(self) -> dict:
+        """aceapex_archive_parse_stats: token, command and run counts of the
+        device's parse-only pass (builds the match index if absent)."""
+        st = ParseStats()
+        _check(self.ctx._L.aceapex_archive_parse_stats(self.ctx.h, self.h, ctypes.byref(st)), self.ctx.h,
+               "archive_parse_stats")
+        return st.as_dict()
 
     @property
     def total(self) -> int:

@@ -92,6 +92,31 @@ def test_parse_only_pass_equals_oracle_parse(acx, ctx, enc):
     A.close()
 
 
+@pytest.mark.parametrize("enc", ["lib-dna", "lib-dna-norep", "lib-text", "oracle-text"])
+def test_parse_stats_equal_oracle_stats(acx, ctx, enc):
+    """Command counts, repeat-code shares and the dependency-free runs (paper,
+    The Last Sequential Element) of the device's parse equal the oracle's."""
+    kind = "text" if "text" in enc else "dna"
+    data = synth.corpus(kind, (3 << 20) + 901, 44)
+    arc = oracle.encode(data) if enc.startswith("oracle") else acx.encode(data, no_rep="norep" in enc)
+    A = opened(acx, ctx, arc)
+    got = A.parse_stats()
+    want = oracle.stats(arc)
+    assert got["bad_blocks"] == 0
+    pairs = [("blocks", "n_blocks"), ("tokens", "n_tokens"), ("new_matches", "n_new"), ("rep_matches", "n_rep"),
+             ("lit_only", "n_litonly"), ("values", "n_values"), ("multibyte_values", "n_multibyte_values"),
+             ("literal_bytes", "n_literal_bytes"), ("match_bytes", "n_match_bytes"),
+             ("overlap_matches", "n_overlap_tokens"), ("external_matches", "n_external_tokens"),
+             ("max_tokens_block", "max_tokens_block"), ("runs", "runs"), ("run_len_sum", "run_len_sum"),
+             ("median_run", "median_run")]
+    for g, w in pairs:
+        assert got[g] == want[w], (g, got[g], want[w])
+    assert sum(got["rep_matches"]) == want["hist_dependent"]
+    if "norep" in enc:
+        assert sum(got["rep_matches"]) == 0 and got["runs"] == got["blocks"]
+    A.close()
+
+
 @pytest.mark.parametrize("variant", [0, 1])
 def test_random_periodic_fills(acx, ctx, variant):
     """Random (distance, length) with distance in [1, 200] and length up to
