@@ -514,6 +514,7 @@ def run_serve(args, dist):
     by_id = {c["id"]: c for c in comps}
     idx = {int(i): k for k, i in enumerate(ids)}
     lat, win_bytes, closure, t_last = [], 0, [], 0.0
+    served, dec_blocks = [], []
     bad = [c for c in comps if c["status"] != 0]
     if bad:
         raise RuntimeError(f"{len(bad)} requests failed, first status {bad[0]['status']}")
@@ -523,8 +524,20 @@ def run_serve(args, dist):
             lat.append(c["latency_us"])
             win_bytes += int(lens[k])
             closure.append(c["closure_blocks"])
+            served.append(c["latency_us"] - c["queue_us"])
+            dec_blocks.append(c["decoded_blocks"])
             t_last = max(t_last, at[k] + c["latency_us"] / 1e6)
     lat = np.array(lat)
+    # service time (admission -> completion) against the blocks a request
+    # added to its tick's decode: fixed cost + cost per block, the form of
+    # the paper's single-seek model (a launch-bound fixed part plus a part
+    # that scales with work); meaningful when ticks hold one request each
+    if len(set(dec_blocks)) > 1:
+        slope, fixed = np.polyfit(np.array(dec_blocks, float), np.array(served, float), 1)
+        fit = {"fixed_us": round(float(fixed), 1), "us_per_decoded_block": round(float(slope), 3),
+               "requests": len(served)}
+    else:
+        fit = None
     # correctness: a sample of the requests against the generator's bytes
     smp = rng.choice(n_req, size=min(2000, n_req), replace=False)
     for k in smp:
@@ -549,6 +562,10 @@ def run_serve(args, dist):
         "throughput": {"value": round(gbs, 3), "unit": "GB/s", "requests_per_s": round(lat.size / window, 1)},
         "closure_blocks": {"mean": round(float(np.mean(closure)), 1), "p50": float(np.percentile(closure, 50)),
                            "p99": float(np.percentile(closure, 99))},
+        "decoded_blocks": {"mean": round(float(np.mean(dec_blocks)), 1),
+                           "p50": float(np.percentile(dec_blocks, 50)), "p99": float(np.percentile(dec_blocks, 99))},
+        "service_us": {"p50": round(float(np.percentile(served, 50)), 1),
+                       "p99": round(float(np.percentile(served, 99)), 1), "fit": fit},
         "server": {"ticks": st_all["ticks"], "blocks_decoded": st_all["blocks_decoded"],
                    "blocks_hit": st_all["blocks_hit"],
                    "hit_rate": round(st_all["blocks_hit"] / max(1, st_all["blocks_hit"] + st_all["blocks_decoded"]), 4),
