@@ -610,7 +610,9 @@ __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
 
 // ---- cross-block pass --------------------------------------------------------------------
 // Are the bytes [s, e) (absolute) final?  The local pass writes every
-// block's pending-byte bitmap; a clear bit means a final byte.
+// block's pending-byte bitmap; a clear bit means a final byte.  The loads are
+// relaxed: a caller that goes on to read the bytes issues one fence first
+// (strong read + fence = acquire pattern), so a failed poll costs no fence.
 __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t e) {
     for (uint64_t a = s >> 14; a <= (e - 1) >> 14; a++) {
         const uint64_t A = a << 14;
@@ -620,7 +622,7 @@ __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t 
         if (sl == kNoSlot) return false;  // not in this decode's output: never final
         const uint32_t* pm = L.pmap + sl * (kBlock / 32);
         for (uint32_t w = lo >> 5; w <= ((hi - 1) >> 5); w++)
-            if (ld_acquire_u32(pm + w) & range_mask(w, lo, hi)) return false;  // pairs with red_and_release
+            if (ld_relaxed_u32(pm + w) & range_mask(w, lo, hi)) return false;  // pairs with the fenced clears
     }
     return true;
 }
@@ -653,6 +655,7 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec re
     const bool ready = has && piece_final(L, src, phase, period, len);
     const uint32_t rmask = __ballot_sync(ACX_FULL, ready);
     if (!rmask) return false;
+    __threadfence();  // acquire: the bitmap reads above are ordered before the source reads below
     wrec[lane] = rec;
     wdst[lane] = (uint64_t)dslot * kBlock + o;
     __syncwarp();
@@ -688,10 +691,10 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec re
             }
         }
     }
-    __threadfence();  // every lane's stores are visible before any bit is cleared
+    __threadfence();  // release: every lane's stores are visible before any bit is cleared
     if (ready) {
         uint32_t* pm = L.pmap + (uint64_t)dslot * (kBlock / 32);
-        for (uint32_t w = o >> 5; w <= ((o + len - 1) >> 5); w++) red_and_release(pm + w, ~range_mask(w, o, o + len));
+        for (uint32_t w = o >> 5; w <= ((o + len - 1) >> 5); w++) red_and_relaxed(pm + w, ~range_mask(w, o, o + len));
     }
     __syncwarp();
     return ready;

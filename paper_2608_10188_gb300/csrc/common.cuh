@@ -56,10 +56,10 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-// Atomic AND with release semantics: the thread's earlier writes are visible
-// to any thread that observes this update with an acquire load.
-__device__ __forceinline__ void red_and_release(uint32_t* p, uint32_t v) {
-    asm volatile("red.release.gpu.global.and.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// Atomic AND without ordering of its own: after a fence (fence + strong write
+// is a release pattern), several of them share that one fence.
+__device__ __forceinline__ void red_and_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.and.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // ---- mbarrier / TMA (1-D bulk copies) ---------------------------------------------------
