@@ -125,6 +125,20 @@ int aceapex_archive_open(aceapex_ctx* c, const void* d_arc, const void* h_arc, u
         if (e == cudaSuccess && !A->plan.deps.empty())
             e = cudaMemcpy(A->d_deps, A->plan.deps.data(), A->plan.deps.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && nb) {
+        // entropy-stage hand-out order: most symbols first (longest-first
+        // scheduling keeps the last wave of the persistent warps short)
+        std::vector<uint32_t> ord(nb);
+        std::vector<uint64_t> key(nb);
+        for (size_t b = 0; b < nb; b++) {
+            const BlockDev& bd = A->plan.blk[b];
+            ord[b] = (uint32_t)b;
+            key[b] = (uint64_t)bd.s_raw[0] + bd.s_raw[1] + bd.s_raw[2] + bd.s_raw[3];
+        }
+        std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return key[x] > key[y]; });
+        e = cudaMalloc(&A->d_order, nb * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMemcpy(A->d_order, ord.data(), nb * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         aceapex_archive_close(A);
         return cuda_fail(c, e, "archive_open");
@@ -139,6 +153,7 @@ int aceapex_archive_close(aceapex_archive* A) {
     if (A->d_blk) cudaFree(A->d_blk);
     if (A->d_dtab) cudaFree(A->d_dtab);
     if (A->d_deps) cudaFree(A->d_deps);
+    if (A->d_order) cudaFree(A->d_order);
     if (A->d_slot) cudaFree(A->d_slot);
     delete A->midx;
     delete A;
@@ -227,6 +242,7 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     J.min_match = P.min_match;
     J.item_base = 0;
     J.deps = A->d_deps;
+    J.order = A->d_order;
     job.arcs = nullptr;
     job.n_arcs = 1;
     job.n_items = P.n_blocks;

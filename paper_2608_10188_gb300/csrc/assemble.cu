@@ -25,6 +25,8 @@
 //   final, so a pending span waits only on the spans its source really
 //   depends on, which lie at lower positions and were taken earlier: the
 //   ascending order makes the bounded waits deadlock-free.
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -613,13 +615,28 @@ __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
 // block's pending-byte bitmap; a clear bit means a final byte.  The loads are
 // relaxed: a caller that goes on to read the bytes issues one fence first
 // (strong read + fence = acquire pattern), so a failed poll costs no fence.
+// A range of at most 32 bytes (every piece) covers at most two bitmap words,
+// possibly of two blocks: both are loaded before either is tested.
 __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t e) {
+    if (e - s <= 32) {
+        const uint64_t l = e - 1;
+        const uint64_t s0 = slot_of(L, s >> 14), s1 = slot_of(L, l >> 14);
+        if (s0 == kNoSlot || s1 == kNoSlot) return false;  // not in this decode's output: never final
+        const uint32_t o0 = (uint32_t)(s & (kBlock - 1)), o1 = (uint32_t)(l & (kBlock - 1));
+        const uint32_t* p0 = L.pmap + s0 * (kBlock / 32) + (o0 >> 5);
+        const uint32_t* p1 = L.pmap + s1 * (kBlock / 32) + (o1 >> 5);
+        const uint32_t lo0 = 0xffffffffu << (o0 & 31);         // bits from o0 on in its word
+        const uint32_t hi1 = 0xffffffffu >> (31 - (o1 & 31));  // bits up to o1 in its word
+        if (p0 == p1) return (ld_relaxed_u32(p0) & lo0 & hi1) == 0;
+        const uint32_t w0 = ld_relaxed_u32(p0), w1 = ld_relaxed_u32(p1);
+        return ((w0 & lo0) | (w1 & hi1)) == 0;
+    }
     for (uint64_t a = s >> 14; a <= (e - 1) >> 14; a++) {
         const uint64_t A = a << 14;
         const uint32_t lo = (uint32_t)((s > A ? s : A) - A);
         const uint32_t hi = (uint32_t)((e < A + kBlock ? e : A + kBlock) - A);
         const uint64_t sl = slot_of(L, a);
-        if (sl == kNoSlot) return false;  // not in this decode's output: never final
+        if (sl == kNoSlot) return false;
         const uint32_t* pm = L.pmap + sl * (kBlock / 32);
         for (uint32_t w = lo >> 5; w <= ((hi - 1) >> 5); w++)
             if (ld_relaxed_u32(pm + w) & range_mask(w, lo, hi)) return false;  // pairs with the fenced clears
@@ -963,11 +980,17 @@ cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st) {
     const size_t sm = local_smem_bytes(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0);
     cudaError_t e = cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    // a small job (a seek, a serving tick) needs no more CTAs than ticket runs
+    const uint64_t runs = (job.n_items + (uint64_t)(job.chunk ? job.chunk : 1) - 1) / (job.chunk ? job.chunk : 1);
+    grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, runs));
     k_local<<<grid, kLocThreads, sm, st>>>(job);
     return cudaGetLastError();
 }
 
 cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st) {
+    // round 0 gives each warp one block at a time: a small job needs no more
+    // warps than blocks (the rounds' progress does not depend on the grid)
+    grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, (job.n_items + 31) / 32));
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kExtThreads);

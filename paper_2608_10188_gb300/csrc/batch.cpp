@@ -149,6 +149,7 @@ int aceapex_batch_create(aceapex_ctx* c, const aceapex_batch_item* items, int n,
         J.min_match = P.min_match;
         J.item_base = item_base;
         J.deps = A->d_deps;
+        J.order = A->d_order;
         item_base += P.n_blocks;
     }
     JobDev& job = B->job;

@@ -81,6 +81,7 @@ struct aceapex_archive {
     acx::BlockDev* d_blk = nullptr;
     uint32_t* d_dtab = nullptr;
     uint32_t* d_deps = nullptr;    // dependency lists (archives that carry them)
+    uint32_t* d_order = nullptr;   // blocks by decreasing symbol count (entropy-stage hand-out order)
     uint32_t* d_slot = nullptr;    // block -> output slot of subset decodes (allocated on first use)
     acx::MatchIndex* midx = nullptr;  // match index (aceapex_archive_index), or nullptr
     std::vector<uint32_t> seen;    // closure walk marks (epoch per block)

@@ -96,6 +96,9 @@ struct ArcJob {
     uint32_t* slot;           // block -> output slot: block b's bytes at out + slot[b]*kBlock, its
                               // pending count at npend[slot[b]] and bitmap at pmap + slot[b]*512;
                               // the entropy stage writes the entries of the job's items
+    const uint32_t* order;    // whole-archive jobs (items == nullptr, lo = 0): the entropy stage's
+                              // ticket t decodes item order[t] (blocks with the most symbols first,
+                              // so the stage's last wave is short); nullptr: ticket t is item t
 };
 
 constexpr uint32_t kMaxArcsPerJob = 3000;  // rANS tickets [3, 3 + n_arcs) stay below kTrace

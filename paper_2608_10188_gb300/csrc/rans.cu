@@ -16,6 +16,8 @@
 //  * K = 64 / 128 lanes run as 2 / 4 independent states per warp lane (ILP);
 //  * ring residency is checked once per 4 steps, not per step.
 // Every wait is bounded by %globaltimer.
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -340,10 +342,10 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
                 cnext = __shfl_sync(ACX_FULL, t0, 0);
                 cleft = chunk;
             }
-            const uint32_t it = cnext++;
+            const uint32_t tk = cnext++;
             cleft--;
-            if (it >= n_a) break;
-            const ItemRef ir = item_ref(J, it);
+            if (tk >= n_a) break;
+            const ItemRef ir = item_ref(J, J.order ? J.order[tk] : tk);
             const uint32_t b = ir.blk;
             if (J.items && J.slot && lane == 0) J.slot[b] = ir.slot;  // read by the cross-block pass
             const BlockDev& bd = J.blk[b];
@@ -408,6 +410,9 @@ cudaError_t launch_rans(const JobDev& job, int grid, cudaStream_t st) {
     const size_t sm = rans_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_rans, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    // a small job needs no more CTAs than its warps can take ticket runs
+    const uint64_t per_cta = (uint64_t)kRansWarps * (job.chunk ? job.chunk : 1);
+    grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, (job.n_items + per_cta - 1) / per_cta));
     k_rans<<<grid, kRansWarps * 32, sm, st>>>(job);
     return cudaGetLastError();
 }
