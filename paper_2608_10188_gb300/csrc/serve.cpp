@@ -112,6 +112,8 @@ struct aceapex_server {
         std::vector<Ivs> need;  // wanted bytes of sched[i]
         bool bad = false;       // depends on a block the parse found corrupt
     };
+    static constexpr int64_t kSpinNs = 250000;  // the worker yields instead of sleeping this close to an arrival
+    static constexpr size_t kInlineWalks = 2;  // ticks of at most this many candidates walk on the worker alone
     std::vector<std::thread> pool;
     std::vector<TickState> pool_ts;
     std::mutex pool_mu;
@@ -241,6 +243,12 @@ void aceapex_server::walk_all(const std::vector<Req>& reqs, std::vector<WalkOut>
     pool_outs = &outs;
     pool_n = reqs.size();
     pool_next.store(0);
+    if (reqs.size() <= kInlineWalks || pool.empty()) {
+        // a lone request (an unloaded server): waking the pool threads would
+        // cost more than the walk itself
+        walk_items(0);
+        return;
+    }
     {
         std::lock_guard<std::mutex> g(pool_mu);
         pool_busy = (int)pool.size();
@@ -507,8 +515,10 @@ void aceapex_server::run() {
             const int64_t tn = now();
             int64_t wait_ns = 2000000;
             if (next_at >= 0) wait_ns = std::max<int64_t>(0, std::min<int64_t>(wait_ns, next_at - tn));
-            if (wait_ns > 20000)
-                cv.wait_for(g, std::chrono::nanoseconds(wait_ns - 10000));
+            // a timed sleep may end tens of microseconds late (timer slack):
+            // sleep until shortly before the next arrival, then yield
+            if (wait_ns > kSpinNs)
+                cv.wait_for(g, std::chrono::nanoseconds(wait_ns - kSpinNs));
             else if (wait_ns > 0) {
                 g.unlock();
                 std::this_thread::yield();
