@@ -773,9 +773,9 @@ def main():
 # (4,096 blocks) scaled to the genome's 15,499 blocks; absent (null) for
 # workloads and kernels without a capture of the current code
 TRAFFIC = {
-    ("chr1-shaped synthetic genome 253,935,557 B", "k_rans"): 100_760_000,
-    ("chr1-shaped synthetic genome 253,935,557 B", "k_local"): 333_290_000,
-    ("chr1-shaped synthetic genome 253,935,557 B", "k_external"): 140_710_000,
+    ("chr1-shaped synthetic genome 253,935,557 B", "k_rans"): 99_840_000,
+    ("chr1-shaped synthetic genome 253,935,557 B", "k_local"): 332_140_000,
+    ("chr1-shaped synthetic genome 253,935,557 B", "k_external"): 140_940_000,
 }
 
 

@@ -744,15 +744,29 @@ __device__ bool grid_barrier(uint32_t* counters, uint32_t reset, uint64_t deadli
     return ok_s != 0;
 }
 
-// Append the lanes' unfinished spans to a work list (warp-aggregated).
+// Appends to a work list go through a per-warp staging buffer in shared
+// memory: the list's count is one word that every warp of the grid would
+// otherwise hit with an atomic at every step, so a warp reserves space for
+// kStage entries at a time.  `sn` (warp-uniform) counts the staged entries.
 typedef JobDev::ListEnt ListEnt;
-__device__ __forceinline__ void append(bool keep, ListEnt e, ListEnt* list, uint32_t* cnt, int lane) {
+constexpr uint32_t kStage = 64;
+__device__ __forceinline__ void stage_flush(ListEnt* buf, uint32_t& sn, ListEnt* list, uint32_t* cnt, int lane) {
+    if (sn == 0) return;
+    __syncwarp();
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(cnt, sn);
+    base = __shfl_sync(ACX_FULL, base, 0);
+    for (uint32_t i = lane; i < sn; i += 32) list[base + i] = buf[i];
+    __syncwarp();
+    sn = 0;
+}
+__device__ __forceinline__ void append(bool keep, ListEnt e, ListEnt* buf, uint32_t& sn, ListEnt* list, uint32_t* cnt,
+                                       int lane) {
     const uint32_t m = __ballot_sync(ACX_FULL, keep);
     if (!m) return;
-    uint32_t base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(cnt, (uint32_t)__popc(m));
-    base = __shfl_sync(ACX_FULL, base, __ffs(m) - 1);
-    if (keep) list[base + __popc(m & ((1u << lane) - 1))] = e;
+    if (sn + __popc(m) > kStage) stage_flush(buf, sn, list, cnt, lane);
+    if (keep) buf[sn + __popc(m & ((1u << lane) - 1))] = e;
+    sn += __popc(m);
 }
 
 // Round trace (diagnostics): work-list size and start time (ns) of every round.
@@ -780,7 +794,8 @@ __device__ void report_stalled(const JobDev& job, uint32_t in, uint32_t n, uint3
 // One pass over work list `in` (n entries) by warps w0, w0 + nw, ...: every
 // piece is attempted once; the unfinished ones go to list `out`.
 __device__ void round_pass(const JobDev& job, uint32_t in, uint32_t out, uint32_t n, uint32_t w0, uint32_t nw,
-                           SpanRec* wrec, uint64_t* wdst, int lane) {
+                           SpanRec* wrec, uint64_t* wdst, ListEnt* sbuf, int lane) {
+    uint32_t sn = 0;
     for (uint32_t i0 = w0 * 32; i0 < n; i0 += nw * 32) {
         const uint32_t i = i0 + lane;
         const bool has = i < n;
@@ -800,8 +815,9 @@ __device__ void round_pass(const JobDev& job, uint32_t in, uint32_t out, uint32_
             if (mine) done = d2;
             todo &= ~__ballot_sync(ACX_FULL, mine);
         }
-        append(has && !done, e, job.lists[out], &job.counters[kListCnt + out], lane);
+        append(has && !done, e, sbuf, sn, job.lists[out], &job.counters[kListCnt + out], lane);
     }
+    stage_flush(sbuf, sn, job.lists[out], &job.counters[kListCnt + out], lane);
 }
 
 // The last rounds on one CTA (the other CTAs have left): list `in` holds n
@@ -809,12 +825,12 @@ __device__ void round_pass(const JobDev& job, uint32_t in, uint32_t out, uint32_
 // CTA barriers; the same progress argument as the grid rounds ends them.
 constexpr uint32_t kSoloMax = 4 * kExtThreads;  // lists up to four CTA-wide passes
 __device__ void solo_rounds(const JobDev& job, uint32_t in, uint32_t n, uint32_t round, uint64_t deadline,
-                            SpanRec* wrec, uint64_t* wdst, int lane) {
+                            SpanRec* wrec, uint64_t* wdst, ListEnt* sbuf, int lane) {
     __shared__ uint32_t n_next;
     const uint32_t warp = threadIdx.x >> 5, nw = kExtThreads / 32;
     for (;;) {
         const uint32_t out = in ^ 1u;
-        round_pass(job, in, out, n, warp, nw, wrec, wdst, lane);
+        round_pass(job, in, out, n, warp, nw, wrec, wdst, sbuf, lane);
         __syncthreads();  // every append of this round is visible to the CTA
         if (threadIdx.x == 0) {
             n_next = *((volatile uint32_t*)&job.counters[kListCnt + out]);
@@ -849,8 +865,10 @@ __device__ void solo_rounds(const JobDev& job, uint32_t in, uint32_t n, uint32_t
 __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
     __shared__ SpanRec recs[kExtThreads];
     __shared__ uint64_t dsts[kExtThreads];
+    __shared__ ListEnt stage[kExtThreads / 32][kStage];
     SpanRec* wrec = recs + (threadIdx.x & ~31u);
     uint64_t* wdst = dsts + (threadIdx.x & ~31u);
+    ListEnt* sbuf = stage[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -887,6 +905,7 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
         int l_arc = 0;
         uint64_t t0 = 0;
         uint32_t spins = 0, nap = 64;
+        uint32_t sn0 = 0;  // entries staged for list 0
         const uint32_t lt_mask = (1u << lane) - 1;
         for (;;) {
             uint32_t idle = __ballot_sync(ACX_FULL, !has);
@@ -933,7 +952,7 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             }
             // give up on pieces that waited too long: the rounds finish them
             const bool giveup = has && gtimer() - t0 > wait_ns;
-            append(giveup, ListEnt{l_span, l_item}, job.lists[0], &job.counters[kListCnt], lane);
+            append(giveup, ListEnt{l_span, l_item}, sbuf, sn0, job.lists[0], &job.counters[kListCnt], lane);
             if (giveup) has = false;
             if (__any_sync(ACX_FULL, progressed || giveup)) {
                 spins = 0;
@@ -947,6 +966,7 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
                 }
             }
         }
+        stage_flush(sbuf, sn0, job.lists[0], &job.counters[kListCnt], lane);
     }
     uint32_t n_prev = 0xffffffffu;
     for (uint32_t round = 1;; round++) {
@@ -967,10 +987,10 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
         if (n <= kSoloMax) {
             // a short list: one CTA finishes the remaining rounds with CTA
             // barriers instead of grid barriers
-            if (blockIdx.x == 0) solo_rounds(job, in, n, round, deadline, wrec, wdst, lane);
+            if (blockIdx.x == 0) solo_rounds(job, in, n, round, deadline, wrec, wdst, sbuf, lane);
             return;
         }
-        round_pass(job, in, out, n, gwarp, nwarps, wrec, wdst, lane);
+        round_pass(job, in, out, n, gwarp, nwarps, wrec, wdst, sbuf, lane);
     }
 }
 
