@@ -64,6 +64,61 @@ void iv_add(Ivs& v, uint32_t s, uint32_t e) {
 
 }  // namespace
 
+namespace {
+
+// Count one parsed block into the parse statistics (paper, The Last
+// Sequential Element).  Its token records, in token order, hold the source
+// (x, y bits 0..7), the destination offset and match length (z) and the
+// command (w).  A token's literal run is its destination minus the previous
+// token's end; a repeat-coded token ends a dependency-free run, and the block
+// end ends the last one (the history resets per block).
+void count_block(const SpanRec* h, uint32_t n, uint64_t B, aceapex_parse_stats& S, std::vector<uint32_t>& runs) {
+    S.blocks++;
+    S.tokens += n;
+    S.values += 2ull * n;
+    S.max_tokens_block = std::max<uint64_t>(S.max_tokens_block, n);
+    uint32_t end = 0, run = 0;
+    for (uint32_t q = 0; q < n; q++) {
+        const SpanRec& r = h[q];
+        const uint32_t ml = r.z >> 16, o = r.z & 0xffff, ll = o - end;
+        const uint64_t src = (uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32);
+        end = o + ml;
+        S.literal_bytes += ll;
+        S.match_bytes += ml;
+        S.multibyte_values += (ll >= 128) + (ml >= 128);
+        if (r.w == kLitOnly) {
+            S.lit_only++;
+            run++;
+        } else {
+            if (B + o - src < ml) S.overlap_matches++;
+            if (src < B) S.external_matches++;
+            if (r.w == kNew) {
+                S.new_matches++;
+                run++;
+            } else {
+                S.rep_matches[r.w - kRep0]++;
+                runs.push_back(run);
+                run = 0;
+            }
+        }
+    }
+    runs.push_back(run);
+}
+
+// Sum, maximum and median (rank floor(runs / 2)) of the run lengths.
+void finish_runs(aceapex_parse_stats& S, std::vector<uint32_t>& runs) {
+    if (runs.empty()) return;
+    for (uint32_t v : runs) {
+        S.run_len_sum += v;
+        S.max_run = std::max<uint64_t>(S.max_run, v);
+    }
+    S.runs = runs.size();
+    std::nth_element(runs.begin(), runs.begin() + runs.size() / 2, runs.end());
+    S.median_run = runs[runs.size() / 2];
+}
+
+}  // namespace
+
 int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
     if (A->midx) return ACEAPEX_OK;
     const Plan& P = A->plan;
@@ -160,55 +215,19 @@ int acx::build_match_index(aceapex_ctx* c, aceapex_archive* A) {
                 t += n;
                 continue;
             }
-            // token records in token order: LL = this match's destination
-            // minus the previous token's end; a repeat-coded token ends a run
-            S.blocks++;
-            S.tokens += n;
-            S.values += 2ull * n;
-            S.max_tokens_block = std::max<uint64_t>(S.max_tokens_block, n);
-            const uint64_t B = (uint64_t)b * kBlock;
-            uint32_t end = 0, run = 0;
+            count_block(h.data() + t, n, (uint64_t)b * kBlock, S, runs);
             for (uint32_t q = 0; q < n; q++, t++) {
                 const SpanRec& r = h[t];
-                const uint32_t ml = r.z >> 16, o = r.z & 0xffff, ll = o - end;
-                const uint64_t src = (uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32);
-                end = o + ml;
-                S.literal_bytes += ll;
-                S.match_bytes += ml;
-                S.multibyte_values += (ll >= 128) + (ml >= 128);
-                if (r.w == kLitOnly) {
-                    S.lit_only++;
-                    run++;
-                } else {
-                    if (B + o - src < ml) S.overlap_matches++;
-                    if (src < B) S.external_matches++;
-                    if (r.w == kNew) {
-                        S.new_matches++;
-                        run++;
-                    } else {
-                        S.rep_matches[r.w - kRep0]++;
-                        runs.push_back(run);
-                        run = 0;
-                    }
-                }
+                const uint32_t ml = r.z >> 16;
                 if (!ml) continue;
-                M->o.push_back((uint16_t)o);
+                M->o.push_back((uint16_t)(r.z & 0xffff));
                 M->ml.push_back((uint16_t)ml);
-                M->src.push_back(src);
+                M->src.push_back((uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32));
             }
-            runs.push_back(run);
         }
     }
     M->first[P.n_blocks] = M->o.size();
-    if (!runs.empty()) {
-        for (uint32_t v : runs) {
-            S.run_len_sum += v;
-            S.max_run = std::max<uint64_t>(S.max_run, v);
-        }
-        S.runs = runs.size();
-        std::nth_element(runs.begin(), runs.begin() + runs.size() / 2, runs.end());
-        S.median_run = runs[runs.size() / 2];
-    }
+    finish_runs(S, runs);
     M->stats = S;
     cudaStreamDestroy(st);
     items.release();
@@ -347,6 +366,26 @@ extern "C" int aceapex_archive_parse_stats(aceapex_ctx* c, aceapex_archive* A, a
     if (rc) return rc;
     *stats = A->midx->stats;
     return ACEAPEX_OK;
+}
+
+// Diagnostics (not part of the documented ABI; host only): the parse
+// statistics of token records given on the host — recs[4 * t .. 4 * t + 4)
+// is token t's record (as the parse-only pass writes it), blocks in order,
+// n_tok[b] tokens each.
+extern "C" int acx_debug_parse_stats(const uint32_t* recs, const uint32_t* n_tok, uint32_t n_blocks,
+                                     aceapex_parse_stats* out) {
+    if (!recs || !n_tok || !out) return -1;
+    aceapex_parse_stats S{};
+    std::vector<uint32_t> runs;
+    const SpanRec* h = reinterpret_cast<const SpanRec*>(recs);
+    uint64_t t = 0;
+    for (uint32_t b = 0; b < n_blocks; b++) {
+        count_block(h + t, n_tok[b], (uint64_t)b * kBlock, S, runs);
+        t += n_tok[b];
+    }
+    finish_runs(S, runs);
+    *out = S;
+    return 0;
 }
 
 // Diagnostics (not part of the documented ABI; host only): the byte-level

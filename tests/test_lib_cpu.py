@@ -227,3 +227,48 @@ def test_byte_level_closure_is_sufficient(acx, kind, no_rep):
                     for j in range(m):
                         out[d + j] = out[s + j]
         assert np.array_equal(out[start:start + length], data[start:start + length]), (start, length)
+
+
+BLOCK = 16384
+PARSE_STAT_PAIRS = [("blocks", "n_blocks"), ("tokens", "n_tokens"), ("new_matches", "n_new"),
+                    ("rep_matches", "n_rep"), ("lit_only", "n_litonly"), ("values", "n_values"),
+                    ("multibyte_values", "n_multibyte_values"), ("literal_bytes", "n_literal_bytes"),
+                    ("match_bytes", "n_match_bytes"), ("overlap_matches", "n_overlap_tokens"),
+                    ("external_matches", "n_external_tokens"), ("max_tokens_block", "max_tokens_block"),
+                    ("runs", "runs"), ("run_len_sum", "run_len_sum"), ("median_run", "median_run")]
+
+
+@pytest.mark.parametrize("kind,no_rep", [("dna", False), ("dna", True), ("text", False)])
+def test_parse_stats_counting_equals_oracle_counts(acx, kind, no_rep):
+    """The host counting behind aceapex_archive_parse_stats (paper, The Last
+    Sequential Element: repeat-coded share and dependency-free runs), fed the
+    token records the parse-only pass would write, built here from the
+    oracle's parse, gives the oracle's own counts."""
+    import ctypes
+    data = synth.corpus(kind, (1 << 20) + 333, 7)
+    arc = acx.encode(data, no_rep=no_rep)
+    nb = (data.size + BLOCK - 1) // BLOCK
+    recs, ntok = [], np.zeros(nb, np.uint32)
+    for b in range(nb):
+        t = oracle.parse_block(arc, b)
+        ntok[b] = t["cmd"].size
+        r = np.zeros((t["cmd"].size, 4), np.uint32)
+        src = t["src"].astype(np.uint64)
+        r[:, 0] = (src & np.uint64(0xffffffff)).astype(np.uint32)
+        r[:, 1] = ((src >> np.uint64(32)) & np.uint64(0xff)).astype(np.uint32)
+        r[:, 2] = (t["dst"].astype(np.int64) - b * BLOCK).astype(np.uint32) | (t["ml"].astype(np.uint32) << 16)
+        r[:, 3] = t["cmd"]
+        recs.append(r)
+    recs = np.ascontiguousarray(np.concatenate(recs))
+    f = acx.load().acx_debug_parse_stats
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    st = acx.lib.ParseStats()
+    assert f(recs.ctypes.data, ntok.ctypes.data, nb, ctypes.byref(st)) == 0
+    got, want = st.as_dict(), oracle.stats(arc)
+    for g, w in PARSE_STAT_PAIRS:
+        assert got[g] == want[w], (g, got[g], want[w])
+    assert sum(got["rep_matches"]) == want["hist_dependent"]
+    if no_rep:
+        # no repeat codes: one run per block, the block's token count
+        assert got["runs"] == nb and got["median_run"] == int(np.sort(ntok)[nb // 2])
