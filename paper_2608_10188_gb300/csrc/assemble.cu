@@ -1002,15 +1002,12 @@ cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     // a small job (a seek, a serving tick) needs no more CTAs than ticket runs
     const uint64_t runs = (job.n_items + (uint64_t)(job.chunk ? job.chunk : 1) - 1) / (job.chunk ? job.chunk : 1);
-    grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, runs));
+    grid = job_grid(grid, runs);
     k_local<<<grid, kLocThreads, sm, st>>>(job);
     return cudaGetLastError();
 }
 
 cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st) {
-    // round 0 gives each warp one block at a time: a small job needs no more
-    // warps than blocks (the rounds' progress does not depend on the grid)
-    grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, (job.n_items + 31) / 32));
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kExtThreads);

@@ -20,6 +20,10 @@ cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st);
 cudaError_t launch_plain(const JobDev& job, int grid, cudaStream_t st);
 size_t local_smem_bytes(uint32_t T, uint32_t LB, bool need = false);
 int rans_occupancy();
+// Grid of a persistent kernel for a job that can use `need` CTAs at most:
+// no more than `full`, and no fewer than one per SM, so that a mid-size job
+// spreads its warps over the whole GPU instead of packing a few SMs.
+int job_grid(int full, uint64_t need);
 int local_occupancy(size_t smem);
 int external_occupancy();
 int plain_occupancy();

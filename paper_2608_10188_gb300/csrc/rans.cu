@@ -401,6 +401,13 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
 
 size_t rans_smem_bytes() { return sizeof(RansSmem); }
 
+int job_grid(int full, uint64_t need) {
+    int dev = 0, n_sms = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t g = std::max<uint64_t>(need, (uint64_t)std::max(n_sms, 1));
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)full, g));
+}
+
 cudaError_t launch_prologue(uint32_t* counters, uint32_t n_counters, cudaStream_t st, int* errs, uint32_t n_errs) {
     k_prologue<<<1, 128, 0, st>>>(counters, n_counters, errs, n_errs);
     return cudaGetLastError();
@@ -412,7 +419,7 @@ cudaError_t launch_rans(const JobDev& job, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     // a small job needs no more CTAs than its warps can take ticket runs
     const uint64_t per_cta = (uint64_t)kRansWarps * (job.chunk ? job.chunk : 1);
-    grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, (job.n_items + per_cta - 1) / per_cta));
+    grid = job_grid(grid, (job.n_items + per_cta - 1) / per_cta);
     k_rans<<<grid, kRansWarps * 32, sm, st>>>(job);
     return cudaGetLastError();
 }
