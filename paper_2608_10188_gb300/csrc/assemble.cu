@@ -263,7 +263,6 @@ __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
         const uint64_t B = (uint64_t)b * kBlock;
         const uint32_t R = bd.raw_len, n = bd.n_tok, LB = bd.s_raw[kLen], n_lit = bd.s_raw[kLit];
         const uint32_t n_new = bd.n_new;
-        const uint8_t* scr = J.scratch + ir.scratch;
         bool bad = n > job.max_tok || LB > job.max_lenb || n_new > job.max_tok;
         int stage = bad ? kStageLimits : 0;
         auto mark = [&](bool cond, int st) {
@@ -272,7 +271,6 @@ __global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
 
         // ---- stage the four decoded streams with 1-D TMA bulk copies (unless
         //      they were prefetched during the previous block) ----
-        (void)scr;
         if (!bad && tid == 0 && !prefetched) stage_streams(job, item, tcmd, lenb, soff, slit, bar);
         for (uint32_t i = tid; i < kBlock / 32; i += kLocThreads) pend[i] = 0;
         if (tid == 0) misc[1] = 0;
