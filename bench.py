@@ -45,8 +45,9 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
-                   help="single: one archive (--corpus); batch: the 96-archive mixed batch; serve: region server")
+    p.add_argument("--workload", default="single", choices=["single", "batch", "serve", "depth"],
+                   help="single: one archive (--corpus); batch: the 96-archive mixed batch; serve: region server; "
+                        "depth: the encoder's chain-depth statistics of the corpus (host only, no GPU)")
     p.add_argument("--corpus", default="dna", choices=["dna", "text"])
     p.add_argument("--size", type=int, default=0)
     p.add_argument("--encoding", default="history", choices=["history", "no_rep"])
@@ -593,8 +594,46 @@ def init_dist(args):
     return d
 
 
+def run_depth(args):
+    """Chain-depth statistics of the corpus as the library encoder parses it
+    (paper, Depth Does Not Govern Latency): the per-block maximum depth, its
+    median and tail, and the depth of the matches.  Host-only work."""
+    import paper_2608_10188_gb300 as acx
+    acx.build.build()
+    size, wname = workload(args)
+    data = synth.corpus(args.corpus, size, 0)
+    st = {}
+    t = time.perf_counter()
+    arc = acx.encode(data, no_rep=args.encoding == "no_rep", max_lanes=args.lanes, max_depth=args.max_depth,
+                     stats=st)
+    enc_s = time.perf_counter() - t
+    bm = np.array(st["block_max_depth"], np.int64)
+    md = np.array(st["match_depth"], np.int64)
+
+    def rank(h, q):  # the element of rank floor(q * (count - 1)) of the sorted values
+        c = np.cumsum(h)
+        return int(np.searchsorted(c, int(q * (c[-1] - 1)), side="right"))
+
+    line = {
+        "metric": "chain depth", "workload": wname, "encoding": args.encoding,
+        "max_depth": "none" if args.max_depth == 0xFFFFFFFF else (args.max_depth or 16),
+        "ratio": round(size / len(arc), 4), "archive_bytes": len(arc), "blocks": st["blocks"],
+        "matches": st["matches"], "encode_s": round(enc_s, 1),
+        "block_max_depth": {"median": rank(bm, 0.5), "p90": rank(bm, 0.9), "p99": rank(bm, 0.99),
+                            "max": int(np.nonzero(bm)[0].max()),
+                            "blocks_with_matches": int(bm[1:].sum())},
+        "match_depth": {"median": rank(md, 0.5), "p99": rank(md, 0.99), "max": int(np.nonzero(md)[0].max()),
+                        "share_depth_1": round(float(md[1] / max(md.sum(), 1)), 4),
+                        "mean": round(float((md * np.arange(256)).sum() / max(md.sum(), 1)), 3)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == "depth":
+        run_depth(args)
+        return
     dist = init_dist(args)
     if args.impl == "reference":
         run_reference(args, dist)

@@ -150,6 +150,24 @@ int aceapex_encode(const uint8_t* src, uint64_t n, const aceapex_enc_params* par
 void aceapex_free(void* p);
 
 /*
+ * Chain-depth statistics of an encode (paper, "Depth Does Not Govern
+ * Latency": the depth of the copy chains, and how a cap on it is an
+ * encode-time choice).  A literal byte has depth 0; the bytes of a match have
+ * depth 1 + the deepest byte of the source window the match reads ([src,
+ * src + min(distance, length)): one period of a self-overlapping match).
+ * Depths saturate at 255.  block_max_depth[d] counts the blocks whose deepest
+ * byte has depth d; match_depth[d] counts the matches of depth d.
+ */
+typedef struct {
+    uint64_t blocks, matches;
+    uint64_t block_max_depth[256];
+    uint64_t match_depth[256];
+} aceapex_enc_stats;
+/* aceapex_encode that also fills *stats (host pointer, may be NULL). */
+int aceapex_encode_ex(const uint8_t* src, uint64_t n, const aceapex_enc_params* params, uint8_t** out,
+                      uint64_t* out_len, aceapex_enc_stats* stats);
+
+/*
  * Open an archive for decoding.  d_arc: device pointer to the archive bytes
  * (caller-owned, must stay valid until aceapex_archive_close).  h_arc: host
  * pointer to the same bytes (read during this call only; the header, index

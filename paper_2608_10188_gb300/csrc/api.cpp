@@ -93,10 +93,23 @@ int aceapex_ctx_set_params(aceapex_ctx* c, const aceapex_dec_params* p) {
 }
 
 int aceapex_encode(const uint8_t* src, uint64_t n, const aceapex_enc_params* p, uint8_t** out, uint64_t* out_len) {
+    return aceapex_encode_ex(src, n, p, out, out_len, nullptr);
+}
+
+int aceapex_encode_ex(const uint8_t* src, uint64_t n, const aceapex_enc_params* p, uint8_t** out, uint64_t* out_len,
+                      aceapex_enc_stats* stats) {
     aceapex_enc_params d{};
     if (p) d = *p;
-    return encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, d.latest_source, d.max_depth,
-                          d.short_latest, d.deps, d.segment, out, out_len);
+    EncDepthStats S;
+    const int rc = encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, d.latest_source, d.max_depth,
+                                  d.short_latest, d.deps, d.segment, out, out_len, stats ? &S : nullptr);
+    if (rc == 0 && stats) {
+        stats->blocks = S.blocks;
+        stats->matches = S.matches;
+        memcpy(stats->block_max_depth, S.block_max_depth, sizeof S.block_max_depth);
+        memcpy(stats->match_depth, S.match_depth, sizeof S.match_depth);
+    }
+    return rc;
 }
 
 void aceapex_free(void* p) { free(p); }

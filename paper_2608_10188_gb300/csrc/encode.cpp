@@ -339,7 +339,7 @@ void parallel_for(uint32_t n, int threads, F fn) {
 
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
                    int latest, uint32_t max_depth, int short_latest, int deps, uint64_t segment, uint8_t** out,
-                   uint64_t* out_len) {
+                   uint64_t* out_len, EncDepthStats* stats) {
     if (segment % kBlock) return -1;
     if (!out || !out_len || (n && !src)) return -1;
     if (min_match == 0) min_match = 4;
@@ -352,6 +352,8 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
     // dependency lists: per block, the ascending ids of the earlier blocks
     // holding bytes that its matches read
     std::vector<uint32_t> dep_ids, dep_off(nb, 0), dep_n(nb, 0);
+    // chain-depth statistics: each block's deepest byte, each segment's match histogram
+    std::vector<uint8_t> blk_depth(stats ? nb : 0, 0);
     try {
         // order-0 literal cost estimate
         uint64_t hist[256] = {0};
@@ -367,6 +369,7 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
         const uint64_t seg = segment ? segment : std::max<uint64_t>(n, 1);
         const uint32_t n_seg = (uint32_t)((n + seg - 1) / seg);
         std::vector<std::vector<uint32_t>> seg_deps(deps ? nb : 0);
+        std::vector<std::vector<uint64_t>> seg_hist(stats ? n_seg : 0);
         std::atomic<int> failed(0);
         auto parse_segment = [&](uint32_t g) {
             try {
@@ -393,6 +396,17 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
                     const uint64_t B = (uint64_t)b * kBlock, E = std::min<uint64_t>(s1, B + kBlock);
                     P.parse_block(B, E, blocks[b], ins);
                 }
+                if (stats) {
+                    for (uint32_t b = b0; b < b1; b++) {
+                        const uint64_t B = (uint64_t)b * kBlock, E = std::min<uint64_t>(s1, B + kBlock);
+                        uint8_t m = 0;
+                        for (uint64_t q = B; q < E; q++) m = std::max(m, P.depth[q - s0]);
+                        blk_depth[b] = m;
+                    }
+                    std::vector<uint64_t>& hh = seg_hist[g];
+                    hh.assign(256, 0);
+                    for (const Parser::Emitted& M : P.emitted) hh[P.depth[M.dst - s0]]++;
+                }
                 if (deps) {
                     std::vector<uint32_t> ids;
                     for (uint32_t b = b0; b < b1; b++) {
@@ -417,6 +431,16 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
         };
         parallel_for(n_seg, std::min<int>(threads, (int)std::max<uint32_t>(n_seg, 1)), parse_segment);
         if (failed) return -3;
+        if (stats) {
+            *stats = EncDepthStats{};
+            stats->blocks = nb;
+            for (uint32_t b = 0; b < nb; b++) stats->block_max_depth[blk_depth[b]]++;
+            for (const std::vector<uint64_t>& hh : seg_hist)
+                for (size_t d = 0; d < hh.size(); d++) {
+                    stats->match_depth[d] += hh[d];
+                    stats->matches += hh[d];
+                }
+        }
         if (deps)
             for (uint32_t b = 0; b < nb; b++) {
                 dep_off[b] = (uint32_t)dep_ids.size();

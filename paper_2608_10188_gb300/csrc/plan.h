@@ -25,9 +25,16 @@ struct Plan {
 int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why);
 
 // Library encoder (format v1); out is malloc'ed.
+// Optional statistics: per-block maximum and per-match chain-depth histograms
+// (see aceapex_enc_stats).
+struct EncDepthStats {
+    uint64_t blocks = 0, matches = 0;
+    uint64_t block_max_depth[256] = {};
+    uint64_t match_depth[256] = {};
+};
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
                    int latest, uint32_t max_depth, int short_latest, int deps, uint64_t segment, uint8_t** out,
-                   uint64_t* out_len);
+                   uint64_t* out_len, EncDepthStats* stats = nullptr);
 
 // FNV-1a 64.
 uint64_t fnv1a64(const uint8_t* p, uint64_t n);

@@ -19,7 +19,7 @@ BLOCK_SIZE = 16384
 
 EXPORTED = [
     "aceapex_status_string", "aceapex_last_error", "aceapex_ctx_create", "aceapex_ctx_destroy",
-    "aceapex_ctx_set_params", "aceapex_encode", "aceapex_free", "aceapex_archive_open", "aceapex_archive_close",
+    "aceapex_ctx_set_params", "aceapex_encode", "aceapex_encode_ex", "aceapex_free", "aceapex_archive_open", "aceapex_archive_close",
     "aceapex_archive_get_info", "aceapex_decode_all", "aceapex_decode_all_async", "aceapex_sync",
     "aceapex_decode_host", "aceapex_archive_check", "aceapex_decode_noalloc", "aceapex_batch_create",
     "aceapex_batch_run_async", "aceapex_batch_wait", "aceapex_batch_run", "aceapex_batch_destroy",
@@ -54,6 +54,15 @@ class ArchiveInfo(ctypes.Structure):
     _fields_ = [("total_size", ctypes.c_uint64), ("n_blocks", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("min_match", ctypes.c_uint32), ("max_tokens", ctypes.c_uint32),
                 ("archive_bytes", ctypes.c_uint64), ("tokens", ctypes.c_uint64)]
+
+
+class EncStats(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.c_uint64), ("matches", ctypes.c_uint64),
+                ("block_max_depth", ctypes.c_uint64 * 256), ("match_depth", ctypes.c_uint64 * 256)]
+
+    def as_dict(self):
+        return {"blocks": self.blocks, "matches": self.matches,
+                "block_max_depth": list(self.block_max_depth), "match_depth": list(self.match_depth)}
 
 
 class ParseStats(ctypes.Structure):
@@ -121,6 +130,7 @@ def load(path: str | None = None):
     L.aceapex_ctx_destroy.argtypes = [vp]
     L.aceapex_ctx_set_params.argtypes = [vp, c.POINTER(DecParams)]
     L.aceapex_encode.argtypes = [vp, u64, c.POINTER(EncParams), c.POINTER(vp), c.POINTER(u64)]
+    L.aceapex_encode_ex.argtypes = [vp, u64, c.POINTER(EncParams), c.POINTER(vp), c.POINTER(u64), c.POINTER(EncStats)]
     L.aceapex_free.argtypes = [vp]
     L.aceapex_free.restype = None
     L.aceapex_archive_open.argtypes = [vp, vp, vp, u64, c.POINTER(vp)]
@@ -173,8 +183,10 @@ def _check(rc, ctx=None, what=""):
 
 def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, threads: int = 0,
            latest_source: bool = False, max_depth: int = 0, short_latest: bool = False, deps: bool = False,
-           segment: int = 0) -> bytes:
-    """aceapex_encode on host bytes (numpy uint8 array or bytes)."""
+           segment: int = 0, stats: dict = None) -> bytes:
+    """aceapex_encode on host bytes (numpy uint8 array or bytes).  With a
+    dict `stats`, aceapex_encode_ex fills it with the chain-depth statistics
+    (see aceapex_enc_stats)."""
     import numpy as np
     L = load()
     a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data,
@@ -183,8 +195,11 @@ def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, 
                   int(deps), segment)
     ptr = ctypes.c_void_p()
     n = ctypes.c_uint64()
-    _check(L.aceapex_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(p), ctypes.byref(ptr),
-                            ctypes.byref(n)), None, "encode")
+    st = EncStats()
+    _check(L.aceapex_encode_ex(a.ctypes.data if a.size else None, a.size, ctypes.byref(p), ctypes.byref(ptr),
+                               ctypes.byref(n), ctypes.byref(st) if stats is not None else None), None, "encode")
+    if stats is not None:
+        stats.update(st.as_dict())
     try:
         if n.value < (1 << 31):
             return ctypes.string_at(ptr.value, n.value)

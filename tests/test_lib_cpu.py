@@ -272,3 +272,34 @@ def test_parse_stats_counting_equals_oracle_counts(acx, kind, no_rep):
     if no_rep:
         # no repeat codes: one run per block, the block's token count
         assert got["runs"] == nb and got["median_run"] == int(np.sort(ntok)[nb // 2])
+
+
+@pytest.mark.parametrize("kind,max_depth", [("dna", 0), ("dna", 0xFFFFFFFF), ("text", 0), ("text", 4)])
+def test_encoder_depth_statistics_follow_the_archive(acx, kind, max_depth):
+    """aceapex_encode_ex's chain-depth histograms (paper, Depth Does Not
+    Govern Latency) equal the depths recomputed from the archive alone: each
+    match, in output order, gets 1 + the deepest byte of the source window it
+    reads (one period of a self-overlapping match), literals depth 0.  With a
+    cap, no match is deeper than the cap."""
+    data = synth.corpus(kind, (1 << 20) + 4321, 11)
+    st = {}
+    arc = acx.encode(data, max_depth=max_depth, stats=st)
+    nb = (data.size + BLOCK - 1) // BLOCK
+    D = np.zeros(data.size, np.int64)
+    match_hist = np.zeros(256, np.int64)
+    for b in range(nb):
+        t = oracle.parse_block(arc, b)
+        for dst, src, ml in zip(t["dst"].tolist(), t["src"].tolist(), t["ml"].tolist()):
+            if not ml:
+                continue
+            w = min(dst - src, ml)
+            dep = min(1 + int(D[src:src + w].max()), 255)
+            D[dst:dst + ml] = dep
+            match_hist[dep] += 1
+    blk = np.array([D[b * BLOCK:(b + 1) * BLOCK].max() for b in range(nb)])
+    assert st["blocks"] == nb and st["matches"] == int(match_hist.sum())
+    assert st["match_depth"] == match_hist.tolist()
+    assert st["block_max_depth"] == np.bincount(blk, minlength=256).tolist()
+    cap = 16 if max_depth == 0 else max_depth
+    if cap < 255:
+        assert max(d for d in range(256) if st["match_depth"][d]) <= cap
