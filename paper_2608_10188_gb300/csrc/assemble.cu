@@ -13,7 +13,8 @@
 //     maps compose associatively, so the history before every token is a
 //     prefix "sum" too.  Skipped when a block has no repeat code (history-
 //     free encoding, where the parse is a dependency-free prefix scan).
-//   * literals are placed with 4-byte funnel-shifted copies, one warp per run.
+//   * literals: runs of up to 32 bytes are copied by one thread each, all
+//     threads at once; longer runs by a warp with 4-byte funnel-shifted copies.
 //   * matches whose source lies inside the block are periodic fills
 //     out[dst+k] = out[src + (k mod d)] ("What Does: Periods, Not Chains"),
 //     done in rounds as their sources become final; matches whose source
@@ -24,7 +25,10 @@
 //   after the kernel boundary every literal and every in-block match byte is
 //   final, so a pending span waits only on the spans its source really
 //   depends on, which lie at lower positions and were taken earlier: the
-//   ascending order makes the bounded waits deadlock-free.
+//   ascending order makes the bounded waits deadlock-free.  Spans that wait
+//   too long (many pieces, long chains) go to work lists, staged per warp in
+//   shared memory; barrier-separated rounds walk the lists until they are
+//   empty, each round finishing at least the lowest span.
 #include <algorithm>
 
 #include "common.cuh"
@@ -657,11 +661,12 @@ __device__ __forceinline__ bool piece_final(const ArcJob& L, uint64_t src, uint3
 }
 
 // A warp's attempt at its lanes' pieces (lane `has` a piece `rec` of the
-// block in output slot `dslot`, all of archive L).  Each lane checks its own piece; the ready pieces
-// are then copied by the whole warp, lane i moving byte i (one coalesced
-// request per piece), eight pieces' loads in flight before their stores;
-// after one fence the owners clear the pieces' pending bits with release
-// reductions.  Returns true on the lanes whose piece is done.
+// block in output slot `dslot`, all of archive L).  Each lane checks its own
+// piece; the ready pieces are then copied by the whole warp, lane i moving
+// byte i (one coalesced request per piece), eight pieces' loads in flight
+// before their stores; after one fence (the release) the owners clear the
+// pieces' pending bits with relaxed atomic ANDs.  Returns true on the lanes
+// whose piece is done.
 constexpr int kCopyBatch = 8;
 __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec rec, SpanRec* wrec, uint64_t* wdst,
                            int lane) {
