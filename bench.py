@@ -609,6 +609,8 @@ def run_depth(args):
     enc_s = time.perf_counter() - t
     bm = np.array(st["block_max_depth"], np.int64)
     md = np.array(st["match_depth"], np.int64)
+    ml = np.array(st["match_level"], np.int64)
+    lb = np.array(st["level_bytes"], np.int64)
 
     def rank(h, q):  # the element of rank floor(q * (count - 1)) of the sorted values
         c = np.cumsum(h)
@@ -625,6 +627,11 @@ def run_depth(args):
         "match_depth": {"median": rank(md, 0.5), "p99": rank(md, 0.99), "max": int(np.nonzero(md)[0].max()),
                         "share_depth_1": round(float(md[1] / max(md.sum(), 1)), 4),
                         "mean": round(float((md * np.arange(256)).sum() / max(md.sum(), 1)), 3)},
+        # cross-block levels: level 0 is finished by the local pass; a pass
+        # taking the levels in order needs one round per level above 0
+        "cross_block_level": {"max": int(np.nonzero(ml)[0].max()) if ml.any() else 0,
+                              "matches": {str(l): int(ml[l]) for l in np.nonzero(ml)[0]},
+                              "bytes": {str(l): int(lb[l]) for l in np.nonzero(lb)[0]}},
     }
     print(json.dumps(line), flush=True)
 

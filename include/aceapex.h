@@ -162,6 +162,15 @@ typedef struct {
     uint64_t blocks, matches;
     uint64_t block_max_depth[256];
     uint64_t match_depth[256];
+    /* Cross-block levels: a match whose source window lies in its own block and
+     * holds only level-0 bytes is finished by the decoder's local pass (level
+     * 0); any other match has level 1 + the highest level in its window.
+     * match_level[l] / level_bytes[l]: matches of level l and their bytes.  A
+     * cross-block pass that took the levels in order would finish every match
+     * of level l in its l-th round, so the highest level is the number of such
+     * rounds (paper, "Depth Does Not Govern Latency": waves). */
+    uint64_t match_level[256];
+    uint64_t level_bytes[256];
 } aceapex_enc_stats;
 /* aceapex_encode that also fills *stats (host pointer, may be NULL). */
 int aceapex_encode_ex(const uint8_t* src, uint64_t n, const aceapex_enc_params* params, uint8_t** out,

@@ -108,6 +108,8 @@ int aceapex_encode_ex(const uint8_t* src, uint64_t n, const aceapex_enc_params* 
         stats->matches = S.matches;
         memcpy(stats->block_max_depth, S.block_max_depth, sizeof S.block_max_depth);
         memcpy(stats->match_depth, S.match_depth, sizeof S.match_depth);
+        memcpy(stats->match_level, S.match_level, sizeof S.match_level);
+        memcpy(stats->level_bytes, S.level_bytes, sizeof S.level_bytes);
     }
     return rc;
 }

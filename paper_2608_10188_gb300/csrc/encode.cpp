@@ -369,7 +369,7 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
         const uint64_t seg = segment ? segment : std::max<uint64_t>(n, 1);
         const uint32_t n_seg = (uint32_t)((n + seg - 1) / seg);
         std::vector<std::vector<uint32_t>> seg_deps(deps ? nb : 0);
-        std::vector<std::vector<uint64_t>> seg_hist(stats ? n_seg : 0);
+        std::vector<std::vector<uint64_t>> seg_hist(stats ? n_seg : 0);  // per segment: 3 x 256 counts
         std::atomic<int> failed(0);
         auto parse_segment = [&](uint32_t g) {
             try {
@@ -404,8 +404,19 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
                         blk_depth[b] = m;
                     }
                     std::vector<uint64_t>& hh = seg_hist[g];
-                    hh.assign(256, 0);
+                    hh.assign(3 * 256, 0);
                     for (const Parser::Emitted& M : P.emitted) hh[P.depth[M.dst - s0]]++;
+                    // cross-block levels, matches in output order
+                    std::vector<uint8_t> lvl(s1 - s0, 0);
+                    for (const Parser::Emitted& M : P.emitted) {
+                        const uint64_t B = M.dst / kBlock * kBlock, d = M.dst - M.src, w = d < M.len ? d : M.len;
+                        uint32_t mx = 0;
+                        for (uint64_t q = M.src; q < M.src + w; q++) mx = std::max<uint32_t>(mx, lvl[q - s0]);
+                        const uint32_t l = (M.src >= B && mx == 0) ? 0 : std::min<uint32_t>(mx + 1, 255);
+                        memset(&lvl[M.dst - s0], (int)l, M.len);
+                        hh[256 + l]++;
+                        hh[512 + l] += M.len;
+                    }
                 }
                 if (deps) {
                     std::vector<uint32_t> ids;
@@ -436,9 +447,11 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
             stats->blocks = nb;
             for (uint32_t b = 0; b < nb; b++) stats->block_max_depth[blk_depth[b]]++;
             for (const std::vector<uint64_t>& hh : seg_hist)
-                for (size_t d = 0; d < hh.size(); d++) {
+                for (size_t d = 0; d < 256 && d < hh.size(); d++) {
                     stats->match_depth[d] += hh[d];
                     stats->matches += hh[d];
+                    stats->match_level[d] += hh[256 + d];
+                    stats->level_bytes[d] += hh[512 + d];
                 }
         }
         if (deps)

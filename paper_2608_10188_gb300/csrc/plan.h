@@ -31,6 +31,8 @@ struct EncDepthStats {
     uint64_t blocks = 0, matches = 0;
     uint64_t block_max_depth[256] = {};
     uint64_t match_depth[256] = {};
+    uint64_t match_level[256] = {};
+    uint64_t level_bytes[256] = {};
 };
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
                    int latest, uint32_t max_depth, int short_latest, int deps, uint64_t segment, uint8_t** out,

@@ -58,11 +58,13 @@ class ArchiveInfo(ctypes.Structure):
 
 class EncStats(ctypes.Structure):
     _fields_ = [("blocks", ctypes.c_uint64), ("matches", ctypes.c_uint64),
-                ("block_max_depth", ctypes.c_uint64 * 256), ("match_depth", ctypes.c_uint64 * 256)]
+                ("block_max_depth", ctypes.c_uint64 * 256), ("match_depth", ctypes.c_uint64 * 256),
+                ("match_level", ctypes.c_uint64 * 256), ("level_bytes", ctypes.c_uint64 * 256)]
 
     def as_dict(self):
         return {"blocks": self.blocks, "matches": self.matches,
-                "block_max_depth": list(self.block_max_depth), "match_depth": list(self.match_depth)}
+                "block_max_depth": list(self.block_max_depth), "match_depth": list(self.match_depth),
+                "match_level": list(self.match_level), "level_bytes": list(self.level_bytes)}
 
 
 class ParseStats(ctypes.Structure):

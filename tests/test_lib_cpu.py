@@ -303,3 +303,31 @@ def test_encoder_depth_statistics_follow_the_archive(acx, kind, max_depth):
     cap = 16 if max_depth == 0 else max_depth
     if cap < 255:
         assert max(d for d in range(256) if st["match_depth"][d]) <= cap
+
+
+@pytest.mark.parametrize("kind,max_depth", [("dna", 0), ("text", 0), ("text", 4)])
+def test_encoder_level_statistics_follow_the_archive(acx, kind, max_depth):
+    """The cross-block levels of aceapex_encode_ex, recomputed from the
+    archive alone: in output order, a match whose source window lies in its
+    own block and holds only level-0 bytes gets level 0 (the local pass
+    finishes it); any other match gets 1 + the highest level in its window."""
+    data = synth.corpus(kind, (1 << 20) + 999, 12)
+    st = {}
+    arc = acx.encode(data, max_depth=max_depth, stats=st)
+    nb = (data.size + BLOCK - 1) // BLOCK
+    lv = np.zeros(data.size, np.int64)
+    count, nbytes = np.zeros(256, np.int64), np.zeros(256, np.int64)
+    for b in range(nb):
+        t = oracle.parse_block(arc, b)
+        for dst, src, ml in zip(t["dst"].tolist(), t["src"].tolist(), t["ml"].tolist()):
+            if not ml:
+                continue
+            mx = int(lv[src:src + min(dst - src, ml)].max())
+            level = 0 if (src >= b * BLOCK and mx == 0) else min(mx + 1, 255)
+            lv[dst:dst + ml] = level
+            count[level] += 1
+            nbytes[level] += ml
+    assert st["match_level"] == count.tolist()
+    assert st["level_bytes"] == nbytes.tolist()
+    # a match's level never exceeds its chain depth
+    assert max(l for l in range(256) if count[l]) <= max(d for d in range(256) if st["match_depth"][d])
