@@ -50,6 +50,7 @@ int aceapex_ctx_create(int device, const aceapex_dec_params* params, aceapex_ctx
         aceapex_ctx_destroy(c);
         return ACEAPEX_E_CUDA;
     }
+    note_sm_count(c->n_sms);
     for (auto& ev : c->ev) {
         if (cudaEventCreate(&ev) != cudaSuccess) {
             aceapex_ctx_destroy(c);

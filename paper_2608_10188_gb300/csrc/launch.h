@@ -22,8 +22,11 @@ size_t local_smem_bytes(uint32_t T, uint32_t LB, bool need = false);
 int rans_occupancy();
 // Grid of a persistent kernel for a job that can use `need` CTAs at most:
 // no more than `full`, and no fewer than one per SM, so that a mid-size job
-// spreads its warps over the whole GPU instead of packing a few SMs.
+// spreads its warps over the whole GPU instead of packing a few SMs.  The SM
+// count is recorded when a context is created (no API call at launch time,
+// which may be inside a graph capture).
 int job_grid(int full, uint64_t need);
+void note_sm_count(int n_sms);
 int local_occupancy(size_t smem);
 int external_occupancy();
 int plain_occupancy();

@@ -264,6 +264,7 @@ extern "C" int aceapex_decode_noalloc(const void* d_arc, uint64_t arc_len, void*
     job.lists[1] = job.lists[0] + kNaSpanSlots;
     int n_sms = 0;
     if (cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ACEAPEX_E_CUDA;
+    note_sm_count(n_sms);
     // the array keeps the previous call's contents: clear the error word; the
     // prologue kernel clears the tickets and statistics
     if (cudaMemsetAsync(job.err, 0, 16, st) != cudaSuccess) return ACEAPEX_E_CUDA;

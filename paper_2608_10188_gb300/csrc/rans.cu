@@ -17,6 +17,7 @@
 //  * ring residency is checked once per 4 steps, not per step.
 // Every wait is bounded by %globaltimer.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "launch.h"
@@ -401,10 +402,13 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
 
 size_t rans_smem_bytes() { return sizeof(RansSmem); }
 
+static std::atomic<int> g_sm_count{0};
+
+void note_sm_count(int n_sms) { g_sm_count.store(n_sms); }
+
 int job_grid(int full, uint64_t need) {
-    int dev = 0, n_sms = 1;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t g = std::max<uint64_t>(need, (uint64_t)std::max(n_sms, 1));
+    const int n_sms = std::max(g_sm_count.load(), 1);
+    const uint64_t g = std::max<uint64_t>(need, (uint64_t)n_sms);
     return (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)full, g));
 }
 
