@@ -825,6 +825,16 @@ TRAFFIC = {
 }
 
 
+# Issue (ALU) ceiling of the entropy stage, which ncu shows issue-bound:
+# warp-instructions per decoded symbol from the same --set full capture
+# (94,815,686 warp-instructions for the 57,972,156 symbols of that 64 MiB
+# genome; the full genome has the same symbol mix), against one
+# warp-instruction per cycle on each of the 4 schedulers of the 152 SMs at
+# the 2070 MHz maximum clock.
+RANS_INSTR_PER_SYMBOL = 94_815_686 / 57_972_156
+ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions per second
+
+
 def rooflines(stage, pb, size, arc_len, st, n_blocks, variant, ms_step, wname=""):
     """HBM roofline of each decode kernel from its algorithmic bytes per launch
     over its CUDA-event time, the dominant (slowest) kernel first, and of the
@@ -846,6 +856,12 @@ def rooflines(stage, pb, size, arc_len, st, n_blocks, variant, ms_step, wname=""
                "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1) if ms > 0 else None,
                "frac": round(b / (ms / 1e3) / 1e9 / peak, 4) if ms > 0 else None,
                "traffic": TRAFFIC.get((wname, k))} for k, (ms, b) in kern.items()}
+    if wname and stage["ans"] > 0:
+        instr = RANS_INSTR_PER_SYMBOL * pb["decoded"]
+        rate = instr / (stage["ans"] / 1e3)
+        per["k_rans"]["alu"] = {"bound": "alu", "instructions": int(instr), "achieved": round(rate / 1e12, 4),
+                                "peak": round(ISSUE_PEAK / 1e12, 4), "unit": "T warp-instr/s",
+                                "frac": round(rate / ISSUE_PEAK, 4)}
     dom = max(kern, key=lambda k: kern[k][0])
     ms, b = kern[dom]
     achieved = b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
