@@ -335,3 +335,44 @@ def test_self_overlap_reads_one_period_across_a_block_boundary():
         full.append(full[16384 - 4 + j])
     assert oracle.decode(build_archive(blocks, deps=[[], [0]]), verify=False).tobytes() == bytes(full)
     assert oracle.decode_status(build_archive(blocks, deps=[[], []]), verify=False)[0] == oracle.E_CORRUPT
+
+
+def test_archive_statistics_of_a_hand_built_archive():
+    """The oracle's archive statistics (the reference of the parse-statistics
+    parity tests; paper, The Last Sequential Element) on a two-block archive
+    whose every count is worked out by hand.  History starts [1,2,3,4]; NEW
+    pushes its distance, REPk moves entry k to the front.
+
+    Block 0 (16,384 B):
+      t0 NEW  LL 4    ML 4    src 0     d 4    hist [4,1,2,3]
+      t1 REP0 LL 0    ML 8              d 4    overlapping
+      t2 NEW  LL 200  ML 5    src 0     d 216  hist [216,4,1,2]; LL takes 2 bytes
+      t3 REP1 LL 0    ML 6              d 4    overlapping; hist [4,216,1,2]
+      t4 NEW  LL 0    ML 300  src 10    d 217  overlapping; ML takes 2 bytes
+      t5 LIT  LL 15857                         LL takes 2 bytes
+      runs (non-repeat tokens before each repeat, then the tail): 1, 1, 2
+    Block 1 (17 B):
+      t0 NEW  LL 0    ML 10   src 100   (in block 0: external)
+      t1 NEW  LL 2    ML 4    src 16384 d 12
+      t2 LIT  LL 1
+      runs: 3
+    """
+    lit = lambda n, c=b"a": (c * n)[:n]  # noqa: E731
+    blk0 = [{"cmd": 0, "lits": b"ABCD", "ml": 4, "src": 0},
+            {"cmd": 1, "lits": b"", "ml": 8},
+            {"cmd": 0, "lits": lit(200), "ml": 5, "src": 0},
+            {"cmd": 2, "lits": b"", "ml": 6},
+            {"cmd": 0, "lits": b"", "ml": 300, "src": 10},
+            {"cmd": 5, "lits": lit(15857, b"q"), "ml": 0}]
+    blk1 = [{"cmd": 0, "lits": b"", "ml": 10, "src": 100},
+            {"cmd": 0, "lits": b"xy", "ml": 4, "src": 16384},
+            {"cmd": 5, "lits": b"z", "ml": 0}]
+    arc = build_archive([blk0, blk1])
+    st = oracle.stats(arc)
+    want = {"n_blocks": 2, "n_tokens": 9, "n_new": 5, "n_rep": [1, 1, 0, 0], "n_litonly": 2, "n_values": 18,
+            "n_multibyte_values": 3, "n_match_bytes": 337, "n_literal_bytes": 16064, "n_overlap_tokens": 3,
+            "n_external_tokens": 1, "max_tokens_block": 6, "hist_dependent": 2, "runs": 4, "run_len_sum": 7,
+            "median_run": 2}
+    for k, v in want.items():
+        assert st[k] == v, (k, st[k], v)
+    assert oracle.decode(arc, verify=False).size == 16384 + 17
