@@ -83,6 +83,11 @@ typedef struct {
                             16 KiB: the input is parsed as independent segments of this size
                             (sources stay inside their segment, like a genome's chromosomes),
                             in parallel on `threads` threads, into one archive */
+    int levels;          /* 1: write each block's level body (flags bit1): one byte per token, its
+                            cross-block level (see aceapex_enc_stats), a scheduling hint for a
+                            cross-block pass that takes the levels in order (paper, "Depth Does
+                            Not Govern Latency": waves).  Decoders may ignore it; it never changes
+                            the decoded bytes.  0 (default): no level bodies */
 } aceapex_enc_params;
 
 /* Decoder variants. */

@@ -100,6 +100,8 @@ def _load():
         L.orc_parse_block.restype = c.c_int64
         L.orc_block_stream.argtypes = [c.c_void_p, c.c_uint64, c.c_uint32, c.c_int, c.c_void_p, c.c_uint64]
         L.orc_block_stream.restype = c.c_int64
+        L.orc_block_levels.argtypes = [c.c_void_p, c.c_uint64, c.c_uint32, c.c_void_p, c.c_uint64]
+        L.orc_block_levels.restype = c.c_int64
         L.orc_archive_stats.argtypes = [c.c_void_p, c.c_uint64, c.POINTER(Stats)]
         L.orc_archive_stats.restype = c.c_int
         _lib = L
@@ -219,6 +221,17 @@ def block_stream(arc, b: int, which: int) -> np.ndarray:
     n = _load().orc_block_stream(a.ctypes.data, a.size, b, which, out.ctypes.data, cap)
     if n < 0:
         raise OracleError(n, "block_stream")
+    return out[:n]
+
+
+def block_levels(arc, b: int) -> np.ndarray:
+    """The level body of block b (archives whose flags have bit1 set)."""
+    a = _u8(arc)
+    cap = 4 * BLOCK + 16
+    out = np.zeros(cap, np.uint8)
+    n = _load().orc_block_levels(a.ctypes.data, a.size, b, out.ctypes.data, cap)
+    if n < 0:
+        raise OracleError(n, "block_levels")
     return out[:n]
 
 

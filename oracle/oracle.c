@@ -5,7 +5,8 @@
  *
  * Layout of an archive (all integers little-endian):
  *   header   64 B   "ACX1", u16 version=1, u16 flags (bit0: history-free
- *                   encoding, informational), u32 block_size=16384,
+ *                   encoding, informational; bit1: every payload carries
+ *                   a level body), u32 block_size=16384,
  *                   u32 min_match, u64 total, u32 n_blocks, u32 0,
  *                   u64 off_tables, u64 off_index, u64 off_deps (0 = none),
  *                   u64 off_payload
@@ -19,8 +20,13 @@
  *   payload  per block, 16-aligned: 4 descriptors of 12 B (u32 raw_len,
  *            u32 enc_len, u8 mode (0 stored, 1 rANS), u8 K, u16 0) in the
  *            order cmd, len, off, lit, then the 4 bodies, each starting on a
- *            16-byte boundary; payload_len = end of the last body rounded up
- *            to 16.
+ *            16-byte boundary; with flags bit1 a fifth, stored body of
+ *            n_tokens bytes follows at the next 16-byte boundary: each
+ *            token's cross-block level (a scheduling hint for decoders that
+ *            take cross-block copies level by level, the paper's waves;
+ *            "Depth Does Not Govern Latency"; it never changes the decoded
+ *            bytes and is not checked); payload_len = end of the last body
+ *            rounded up to 16.
  *
  * Streams of a block with n tokens (paper, Setup: literals, lengths,
  * absolute offsets, commands):
@@ -510,6 +516,7 @@ typedef struct {
     uint8_t* s[4];      /* decoded streams (malloc'ed) */
     uint32_t n[4];      /* their lengths */
     uint64_t enc[4];
+    uint64_t lvl_off;   /* payload offset of the level body (flags bit1), else 0 */
 } dblk_t;
 
 static void dblk_free(dblk_t* d) {
@@ -566,6 +573,11 @@ static int block_streams(const arc_t* A, uint32_t b, dblk_t* d) {
             return ORC_E_CORRUPT;
         }
         off = pad16(off + enc);
+    }
+    if (A->flags & 2) {  /* the level body: n_tok stored bytes */
+        if (off + d->n_tok > d->payload_len) return ORC_E_CORRUPT;
+        d->lvl_off = off;
+        off = pad16(off + d->n_tok);
     }
     if (off != d->payload_len) return ORC_E_CORRUPT;
     if (d->n[ORC_CMD] != d->n_tok) return ORC_E_CORRUPT;
@@ -715,6 +727,22 @@ int64_t orc_block_stream(const uint8_t* arc, uint64_t arc_len, uint32_t b, int w
     if (rc == ORC_OK) {
         if ((uint64_t)n > cap) rc = ORC_E_ARG;
         else if (n) memcpy(out, d.s[which], (size_t)n);
+    }
+    dblk_free(&d);
+    return rc ? rc : n;
+}
+
+int64_t orc_block_levels(const uint8_t* arc, uint64_t arc_len, uint32_t b, uint8_t* out, uint64_t cap) {
+    arc_t A;
+    int rc = arc_open(arc, arc_len, &A);
+    if (rc) return rc;
+    if (b >= A.nb || !(A.flags & 2)) return ORC_E_ARG;
+    dblk_t d;
+    rc = block_streams(&A, b, &d);
+    int64_t n = d.n_tok;
+    if (rc == ORC_OK) {
+        if ((uint64_t)n > cap) rc = ORC_E_ARG;
+        else if (n) memcpy(out, A.a + d.payload_off + d.lvl_off, (size_t)n);
     }
     dblk_free(&d);
     return rc ? rc : n;

@@ -86,6 +86,11 @@ int64_t orc_parse_block(const uint8_t* arc, uint64_t arc_len, uint32_t b, uint64
 /* Decoded (pre-parse) stream of one block: which = ORC_CMD..ORC_LIT. */
 int64_t orc_block_stream(const uint8_t* arc, uint64_t arc_len, uint32_t b, int which, uint8_t* out, uint64_t cap);
 
+/* The level body of one block (archives with flags bit1): one byte per token,
+ * returned as stored (hints, not checked).  ORC_E_ARG when the archive has
+ * none. */
+int64_t orc_block_levels(const uint8_t* arc, uint64_t arc_len, uint32_t b, uint8_t* out, uint64_t cap);
+
 typedef struct {
     uint64_t n_blocks, n_tokens, n_new, n_rep[4], n_litonly;
     uint64_t n_values, n_multibyte_values;  /* varint values, and those longer than one byte */

@@ -103,7 +103,7 @@ int aceapex_encode_ex(const uint8_t* src, uint64_t n, const aceapex_enc_params* 
     if (p) d = *p;
     EncDepthStats S;
     const int rc = encode_archive(src, n, d.no_rep, d.min_match, d.max_lanes, d.threads, d.latest_source, d.max_depth,
-                                  d.short_latest, d.deps, d.segment, out, out_len, stats ? &S : nullptr);
+                                  d.short_latest, d.deps, d.segment, d.levels, out, out_len, stats ? &S : nullptr);
     if (rc == 0 && stats) {
         stats->blocks = S.blocks;
         stats->matches = S.matches;

@@ -48,6 +48,7 @@ constexpr uint32_t kDefaultMaxDepth = 16;
 
 struct BlockStreams {
     std::vector<uint8_t> s[4];
+    std::vector<uint8_t> lvl;  // per token: its cross-block level (archives with level bodies)
 };
 
 inline uint64_t load64(const uint8_t* p) {
@@ -338,8 +339,8 @@ void parallel_for(uint32_t n, int threads, F fn) {
 }  // namespace
 
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   int latest, uint32_t max_depth, int short_latest, int deps, uint64_t segment, uint8_t** out,
-                   uint64_t* out_len, EncDepthStats* stats) {
+                   int latest, uint32_t max_depth, int short_latest, int deps, uint64_t segment, int levels,
+                   uint8_t** out, uint64_t* out_len, EncDepthStats* stats) {
     if (segment % kBlock) return -1;
     if (!out || !out_len || (n && !src)) return -1;
     if (min_match == 0) min_match = 4;
@@ -396,6 +397,35 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
                     const uint64_t B = (uint64_t)b * kBlock, E = std::min<uint64_t>(s1, B + kBlock);
                     P.parse_block(B, E, blocks[b], ins);
                 }
+                // cross-block levels, matches in output order: a match whose
+                // source window lies in its own block and holds only level-0
+                // bytes is finished by the decoder's local pass (level 0);
+                // any other match has 1 + the highest level in its window
+                std::vector<uint8_t> mlev;  // per emitted match
+                if (stats || levels) {
+                    std::vector<uint8_t> lvl(s1 - s0, 0);
+                    mlev.resize(P.emitted.size());
+                    for (size_t m = 0; m < P.emitted.size(); m++) {
+                        const Parser::Emitted& M = P.emitted[m];
+                        const uint64_t B = M.dst / kBlock * kBlock, d = M.dst - M.src, w = d < M.len ? d : M.len;
+                        uint32_t mx = 0;
+                        for (uint64_t q = M.src; q < M.src + w; q++) mx = std::max<uint32_t>(mx, lvl[q - s0]);
+                        const uint32_t l = (M.src >= B && mx == 0) ? 0 : std::min<uint32_t>(mx + 1, 255);
+                        memset(&lvl[M.dst - s0], (int)l, M.len);
+                        mlev[m] = (uint8_t)l;
+                    }
+                }
+                if (levels) {
+                    // one level byte per token: the block's matches in order,
+                    // then 0 for a closing literal-only token
+                    for (uint32_t b = b0; b < b1; b++) {
+                        const uint64_t lo = P.block_first[b - b0];
+                        const uint64_t hi = b + 1 < b1 ? P.block_first[b + 1 - b0] : P.emitted.size();
+                        std::vector<uint8_t>& L = blocks[b].lvl;
+                        L.assign(mlev.begin() + lo, mlev.begin() + hi);
+                        L.resize(blocks[b].s[kCmd].size(), 0);
+                    }
+                }
                 if (stats) {
                     for (uint32_t b = b0; b < b1; b++) {
                         const uint64_t B = (uint64_t)b * kBlock, E = std::min<uint64_t>(s1, B + kBlock);
@@ -405,17 +435,11 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
                     }
                     std::vector<uint64_t>& hh = seg_hist[g];
                     hh.assign(3 * 256, 0);
-                    for (const Parser::Emitted& M : P.emitted) hh[P.depth[M.dst - s0]]++;
-                    // cross-block levels, matches in output order
-                    std::vector<uint8_t> lvl(s1 - s0, 0);
-                    for (const Parser::Emitted& M : P.emitted) {
-                        const uint64_t B = M.dst / kBlock * kBlock, d = M.dst - M.src, w = d < M.len ? d : M.len;
-                        uint32_t mx = 0;
-                        for (uint64_t q = M.src; q < M.src + w; q++) mx = std::max<uint32_t>(mx, lvl[q - s0]);
-                        const uint32_t l = (M.src >= B && mx == 0) ? 0 : std::min<uint32_t>(mx + 1, 255);
-                        memset(&lvl[M.dst - s0], (int)l, M.len);
-                        hh[256 + l]++;
-                        hh[512 + l] += M.len;
+                    for (size_t m = 0; m < P.emitted.size(); m++) {
+                        const Parser::Emitted& M = P.emitted[m];
+                        hh[P.depth[M.dst - s0]]++;
+                        hh[256 + mlev[m]]++;
+                        hh[512 + mlev[m]] += M.len;
                     }
                 }
                 if (deps) {
@@ -519,6 +543,10 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
             P.insert(P.end(), body.begin(), body.end());
             P.resize((P.size() + 15) & ~(size_t)15, 0);
         }
+        if (levels) {  // the level body, stored, after the four stream bodies
+            P.insert(P.end(), blocks[b].lvl.begin(), blocks[b].lvl.end());
+            P.resize((P.size() + 15) & ~(size_t)15, 0);
+        }
         blocks[b] = BlockStreams();
     });
     const uint64_t off_tab = 64, off_idx = 64 + 2048;
@@ -533,7 +561,7 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
     uint8_t* a = (uint8_t*)calloc(total ? total : 1, 1);
     if (!a) return -3;
     memcpy(a, "ACX1", 4);
-    const uint16_t ver = 1, flags = no_rep ? 1 : 0;
+    const uint16_t ver = 1, flags = (uint16_t)((no_rep ? 1 : 0) | (levels ? kFlagLevels : 0));
     const uint32_t bs = kBlock;
     memcpy(a + 4, &ver, 2);
     memcpy(a + 6, &flags, 2);

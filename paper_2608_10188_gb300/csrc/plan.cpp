@@ -61,6 +61,8 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why) {
     }
     P->blk.assign(P->n_blocks, BlockDev{});
     P->has_deps = off_deps != 0;
+    const bool has_levels = (P->flags & kFlagLevels) != 0;
+    P->lvl_off.assign(has_levels ? P->n_blocks : 0, 0);
     P->deps.clear();
     P->max_tok = 1;
     P->max_lenb = 1;
@@ -120,6 +122,11 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why) {
             bd.s_off[s] = (uint32_t)soff;
             soff = up16(soff + sraw);
             off = up16(off + enc);
+        }
+        if (has_levels) {  // the level body: n_tok stored bytes after the four stream bodies
+            if (off + n_tok > plen) return fail("level body out of bounds");
+            P->lvl_off[b] = (uint32_t)off;
+            off = up16(off + n_tok);
         }
         if (off != plen) return fail("payload length mismatch");
         if (bd.s_raw[kCmd] != n_tok) return fail("token count mismatch");

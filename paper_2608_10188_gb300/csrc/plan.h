@@ -18,7 +18,11 @@ struct Plan {
     std::vector<BlockDev> blk;
     bool has_deps = false;        // the archive carries dependency lists
     std::vector<uint32_t> deps;   // all lists, block b's at [blk[b].dep_off, + blk[b].n_deps)
+    // Level bodies (flags bit1: one cross-block level per token, a scheduling
+    // hint): block b's at payload offset lvl_off[b]; empty without them.
+    std::vector<uint32_t> lvl_off;
 };
+constexpr uint32_t kFlagLevels = 2;
 
 // Validate the archive structure and build its plan.  Returns 0 or -2
 // (corrupt) with a reason in *why.
@@ -35,8 +39,8 @@ struct EncDepthStats {
     uint64_t level_bytes[256] = {};
 };
 int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_match, uint32_t max_lanes, int threads,
-                   int latest, uint32_t max_depth, int short_latest, int deps, uint64_t segment, uint8_t** out,
-                   uint64_t* out_len, EncDepthStats* stats = nullptr);
+                   int latest, uint32_t max_depth, int short_latest, int deps, uint64_t segment, int levels,
+                   uint8_t** out, uint64_t* out_len, EncDepthStats* stats = nullptr);
 
 // FNV-1a 64.
 uint64_t fnv1a64(const uint8_t* p, uint64_t n);

@@ -35,7 +35,7 @@ class EncParams(ctypes.Structure):
     _fields_ = [("no_rep", ctypes.c_int), ("min_match", ctypes.c_uint32), ("max_lanes", ctypes.c_uint32),
                 ("threads", ctypes.c_int), ("latest_source", ctypes.c_int),
                 ("max_depth", ctypes.c_uint32), ("short_latest", ctypes.c_int), ("deps", ctypes.c_int),
-                ("segment", ctypes.c_uint64)]
+                ("segment", ctypes.c_uint64), ("levels", ctypes.c_int)]
 
 
 class DecParams(ctypes.Structure):
@@ -185,7 +185,7 @@ def _check(rc, ctx=None, what=""):
 
 def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, threads: int = 0,
            latest_source: bool = False, max_depth: int = 0, short_latest: bool = False, deps: bool = False,
-           segment: int = 0, stats: dict = None) -> bytes:
+           segment: int = 0, stats: dict = None, levels: bool = False) -> bytes:
     """aceapex_encode on host bytes (numpy uint8 array or bytes).  With a
     dict `stats`, aceapex_encode_ex fills it with the chain-depth statistics
     (see aceapex_enc_stats)."""
@@ -194,7 +194,7 @@ def encode(data, no_rep: bool = False, min_match: int = 4, max_lanes: int = 32, 
     a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data,
                              dtype=np.uint8)
     p = EncParams(int(no_rep), min_match, max_lanes, threads, int(latest_source), max_depth, int(short_latest),
-                  int(deps), segment)
+                  int(deps), segment, int(levels))
     ptr = ctypes.c_void_p()
     n = ctypes.c_uint64()
     st = EncStats()

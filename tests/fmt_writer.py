@@ -44,12 +44,14 @@ def pad16(n: int) -> int:
 
 
 def build_archive(blocks, *, min_match=4, flags=0, expected=None, fnv=None, raw_streams=None,
-                  raw_lens=None, total=None, tables=None, encoded=None, deps=None):
+                  raw_lens=None, total=None, tables=None, encoded=None, deps=None, levels=None):
     """blocks: list of token lists.  raw_streams: optional {block: [cmd, len,
     off, lit]} overriding the streams derived from tokens.  encoded: optional
     {(block, stream): (mode, K, body)} to place an entropy-coded body.
     expected: decoded bytes (for the per-block FNV via fnv).  deps: optional
     per-block lists of source-block ids (writes the dependency section).
+    levels: optional per-block level bytes (one per token): sets flags bit1
+    and writes each block's level body after its four stream bodies.
     Returns bytes."""
     nb = len(blocks)
     streams = [block_streams(t) for t in blocks]
@@ -89,6 +91,9 @@ def build_archive(blocks, *, min_match=4, flags=0, expected=None, fnv=None, raw_
                 body = raw
                 desc += struct.pack("<IIBBH", len(raw), len(raw), 0, 0, 0)
             bodies += body + b"\0" * (pad16(len(body)) - len(body))
+        if levels is not None:
+            lv = bytes(levels[b])
+            bodies += lv + b"\0" * (pad16(len(lv)) - len(lv))
         payload += desc + bodies
         n_tok = len(streams[b][0]) if isinstance(streams[b][0], (bytes, bytearray)) else streams[b][0]
         h = 0
@@ -98,7 +103,7 @@ def build_archive(blocks, *, min_match=4, flags=0, expected=None, fnv=None, raw_
                              dep_pos[b][0], dep_pos[b][1], 0, h)
     hdr = bytearray(64)
     hdr[0:4] = b"ACX1"
-    struct.pack_into("<HHIIQI", hdr, 4, 1, flags, BLOCK, min_match, total, nb)
+    struct.pack_into("<HHIIQI", hdr, 4, 1, flags | (2 if levels is not None else 0), BLOCK, min_match, total, nb)
     struct.pack_into("<QQQQ", hdr, 32, off_tables, off_index, off_deps, off_payload)
     tab = bytearray(2048)
     if tables is not None:

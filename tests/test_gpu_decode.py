@@ -81,6 +81,18 @@ def test_library_encoded_small_config(acx, ctx, dna4m, text4m, kind, no_rep, lan
 
 
 @pytest.mark.parametrize("variant", [FAST, PLAIN])
+@pytest.mark.parametrize("kind", ["dna", "text"])
+def test_level_bodies_do_not_change_the_decode(acx, ctx, dna4m, text4m, kind, variant):
+    """Archives that carry level bodies (flags bit1, one scheduling hint per
+    token) decode bit-exact, like the same archive without them."""
+    data = (dna4m if kind == "dna" else text4m)[: (1 << 20) + 777]
+    arc = acx.encode(data, levels=True)
+    rc, out = dec(ctx, arc, variant)
+    assert rc == 0, ctx.last_error()
+    assert np.array_equal(out, data)
+
+
+@pytest.mark.parametrize("variant", [FAST, PLAIN])
 def test_edge_sizes_and_ragged_tail(acx, ctx, variant):
     from gpu_util import gpu_decode
     rng = np.random.default_rng(7)

@@ -331,3 +331,48 @@ def test_encoder_level_statistics_follow_the_archive(acx, kind, max_depth):
     assert st["level_bytes"] == nbytes.tolist()
     # a match's level never exceeds its chain depth
     assert max(l for l in range(256) if count[l]) <= max(d for d in range(256) if st["match_depth"][d])
+
+
+@pytest.mark.parametrize("kind,no_rep", [("dna", False), ("text", False), ("text", True)])
+def test_encoder_level_bodies(acx, kind, no_rep):
+    """aceapex_enc_params.levels: the archive carries, per token, the level
+    recomputed from its own parse (a match whose source window lies in its
+    own block and holds only level-0 bytes: 0; any other: 1 + the highest
+    level in the window; a closing literal-only token: 0).  The four streams
+    are those of the archive without levels, so both decode alike."""
+    data = synth.corpus(kind, (1 << 20) + 555, 13)
+    arc = acx.encode(data, no_rep=no_rep, levels=True)
+    arc0 = acx.encode(data, no_rep=no_rep)
+    assert np.array_equal(oracle.decode(arc), data)
+    acx.archive_check(arc)
+    nb = (data.size + BLOCK - 1) // BLOCK
+    lv = np.zeros(data.size, np.int64)
+    for b in range(nb):
+        t = oracle.parse_block(arc, b)
+        want = []
+        for cmd, dst, src, ml in zip(t["cmd"].tolist(), t["dst"].tolist(), t["src"].tolist(), t["ml"].tolist()):
+            if cmd == 5:
+                want.append(0)
+                continue
+            mx = int(lv[src:src + min(dst - src, ml)].max())
+            level = 0 if (src >= b * BLOCK and mx == 0) else min(mx + 1, 255)
+            lv[dst:dst + ml] = level
+            want.append(level)
+        assert oracle.block_levels(arc, b).tolist() == want, b
+        for s in range(4):
+            assert np.array_equal(oracle.block_stream(arc, b, s), oracle.block_stream(arc0, b, s))
+
+
+def test_host_checks_accept_level_bodies_and_reject_short_ones(acx):
+    from fmt_writer import build_archive as build
+    blk0 = [{"cmd": 0, "lits": b"ABCDEFGH", "ml": 8, "src": 0},
+            {"cmd": 5, "lits": b"x" * (BLOCK - 16), "ml": 0}]
+    blk1 = [{"cmd": 0, "lits": b"", "ml": 12, "src": 3}, {"cmd": 5, "lits": b"!", "ml": 0}]
+    good = build([blk0, blk1], levels=[[0, 0], [1, 0]])
+    assert acx.archive_check(good)["n_blocks"] == 2
+    bad = bytearray(good)
+    e = int.from_bytes(bad[40:48], "little") + 40
+    plen = int.from_bytes(bad[e + 8:e + 12], "little")
+    bad[e + 8:e + 12] = (plen - 16).to_bytes(4, "little")
+    with pytest.raises(acx.AceapexError):
+        acx.archive_check(bytes(bad))

@@ -376,3 +376,34 @@ def test_archive_statistics_of_a_hand_built_archive():
     for k, v in want.items():
         assert st[k] == v, (k, st[k], v)
     assert oracle.decode(arc, verify=False).size == 16384 + 17
+
+
+def test_level_bodies_are_hints_that_never_change_the_decode():
+    """Format v1 flags bit1: each payload carries a stored level body (one
+    byte per token) after its four stream bodies.  The levels are scheduling
+    hints (paper, Depth Does Not Govern Latency: waves); an archive decodes
+    to the same bytes with or without them, whatever their values, and a
+    level body that leaves its payload is corrupt."""
+    blk0 = [{"cmd": 0, "lits": b"ABCDEFGH", "ml": 8, "src": 0},
+            {"cmd": 5, "lits": b"x" * (oracle.BLOCK - 16), "ml": 0}]
+    blk1 = [{"cmd": 0, "lits": b"", "ml": 12, "src": 3},
+            {"cmd": 1, "lits": b"yz", "ml": 5},
+            {"cmd": 5, "lits": b"!", "ml": 0}]
+    plain = build_archive([blk0, blk1])
+    with_levels = build_archive([blk0, blk1], levels=[[0, 0], [1, 2, 0]])
+    odd_levels = build_archive([blk0, blk1], levels=[[7, 255], [0, 0, 9]])
+    want = oracle.decode(plain, verify=False)
+    assert want.size == oracle.BLOCK + 20
+    assert np.array_equal(oracle.decode(with_levels, verify=False), want)
+    assert np.array_equal(oracle.decode(odd_levels, verify=False), want)
+    assert oracle.block_levels(with_levels, 1).tolist() == [1, 2, 0]
+    assert oracle.block_levels(odd_levels, 0).tolist() == [7, 255]
+    with pytest.raises(oracle.OracleError):
+        oracle.block_levels(plain, 0)
+    # a level body cut short: the payload length no longer covers it
+    bad = bytearray(with_levels)
+    off_index = int.from_bytes(bad[40:48], "little")
+    e = off_index + 40  # block 1's index entry
+    plen = int.from_bytes(bad[e + 8:e + 12], "little")
+    bad[e + 8:e + 12] = (plen - 16).to_bytes(4, "little")
+    assert oracle.decode_status(bytes(bad), verify=False)[0] == oracle.E_CORRUPT
