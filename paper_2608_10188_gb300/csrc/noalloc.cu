@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_plan_small(const uint8_t* a, uint64_t l
     uint32_t* tab = reinterpret_cast<uint32_t*>(base + kOffTab);
     __shared__ int bad;            // 0 ok, -2 corrupt, -1 too large
     __shared__ uint64_t off_tab, off_idx, off_deps, total;
-    __shared__ uint32_t nb, min_match;
+    __shared__ uint32_t nb, min_match, flags;
     __shared__ uint16_t freq[4][256];
     __shared__ uint32_t ok_tab[4];
     const int tid = threadIdx.x;
@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(256) k_plan_small(const uint8_t* a, uint64_t l
             rd32d(a + 8) != kBlock) {
             bad = -2;
         } else {
+            flags = rd16d(a + 6);
             min_match = rd32d(a + 12);
             total = rd64d(a + 16);
             nb = rd32d(a + 24);
@@ -164,6 +165,10 @@ __global__ void __launch_bounds__(256) k_plan_small(const uint8_t* a, uint64_t l
                 bd.s_off[s] = (uint32_t)soff;
                 soff = (soff + sraw + 15) & ~(uint64_t)15;
                 off = (off + enc + 15) & ~(uint64_t)15;
+            }
+            if (flags & 2) {  // the level body (one stored byte per token) after the four streams
+                ok = ok && off + n_tok <= plen;
+                off = (off + n_tok + 15) & ~(uint64_t)15;
             }
             ok = ok && off == plen && bd.s_raw[kCmd] == n_tok && bd.s_raw[kOff] % 5 == 0;
             bd.n_new = bd.s_raw[kOff] / 5;

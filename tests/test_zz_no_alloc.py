@@ -34,11 +34,12 @@ def _regular(acx, ctx, arc_h, d_arc, total):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("kind,no_rep", [("dna", False), ("text", False), ("dna", True)])
-def test_noalloc_matches_decode_all_twice(acx, kind, no_rep):
+@pytest.mark.parametrize("kind,no_rep,levels", [("dna", False, False), ("text", False, False), ("dna", True, False),
+                                                ("text", False, True)])
+def test_noalloc_matches_decode_all_twice(acx, kind, no_rep, levels):
     import torch
     data = synth.corpus(kind, (1 << 20) - 777, 21)  # 64 blocks, ragged last block
-    arc = acx.encode(data, no_rep=no_rep)
+    arc = acx.encode(data, no_rep=no_rep, levels=levels)
     arc_h = np.frombuffer(arc, dtype=np.uint8).copy()
     d_arc = torch.from_numpy(arc_h).cuda()
     ctx = acx.Context(0)
