@@ -376,3 +376,53 @@ def test_host_checks_accept_level_bodies_and_reject_short_ones(acx):
     bad[e + 8:e + 12] = (plen - 16).to_bytes(4, "little")
     with pytest.raises(acx.AceapexError):
         acx.archive_check(bytes(bad))
+
+
+def _levels_from_parse(arc, nb, size):
+    lv = np.zeros(max(size, 1), np.int64)
+    out = []
+    for b in range(nb):
+        t = oracle.parse_block(arc, b)
+        want = []
+        for cmd, dst, src, ml in zip(t["cmd"].tolist(), t["dst"].tolist(), t["src"].tolist(), t["ml"].tolist()):
+            if cmd == 5:
+                want.append(0)
+                continue
+            mx = int(lv[src:src + min(dst - src, ml)].max())
+            level = 0 if (src >= b * BLOCK and mx == 0) else min(mx + 1, 255)
+            lv[dst:dst + ml] = level
+            want.append(level)
+        out.append(want)
+    return out
+
+
+def test_randomized_encoder_options_round_trip(acx):
+    """Random inputs (random bytes, long repeats, DNA, text, their mixtures;
+    0 to 200 KB) under random encoder options: each archive passes the
+    library's host checks, decodes to its input in the oracle, and when it
+    carries levels they are the levels of its own parse."""
+    rng = np.random.default_rng(2024)
+    for it in range(150):
+        n = int(rng.choice([0, 1, 17, 4095, 16384, 16385, int(rng.integers(1, 200_000))]))
+        kind = int(rng.integers(0, 4))
+        if kind == 0:
+            data = rng.integers(0, 256, n, dtype=np.uint8)
+        elif kind == 1:
+            unit = rng.integers(0, 256, int(rng.integers(1, 40)), dtype=np.uint8)
+            data = np.resize(unit, n).astype(np.uint8)
+        elif kind == 2:
+            data = synth.dna(n, int(rng.integers(0, 1000))) if n else np.zeros(0, np.uint8)
+        else:
+            data = synth.text(n, int(rng.integers(0, 1000))) if n else np.zeros(0, np.uint8)
+        opts = {"no_rep": bool(rng.integers(0, 2)), "levels": bool(rng.integers(0, 2)),
+                "max_depth": int(rng.choice([0, 1, 2, 5, 0xFFFFFFFF])),
+                "max_lanes": int(rng.choice([1, 4, 32, 128])), "deps": bool(rng.integers(0, 2)),
+                "segment": int(rng.choice([0, 16384, 65536]))}
+        arc = acx.encode(data, **opts)
+        acx.archive_check(arc)
+        assert np.array_equal(oracle.decode(arc), data), (it, n, kind, opts)
+        if opts["levels"] and n:
+            nb = (n + BLOCK - 1) // BLOCK
+            want = _levels_from_parse(arc, nb, n)
+            for b in range(nb):
+                assert oracle.block_levels(arc, b).tolist() == want[b], (it, b, opts)
