@@ -182,3 +182,26 @@ def test_full_size_genome_matches_oracle(acx, ctx):
     assert np.array_equal(out, data)
     ref = oracle.decode(arc)
     assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("kind", ["dna", "text"])
+def test_cross_block_policies_depths_and_launch_shapes(acx, dna4m, text4m, kind):
+    """The cross-block pass under every round-0 policy (wait without limit,
+    defer at once, the automatic choice), on archives with deep uncapped
+    chains, a cap of 1, and independent segments, and the decode under
+    small launch shapes: every combination decodes bit-exact."""
+    from gpu_util import gpu_decode
+    data = (dna4m if kind == "dna" else text4m)[: (2 << 20) + 4321]
+    archives = {"no cap": acx.encode(data, max_depth=0xFFFFFFFF), "cap 1": acx.encode(data, max_depth=1),
+                "segments": acx.encode(data, segment=1 << 18), "levels": acx.encode(data, levels=True)}
+    shapes = [dict(wait_ns=0xFFFFFFFF), dict(wait_ns=1), dict(wait_ns=0),
+              dict(ctas_per_sm=1, rans_ctas_per_sm=1, queue_chunk=4)]
+    for shape in shapes:
+        ctx = acx.Context(0, timeout_us=2_000_000, **shape)
+        try:
+            for name, arc in archives.items():
+                rc, out = gpu_decode(ctx, arc)  # the context's own parameters (fast decoder)
+                assert rc == 0, (name, shape, ctx.last_error())
+                assert np.array_equal(out, data), (name, shape)
+        finally:
+            ctx.close()
