@@ -93,6 +93,9 @@ typedef struct {
 /* Decoder variants. */
 #define ACEAPEX_VARIANT_FAST 0   /* scan parse + periodic fill + dependency dataflow */
 #define ACEAPEX_VARIANT_PLAIN 1  /* serial parse with history, byte-serial copies (comparison) */
+#define ACEAPEX_VARIANT_FUSED 2  /* FAST, with a whole-archive decode's entropy stage and local pass in one
+                                    kernel, entropy warps and local groups side by side on every SM
+                                    (comparison: slower on GB300, see the design notes) */
 
 typedef struct {
     uint32_t variant;     /* ACEAPEX_VARIANT_* */
@@ -112,8 +115,10 @@ typedef struct {
  * (filled only when stats is non-NULL; timing adds event records). */
 typedef struct {
     double ms_total;  /* whole call, device time */
-    double ms_ans;    /* entropy stage (rANS decode of the four streams) */
-    double ms_parse;  /* local pass: parse, literals and in-block matches */
+    double ms_ans;    /* entropy stage (rANS decode of the four streams); with the fused kernel only the
+                         reset launches before it */
+    double ms_parse;  /* local pass: parse, literals and in-block matches; with the fused kernel the
+                         entropy stage and the local pass together */
     double ms_copy;   /* cross-block pass: matches whose source chain leaves their block */
     uint64_t blocks;  /* blocks decoded */
     uint64_t bytes;   /* bytes written to the output */
@@ -421,21 +426,25 @@ int aceapex_autotune(aceapex_ctx* ctx, const aceapex_batch_item* items, int n, i
 
 /*
  * Decode without allocating anything (the paper has no counterpart: this is a
- * service of this library).  For callers that cannot allocate device memory
- * at decode time — code running while a CUDA graph is being captured,
- * processes whose device memory belongs to a framework pool, latency-bound
- * paths where an allocation may stall or fail.  It needs no context and no
- * opened archive: d_arc (device pointer, arc_len bytes) is validated and
- * planned on the device, and all scratch lives in one static device array of
- * about 5.3 MiB that every device loading this library holds until the
- * process exits.  Limits: at most 64 blocks (1 MiB of output), at most
- * 2 MiB of decoded streams and 96K pending pieces; larger archives return
- * ACEAPEX_E_ARG.  The output goes to d_out (device pointer, out_cap >= the
- * decompressed size).  The call enqueues on `stream` and synchronises it;
- * it returns the decode status.  The first call on a device looks up the
- * array's device address (make that first call before any stream capture).
- * Every call on a device shares the array: calls that overlap on the GPU
- * (from other streams or threads) race and must be serialised by the caller.
+ * service of this library).  For callers that may not allocate device memory
+ * at decode time: processes whose device memory belongs to a framework's pool,
+ * and latency-bound paths where an allocation may stall or fail.  It needs no
+ * context and no opened archive: d_arc (device pointer, arc_len bytes) is
+ * validated and planned on the device, and all scratch lives in one static
+ * device array of about 5.3 MiB that every device loading this library holds
+ * until the process exits.  Limits: at most 64 blocks (1 MiB of output), at
+ * most 2 MiB of decoded streams and 96K pending pieces; valid archives beyond
+ * them return ACEAPEX_E_ARG, and an archive that aceapex_decode_all would
+ * find corrupt returns ACEAPEX_E_CORRUPT.  Dependency lists, when the archive
+ * has them, are checked as in aceapex_decode_all.  The output goes to d_out
+ * (device pointer, out_cap >= the decompressed size).  The call enqueues on
+ * `stream`, reads the device plan's summary back to the host and synchronises
+ * the stream (twice), and returns the decode status; so it cannot be recorded
+ * into a CUDA graph.  The first call on a device looks up the array's device
+ * address.  Every call on a device shares the array and finds the previous
+ * call's contents there (the call clears what must start at zero): calls that
+ * overlap on the GPU (from other streams or threads) race and must be
+ * serialised by the caller.
  */
 int aceapex_decode_noalloc(const void* d_arc, uint64_t arc_len, void* d_out, uint64_t out_cap, void* stream);
 

@@ -27,13 +27,13 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("rans.cu", "assemble.cu", "plain.cu", "noalloc.cu", "gather.cu", "api.cpp",
+    return [os.path.join(CSRC, f) for f in ("rans.cu", "assemble.cu", "fused.cu", "plain.cu", "noalloc.cu", "gather.cu", "api.cpp",
                                           "batch.cpp", "subset.cpp", "closure.cpp", "serve.cpp", "plan.cpp",
                                           "encode.cpp")]
 
 
 def _deps():
-    return sources() + [os.path.join(CSRC, f) for f in ("internal.h", "plan.h", "common.cuh", "launch.h", "host.h")] + [
+    return sources() + [os.path.join(CSRC, f) for f in ("internal.h", "plan.h", "common.cuh", "launch.h", "host.h", "rans_dev.cuh", "local_dev.cuh")] + [
         os.path.join(os.path.dirname(HERE), "include", "aceapex.h")]
 
 

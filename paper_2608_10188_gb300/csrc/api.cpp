@@ -78,6 +78,7 @@ int aceapex_ctx_destroy(aceapex_ctx* c) {
     c->slot_out.release();
     c->items.release();
     c->need.release();
+    c->ready.release();
     if (c->counters) cudaFree(c->counters);
     if (c->d_err) cudaFree(c->d_err);
     for (auto& ev : c->ev)
@@ -271,15 +272,20 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     job.lists[1] = (JobDev::ListEnt*)c->lists.p + std::max<uint64_t>(P.span_slots, 1);
     if (P.n_blocks == 0) return ACEAPEX_OK;
     LaunchPlan lp;
-    int rc = launch_plan(c, c->params, P.max_tok, P.max_lenb, &lp);
+    int rc = launch_plan(c, c->params, P.max_tok, P.max_lenb, &lp, 0, true);
     if (rc) return rc;
+    if (lp.fused_groups) {
+        if ((e = c->ready.ensure(nb * 4)) != cudaSuccess) return cuda_fail(c, e, "ready-flag allocation");
+        job.ready = (uint32_t*)c->ready.p;
+    }
     return enqueue_job(c, job, lp, 3 + 1, nullptr, 0, st, timed ? c->ev : nullptr);
 }
 
 int acx::launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_tok, uint32_t max_lenb,
-                     LaunchPlan* lp, uint32_t job_flags) {
+                     LaunchPlan* lp, uint32_t job_flags, bool whole_single) {
     // parse-only and wanted-byte jobs run the scan decoder (the serial one has neither mode)
     lp->variant = (job_flags & (kJobIndex | kJobNeed)) ? (uint32_t)ACEAPEX_VARIANT_FAST : p.variant;
+    if (lp->variant > ACEAPEX_VARIANT_FUSED) return fail(c, ACEAPEX_E_ARG, "unknown decoder variant");
     lp->chunk = p.queue_chunk ? p.queue_chunk : 1;
     lp->wait_ns = p.wait_ns;
     lp->grid_rans = (p.rans_ctas_per_sm ? std::min<int>(c->occ_rans, (int)p.rans_ctas_per_sm) : c->occ_rans) * c->n_sms;
@@ -292,6 +298,15 @@ int acx::launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_t
         int occ = std::max(1, local_occupancy(lsm));
         if (p.ctas_per_sm) occ = std::min<int>(occ, (int)p.ctas_per_sm);
         lp->grid_local = occ * c->n_sms;
+    }
+    // the fused variant: entropy stage and local pass in one kernel when the
+    // job is one whole archive and a CTA holds the tables and a workspace
+    if (whole_single && lp->variant == ACEAPEX_VARIANT_FUSED && !job_flags) {
+        const int G = fused_groups(max_tok, max_lenb);
+        if (G > 0 && fused_occupancy(G, max_tok, max_lenb) >= 1) {
+            lp->fused_groups = G;
+            lp->grid_fused = c->n_sms;
+        }
     }
     return ACEAPEX_OK;
 }
@@ -308,9 +323,21 @@ int acx::enqueue_job(aceapex_ctx* c, const JobDev& job_in, const LaunchPlan& lp,
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return cuda_fail(c, e, "event");
     if ((e = launch_prologue(job.counters, n_counters, st, errs, n_errs)) != cudaSuccess)
         return cuda_fail(c, e, "prologue launch");
-    if ((e = launch_rans(job, lp.grid_rans, st)) != cudaSuccess) return cuda_fail(c, e, "rANS launch");
-    if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return cuda_fail(c, e, "event");
-    if (lp.variant == ACEAPEX_VARIANT_PLAIN) {
+    if (lp.fused_groups && job.ready) {
+        // fused: one launch for the entropy stage and the local pass (the
+        // stage split reports it as the local pass)
+        if ((e = cudaMemsetAsync(job.ready, 0, (size_t)job.n_items * 4, st)) != cudaSuccess)
+            return cuda_fail(c, e, "ready-flag reset");
+        if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+        if ((e = launch_fused(job, lp.fused_groups, lp.grid_fused, st)) != cudaSuccess)
+            return cuda_fail(c, e, "fused launch");
+    } else {
+        job.ready = nullptr;
+        if ((e = launch_rans(job, lp.grid_rans, st)) != cudaSuccess) return cuda_fail(c, e, "rANS launch");
+        if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    }
+    if (lp.fused_groups && job.ready) {
+    } else if (lp.variant == ACEAPEX_VARIANT_PLAIN) {
         if ((e = launch_plain(job, lp.grid_plain, st)) != cudaSuccess) return cuda_fail(c, e, "plain launch");
     } else {
         if ((e = launch_local(job, lp.grid_local, st)) != cudaSuccess) return cuda_fail(c, e, "local launch");

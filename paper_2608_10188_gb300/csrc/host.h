@@ -68,6 +68,7 @@ struct aceapex_ctx {
     int n_sms = 0;
     acx::DevBuf streams, npend, pmap, spans, lists, arcs, in_arc, out_buf;
     acx::DevBuf slot_out, items, need;   // range decodes: decoded closure blocks, work items, wanted bytes
+    acx::DevBuf ready;                   // fused decodes: per block, its streams are decoded
     uint32_t* counters = nullptr;  // device
     int* d_err = nullptr;          // device
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -105,12 +106,14 @@ std::string device_error_text(const int h[3]);
 struct LaunchPlan {
     uint32_t variant = 0, chunk = 1, wait_ns = 0;
     int grid_rans = 0, grid_local = 0, grid_plain = 0, grid_ext = 0;
+    int fused_groups = 0, grid_fused = 0;  // fused entropy + local pass (whole single-archive jobs), 0: staged
 };
 // Grids for a job whose largest block has max_tok tokens and max_lenb length
 // bytes, under decoder parameters p (fails when a block cannot fit the local
-// pass's shared memory).
+// pass's shared memory).  whole_single: the job decodes one whole archive,
+// which the default variant may do with the fused entropy + local kernel.
 int launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_tok, uint32_t max_lenb, LaunchPlan* lp,
-                uint32_t job_flags = 0);
+                uint32_t job_flags = 0, bool whole_single = false);
 // Synchronise st and return (and clear) the context's device error status.
 int ctx_read_status(aceapex_ctx* c, cudaStream_t st);
 

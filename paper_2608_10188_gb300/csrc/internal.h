@@ -144,6 +144,7 @@ struct JobDev {
         uint32_t x, y;        // span slot, item
     };
     ListEnt* lists[2];        // cross-block work lists
+    uint32_t* ready;          // fused decodes: per item, nonzero once its streams are decoded (else nullptr)
 };
 
 }  // namespace acx

@@ -1,19 +1,22 @@
 // Decode entry point that allocates nothing (aceapex_decode_noalloc).
 //
-// Some callers cannot allocate device memory when they decode: code running
-// while a CUDA graph is being captured, allocators that hand the whole device
-// to a framework pool at start-up, or real-time paths where an allocation's
-// latency or failure is not acceptable.  For small archives they get this
-// entry point: every byte of scratch it needs (the decode plan, the decoded
-// streams, the pending bitmaps and pieces, the work lists, the tickets and
-// the error word) lives in one file-scope device array, and the archive's
-// plan is built on the device by a small kernel, so neither device nor host
-// memory is allocated.
+// Some callers cannot allocate device memory when they decode: allocators
+// that hand the whole device to a framework pool at start-up, or real-time
+// paths where an allocation's latency or failure is not acceptable.  For
+// small archives they get this entry point: every byte of scratch it needs
+// (the decode plan, the dependency lists, the decoded streams, the pending
+// bitmaps and pieces, the work lists, the tickets and the error word) lives
+// in one file-scope device array, and the archive's plan is built on the
+// device by a small kernel, so neither device nor host memory is allocated.
+// The call reads the plan summary and the status back to the host and
+// synchronises its stream twice, so it cannot be recorded into a CUDA graph.
 //
 // Limits: at most kNaMaxBlocks blocks (1 MiB of output) and the per-region
-// capacities below; larger archives are rejected with ACEAPEX_E_ARG.
-// The array is shared by every call in the process on a given device: calls
-// that overlap on the GPU (other streams, other host threads) race on it.
+// capacities below; valid archives beyond them are rejected with
+// ACEAPEX_E_ARG, archives the regular entry point finds corrupt with
+// ACEAPEX_E_CORRUPT.  The array is shared by every call in the process on a
+// given device: calls that overlap on the GPU (other streams, other host
+// threads) race on it.
 #include <algorithm>
 #include <mutex>
 
@@ -38,7 +41,11 @@ constexpr size_t kOffPlan = al(kOffCounters + kCounterWords * 4);
 constexpr size_t kOffTab = al(kOffPlan + kNaMaxBlocks * sizeof(BlockDev));
 constexpr size_t kOffNpend = al(kOffTab + 4 * kM * 4);
 constexpr size_t kOffPmap = al(kOffNpend + kNaMaxBlocks * 4);
-constexpr size_t kOffSpans = al(kOffPmap + (size_t)kNaMaxBlocks * (kBlock / 8));
+// dependency lists, copied out of the archive: block b's (at most b ids) at
+// [b(b-1)/2, b(b-1)/2 + b), so the kernels read aligned words
+constexpr size_t kNaDepWords = (size_t)kNaMaxBlocks * (kNaMaxBlocks - 1) / 2;
+constexpr size_t kOffDeps = al(kOffPmap + (size_t)kNaMaxBlocks * (kBlock / 8));
+constexpr size_t kOffSpans = al(kOffDeps + kNaDepWords * 4);
 constexpr size_t kOffLists = al(kOffSpans + (size_t)kNaSpanSlots * sizeof(SpanRec));
 constexpr size_t kOffStreams = al(kOffLists + 2 * (size_t)kNaSpanSlots * sizeof(JobDev::ListEnt));
 constexpr size_t kNaBytes = al(kOffStreams + kNaStreamBytes + 64);
@@ -53,7 +60,7 @@ namespace {
 // Plan summary written by k_plan_small and read back by the host.
 struct NaSummary {
     int32_t status;       // 0 ok, -2 corrupt, -1 beyond the static limits
-    uint32_t n_blocks, min_match, max_tok, max_lenb, pad;
+    uint32_t n_blocks, min_match, max_tok, max_lenb, has_deps;
     uint64_t total, span_slots, stream_bytes;
 };
 static_assert(sizeof(NaSummary) <= 64, "summary");
@@ -71,6 +78,7 @@ __global__ void __launch_bounds__(256) k_plan_small(const uint8_t* a, uint64_t l
     NaSummary* S = reinterpret_cast<NaSummary*>(base + kOffSummary);
     BlockDev* blk = reinterpret_cast<BlockDev*>(base + kOffPlan);
     uint32_t* tab = reinterpret_cast<uint32_t*>(base + kOffTab);
+    uint32_t* deps = reinterpret_cast<uint32_t*>(base + kOffDeps);
     __shared__ int bad;            // 0 ok, -2 corrupt, -1 too large
     __shared__ uint64_t off_tab, off_idx, off_deps, total;
     __shared__ uint32_t nb, min_match, flags;
@@ -126,13 +134,16 @@ __global__ void __launch_bounds__(256) k_plan_small(const uint8_t* a, uint64_t l
         const uint64_t B = (uint64_t)b * kBlock;
         const uint64_t R = total - B < kBlock ? total - B : kBlock;
         bool ok = raw == R && !(off_deps == 0 && (dep_off || n_deps));
+        // an ascending list of distinct ids below b has at most b entries
+        const uint32_t dslot = b * (b - 1) / 2;
         if (ok && off_deps) {
-            ok = off_deps <= len && (len - off_deps) / 4 >= (uint64_t)dep_off + n_deps;
+            ok = off_deps <= len && (len - off_deps) / 4 >= (uint64_t)dep_off + n_deps && n_deps <= b;
             uint32_t prev = 0;
             for (uint32_t k = 0; ok && k < n_deps; k++) {
                 const uint32_t id = rd32d(a + off_deps + 4 * ((uint64_t)dep_off + k));
                 if (id >= b || (k && id <= prev)) ok = false;
                 prev = id;
+                deps[dslot + k] = id;
             }
         }
         ok = ok && !(poff & 15) && !(plen & 15) && plen >= 48 && poff <= len && len - poff >= plen;
@@ -142,6 +153,10 @@ __global__ void __launch_bounds__(256) k_plan_small(const uint8_t* a, uint64_t l
             bd.payload = poff;
             bd.raw_len = raw;
             bd.n_tok = n_tok;
+            if (off_deps) {
+                bd.dep_off = dslot;
+                bd.n_deps = n_deps;
+            }
             uint64_t off = 48, soff = 0;
             for (int s = 0; s < 4 && ok; s++) {
                 const uint8_t* d = pay + 12 * s;
@@ -171,6 +186,10 @@ __global__ void __launch_bounds__(256) k_plan_small(const uint8_t* a, uint64_t l
                 off = (off + n_tok + 15) & ~(uint64_t)15;
             }
             ok = ok && off == plen && bd.s_raw[kCmd] == n_tok && bd.s_raw[kOff] % 5 == 0;
+            // every token but a closing literal run has a match of at least
+            // min_match bytes: more tokens than that cannot sum to the block
+            // (the regular decode finds such a block corrupt too)
+            ok = ok && n_tok <= raw / min_match + 1;
             bd.n_new = bd.s_raw[kOff] / 5;
             bd.scratch = soff;  // this block's stream bytes; offsets are assigned below
         }
@@ -199,6 +218,7 @@ __global__ void __launch_bounds__(256) k_plan_small(const uint8_t* a, uint64_t l
         S->max_tok = max_tok;
         S->max_lenb = max_lenb;
         S->total = total;
+        S->has_deps = off_deps != 0;
         S->span_slots = slots;
         S->stream_bytes = scratch;
     }
@@ -242,7 +262,7 @@ extern "C" int aceapex_decode_noalloc(const void* d_arc, uint64_t arc_len, void*
     if (out_cap < S.total) return ACEAPEX_E_ARG;
     if (S.n_blocks == 0) return ACEAPEX_OK;
     const size_t lsm = local_smem_bytes(S.max_tok, S.max_lenb);
-    if (lsm > 227 * 1024) return ACEAPEX_E_ARG;
+    if (lsm > 227 * 1024) return ACEAPEX_E_CORRUPT;  // as the regular plan: no valid block needs that much
     JobDev job{};
     ArcJob& J = job.one;
     J.arc = (const uint8_t*)d_arc;
@@ -258,6 +278,7 @@ extern "C" int aceapex_decode_noalloc(const void* d_arc, uint64_t arc_len, void*
     J.lo = 0;
     J.hi = S.n_blocks;
     J.min_match = S.min_match;
+    J.deps = S.has_deps ? reinterpret_cast<const uint32_t*>(base + kOffDeps) : nullptr;
     job.n_arcs = 1;
     job.n_items = S.n_blocks;
     job.counters = reinterpret_cast<uint32_t*>(base + kOffCounters);

@@ -14,7 +14,7 @@ import os
 from . import build as _build
 
 OK, E_ARG, E_CORRUPT, E_NOMEM, E_CUDA, E_TIMEOUT, E_RANGE, E_BUSY = 0, -1, -2, -3, -4, -5, -6, -7
-VARIANT_FAST, VARIANT_PLAIN = 0, 1
+VARIANT_FAST, VARIANT_PLAIN, VARIANT_FUSED = 0, 1, 2
 BLOCK_SIZE = 16384
 
 EXPORTED = [

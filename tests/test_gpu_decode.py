@@ -80,6 +80,23 @@ def test_library_encoded_small_config(acx, ctx, dna4m, text4m, kind, no_rep, lan
     assert np.array_equal(out, oracle.decode(arc))
 
 
+@pytest.mark.parametrize("no_rep", [False, True])
+@pytest.mark.parametrize("kind", ["dna", "text"])
+def test_fused_variant_matches_oracle(acx, dna4m, text4m, kind, no_rep):
+    """The fused comparison variant (entropy warps and local groups in one
+    kernel) decodes bit-exact against the oracle, with and without lists."""
+    from gpu_util import gpu_decode
+    data = (dna4m if kind == "dna" else text4m)[: (1 << 20) + 4567]
+    ctx = acx.Context(0, variant=acx.lib.VARIANT_FUSED, timeout_us=2_000_000)
+    try:
+        for arc in (acx.encode(data, no_rep=no_rep), acx.encode(data, no_rep=no_rep, deps=True)):
+            rc, out = gpu_decode(ctx, arc, acx.lib.VARIANT_FUSED)
+            assert rc == 0, ctx.last_error()
+            assert np.array_equal(out, oracle.decode(arc))
+    finally:
+        ctx.close()
+
+
 @pytest.mark.parametrize("variant", [FAST, PLAIN])
 @pytest.mark.parametrize("kind", ["dna", "text"])
 def test_level_bodies_do_not_change_the_decode(acx, ctx, dna4m, text4m, kind, variant):
@@ -87,9 +104,11 @@ def test_level_bodies_do_not_change_the_decode(acx, ctx, dna4m, text4m, kind, va
     token) decode bit-exact, like the same archive without them."""
     data = (dna4m if kind == "dna" else text4m)[: (1 << 20) + 777]
     arc = acx.encode(data, levels=True)
+    want = oracle.decode(arc)
+    assert np.array_equal(want, data)
     rc, out = dec(ctx, arc, variant)
     assert rc == 0, ctx.last_error()
-    assert np.array_equal(out, data)
+    assert np.array_equal(out, want)
 
 
 @pytest.mark.parametrize("variant", [FAST, PLAIN])
@@ -194,6 +213,9 @@ def test_cross_block_policies_depths_and_launch_shapes(acx, dna4m, text4m, kind)
     data = (dna4m if kind == "dna" else text4m)[: (2 << 20) + 4321]
     archives = {"no cap": acx.encode(data, max_depth=0xFFFFFFFF), "cap 1": acx.encode(data, max_depth=1),
                 "segments": acx.encode(data, segment=1 << 18), "levels": acx.encode(data, levels=True)}
+    want = {name: oracle.decode(arc) for name, arc in archives.items()}
+    for name in archives:
+        assert np.array_equal(want[name], data), name
     shapes = [dict(wait_ns=0xFFFFFFFF), dict(wait_ns=1), dict(wait_ns=0),
               dict(ctas_per_sm=1, rans_ctas_per_sm=1, queue_chunk=4)]
     for shape in shapes:
@@ -202,6 +224,6 @@ def test_cross_block_policies_depths_and_launch_shapes(acx, dna4m, text4m, kind)
             for name, arc in archives.items():
                 rc, out = gpu_decode(ctx, arc)  # the context's own parameters (fast decoder)
                 assert rc == 0, (name, shape, ctx.last_error())
-                assert np.array_equal(out, data), (name, shape)
+                assert np.array_equal(out, want[name]), (name, shape)
         finally:
             ctx.close()
