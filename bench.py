@@ -61,6 +61,12 @@ def parse_args():
                    help="encoder chain-depth cap (0: the library default of 16)")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the comparison measurements (plain decoder, history-free, text, serving)")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving measurement among the comparisons")
+    p.add_argument("--levels", type=int, default=0,
+                   help="1: encode with level bodies (the cross-block pass may take pieces in level order); "
+                        "0: without")
     p.add_argument("--no-graph", action="store_true", help="batch: plain launches instead of a graph replay")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="batch: keep the default lane cap and launch shapes")
@@ -92,13 +98,15 @@ def get_archive(args, acx):
     the local disk between runs of the same source version)."""
     size, _ = workload(args)
     data = synth.corpus(args.corpus, size, 0)
-    key = f"{args.corpus}-{size}-s0-{args.encoding}-k{args.lanes}-d{args.max_depth}-{encoder_key()}.acx"
+    key = (f"{args.corpus}-{size}-s0-{args.encoding}-k{args.lanes}-d{args.max_depth}-lv{args.levels}-"
+           f"{encoder_key()}.acx")
     path = os.path.join(args.cache_dir, key)
     arc = None
     if os.path.exists(path):
         arc = open(path, "rb").read()
     if arc is None:
-        arc = acx.encode(data, no_rep=args.encoding == "no_rep", max_lanes=args.lanes, max_depth=args.max_depth)
+        arc = acx.encode(data, no_rep=args.encoding == "no_rep", max_lanes=args.lanes, max_depth=args.max_depth,
+                         levels=bool(args.levels))
         try:
             os.makedirs(args.cache_dir, exist_ok=True)
             tmp = path + f".{os.getpid()}"
@@ -259,8 +267,103 @@ def cpu_oracle_baseline(arc, data, repeats=3):
     if not np.array_equal(out, data):
         raise RuntimeError("oracle decode mismatch")
     med = statistics.median(times)
-    return {"value": round(data.size / med / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+    return {"value": round(data.size / med / 1e9, 4), "unit": "GB/s", "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": f"whole archive ({data.size:,} B decoded), single-threaded C oracle, median of {repeats}"}
+
+
+def timed_decode(acx, torch, dev, flush, sh, data, arc, steps, warmup, **ctx_kw):
+    """One archive decoded `steps` times after `warmup` warm-ups, the L2
+    flushed between steps and every step timed with CUDA events on the
+    stream, after a correctness gate against the input; clocks sampled over
+    the timed steps."""
+    device = f"cuda:{dev}"
+    ctx = acx.Context(dev, **ctx_kw)
+    h = np.frombuffer(arc, np.uint8).copy()
+    d = torch.from_numpy(h).to(device)
+    A = acx.Archive(ctx, d.data_ptr(), h, h.size)
+    out = torch.empty(max(data.size, 1), dtype=torch.uint8, device=device)
+    rc = acx.decode_all(ctx, A, out.data_ptr(), data.size, sh)
+    if rc != 0:
+        raise RuntimeError(f"decode failed: {rc} {ctx.last_error()}")
+    if not torch.equal(out[:data.size], torch.from_numpy(data).to(device)):
+        raise RuntimeError("GPU decode differs from the input")
+    for _ in range(warmup):
+        flush.fill_(1)
+        acx.decode_all(ctx, A, out.data_ptr(), data.size, sh)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    rows, st = [], {}
+    for _ in range(steps):
+        flush.fill_(1)
+        r, st = acx.decode_all(ctx, A, out.data_ptr(), data.size, sh, stats=True)
+        if r != 0:
+            raise RuntimeError(f"decode failed: {r} {ctx.last_error()}")
+        rows.append((st["ms_total"], st["ms_ans"], st["ms_parse"], st["ms_copy"]))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tot = sum(r[0] for r in rows)
+    res = {"value": round(data.size * steps / (tot / 1e3) / 1e9, 3), "unit": "GB/s",
+           "ms_per_step": round(tot / steps, 4),
+           "stage_ms": {"ans": round(statistics.mean(r[1] for r in rows), 4),
+                        "local_parse_copy": round(statistics.mean(r[2] for r in rows), 4),
+                        "cross_block": round(statistics.mean(r[3] for r in rows), 4)},
+           "archive_bytes": len(arc), "ratio": round(data.size / len(arc), 4),
+           "pending_pieces": st.get("pending_spans"), "rounds_after_first": st.get("wait_polls"),
+           "verified": "decoded output equals the input", "clocks": clk}
+    A.close()
+    ctx.close()
+    return res
+
+
+def start_extra_encodes(args, acx, gdata):
+    """Encode the archives of the comparison measurements on background
+    threads while the headline runs: the genome history-free (level bodies
+    as in the headline), and the 200 MiB text in both encodings with level
+    bodies (its many pieces per lane are taken in level order)."""
+    from concurrent.futures import ThreadPoolExecutor
+    ex = ThreadPoolExecutor(max_workers=3)
+    ek = encoder_key()
+    tdata = synth.corpus("text", TEXT, 0)
+    futs = {"text_data": tdata}
+    futs["genome_history_free"] = ex.submit(
+        cached_encode, args, acx, gdata, f"dna-{gdata.size}-s0-no_rep-k{args.lanes}-lv{args.levels}-{ek}.acx",
+        no_rep=True, max_lanes=args.lanes, levels=bool(args.levels))
+    for enc in ("history", "no_rep"):
+        futs[f"text_{enc}"] = ex.submit(
+            cached_encode, args, acx, tdata, f"text-{TEXT}-s0-{enc}-k{args.lanes}-lv1-{ek}.acx",
+            no_rep=enc == "no_rep", max_lanes=args.lanes, levels=True)
+    futs["pool"] = ex
+    return futs
+
+
+def north_star_extras(args, acx, torch, dev, flush, sh, gdata, garc, futs):
+    """The comparisons the headline is read against, measured in the same
+    process on the same GPU: the plain history-bound decoder on the headline
+    archive, the history-free genome, the 200 MiB text in both encodings,
+    and the region server under load."""
+    steps, warm = max(5, args.steps // 2), 3
+    out = {}
+    out["plain"] = dict(workload="the headline archive, plain decoder (serial parse with the history, "
+                                 "byte-serial copies)",
+                        **timed_decode(acx, torch, dev, flush, sh, gdata, garc, steps, warm,
+                                       variant=acx.lib.VARIANT_PLAIN))
+    out["history_free"] = dict(workload=f"the same genome encoded history-free ({gdata.size:,} B)",
+                               **timed_decode(acx, torch, dev, flush, sh, gdata,
+                                              futs["genome_history_free"].result(), steps, warm))
+    tdata = futs["text_data"]
+    out["text"] = {"workload": f"synthetic Zipf text {tdata.size:,} B (50k-word vocabulary, s = 1.1), "
+                               "level bodies"}
+    for enc, key in (("history", "text_history"), ("history_free", "text_no_rep")):
+        out["text"][enc] = timed_decode(acx, torch, dev, flush, sh, tdata, futs[key].result(), steps, warm)
+    futs["pool"].shutdown()
+    hist, hfree = out["text"]["history"], out["text"]["history_free"]
+    out["history_free_vs_plain"] = round(out["history_free"]["value"] / out["plain"]["value"], 2)
+    out["text"]["history_free_vs_history"] = round(hfree["value"] / hist["value"], 3)
+    if not args.no_serve:
+        out["serve"] = serve_measure(args, dev)
+    return out
 
 
 def run_reference(args, dist):
@@ -288,8 +391,8 @@ def run_reference(args, dist):
         "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": wname, "encoding": args.encoding, "block_size": 16384},
-        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"whole archive per step ({size:,} B), single-threaded C oracle"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle", "sample": f"whole archive per step ({size:,} B), single-threaded C oracle"},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -406,7 +509,8 @@ def run_batch(args, dist):
             oracle.decode(pairs[i][1], verify=False)
             nb += specs[i]["size"]
         el = time.perf_counter() - t
-        cpu = {"value": round(nb / el / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": round(nb / el / 1e9, 4), "unit": "GB/s", "cores": 1, "host_cores": os.cpu_count(),
+               "kind": "oracle",
                "sample": f"the {len(small)} smallest archives of the batch ({nb:,} B), single-threaded C oracle"}
     if dist["rank"] == 0:
         kinds = {k: sum(1 for s in specs if s["kind"] == k) for k in ("dna", "text")}
@@ -464,6 +568,11 @@ def serve_archive(args, acx):
 
 
 def run_serve(args, dist):
+    line = serve_measure(args, dist["local"])
+    print(json.dumps(line), flush=True)
+
+
+def serve_measure(args, dev):
     """Region serving under open-loop Poisson load: requests with lognormal
     lengths (median 16 KiB, sigma 1, clipped to [4 KiB, 1 MiB]) at uniform
     starts arrive at serve_rate per second for 2 s of warm-up plus
@@ -474,7 +583,6 @@ def run_serve(args, dist):
 
     import paper_2608_10188_gb300 as acx
     acx.build.build()
-    dev = dist["local"]
     torch.cuda.set_device(dev)
     device = f"cuda:{dev}"
     t_setup = time.perf_counter()
@@ -574,10 +682,12 @@ def run_serve(args, dist):
         "verified": f"{smp.size} sampled requests equal the generator's bytes",
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
     srv.close()
     A.close()
     ctx.close()
+    del arena, d_arc
+    torch.cuda.empty_cache()
+    return line
 
 
 def init_dist(args):
@@ -662,6 +772,12 @@ def main():
     torch.cuda.set_device(dev)
     size, wname = workload(args)
     data, arc = get_archive(args, acx)
+    world = dist["world"]
+    # the comparisons of the default run (one GPU): their archives are encoded
+    # on host threads while the headline is measured
+    extras = (world == 1 and not args.no_extras and args.corpus == "dna" and not args.size
+              and args.encoding == "history" and args.variant == "fast" and not args.shard)
+    futs = start_extra_encodes(args, acx, data) if extras else None
     variant = acx.lib.VARIANT_PLAIN if args.variant == "plain" else acx.lib.VARIANT_FAST
     ctx = acx.Context(dev, variant=variant, wait_ns=args.wait_ns)
     h_arc = np.frombuffer(arc, dtype=np.uint8).copy()
@@ -673,7 +789,6 @@ def main():
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
-    world = dist["world"]
     # --shard: this rank decodes its block-aligned range through the range's
     # byte-level closure (strong scaling); otherwise every rank decodes its
     # own replica of the whole archive (weak scaling)
@@ -778,6 +893,10 @@ def main():
     if dist["rank"] == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_baseline(arc, data)
 
+    north = None
+    if extras:
+        north = north_star_extras(args, acx, torch, dev, flush, sh, data, arc, futs)
+
     if dist["rank"] == 0:
         line = {
             "metric": "device-resident decode GB/s", "value": round(value, 3), "unit": "GB/s",
@@ -785,6 +904,7 @@ def main():
             "higher_is_better": True, "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
             "dtype": "u8", "data": "synthetic (seeded generator; stands in for chr1 hg38)",
             "config": {"workload": wname, "encoding": args.encoding, "variant": args.variant,
+                       "levels": "level bodies, level-ordered cross-block rounds" if args.levels else "none",
                        "max_depth": args.max_depth or 16,
                        "rans_lanes": args.lanes, "block_size": 16384, "blocks": info["n_blocks"],
                        "tokens": info["tokens"], "archive_bytes": len(arc),
@@ -802,9 +922,11 @@ def main():
             "path_roofline": path_roof,
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": (6 if args.levels and args.variant == "fast" else 4) * args.steps,
+            "gpu_launches_note": "prologue, entropy stage, local pass, [level scan, level fill,] cross-block pass",
             "clocks": clk,
             "wall_s": round(wall, 3),
+            "north_star": north,
         }
         print(json.dumps(line), flush=True)
     A.close()
@@ -814,61 +936,68 @@ def main():
         dist["pg"].destroy_process_group()
 
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, keyed by
-# (workload, kernel): the --set full capture of profiles/ncu_full_decode_dna_64MiB.md
-# (4,096 blocks) scaled to the genome's 15,499 blocks; absent (null) for
-# workloads and kernels without a capture of the current code
-TRAFFIC = {
-    ("chr1-shaped synthetic genome 253,935,557 B", "k_rans"): 99_840_000,
-    ("chr1-shaped synthetic genome 253,935,557 B", "k_local"): 332_140_000,
-    ("chr1-shaped synthetic genome 253,935,557 B", "k_external"): 140_940_000,
-}
+def kernel_source_key():
+    """Hash of the files that make up the decode kernels: profiler counters
+    taken on other sources do not describe these kernels."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2608_10188_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")) or f == "internal.h":
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
-# Issue (ALU) ceiling of the entropy stage, which ncu shows issue-bound:
-# warp-instructions per decoded symbol from the same --set full capture
-# (94,815,686 warp-instructions for the 57,972,156 symbols of that 64 MiB
-# genome; the full genome has the same symbol mix), against one
-# warp-instruction per cycle on each of the 4 schedulers of the 152 SMs at
-# the 2070 MHz maximum clock.
-RANS_INSTR_PER_SYMBOL = 94_815_686 / 57_972_156
-ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions per second
+# Counters from one-kernel ncu captures of the full-size workload, per launch,
+# keyed by (kernel source key, workload, kernel): DRAM bytes read + written,
+# and warp-instructions per decoded symbol of the entropy stage.  A key that
+# does not match the running sources gives null: the counters were taken on
+# other kernels.
+CAPTURED_DRAM = {}
+CAPTURED_RANS_INSTR_PER_SYMBOL = {}
+ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions per second: 4 schedulers x 152 SMs x 2070 MHz
 
 
 def rooflines(stage, pb, size, arc_len, st, n_blocks, variant, ms_step, wname=""):
-    """HBM roofline of each decode kernel from its algorithmic bytes per launch
-    over its CUDA-event time, the dominant (slowest) kernel first, and of the
-    whole path (archive bytes read + output bytes written over the step)."""
+    """HBM roofline of the decode (SURVEY-style accounting of the paper's
+    memory floor): the algorithmic bytes of one decode are the archive read
+    plus the output written; `achieved` divides them by the CUDA-event time of
+    the dominant (slowest) kernel of the step, `frac` by the measured HBM copy
+    peak.  Each kernel's own traffic by design (the decoded streams it writes
+    or reads, the pending pieces) is reported beside it, not as algorithmic."""
     peak, peak_kind = measured_peaks()
+    src = kernel_source_key()
     pend_b = int(st.get("pending_bytes") or 0)
     pend_n = int(st.get("pending_spans") or 0)
     local = "k_plain" if variant == "plain" else "k_local"
+    path_bytes = arc_len + size
     kern = {
         # payload read + decoded streams written
         "k_rans": (stage["ans"], pb["payload"] + pb["decoded"]),
         # decoded streams read + output written
         local: (stage["local"], pb["decoded"] + size),
-        # source bytes read + destination bytes written + 16 B per piece record
-        # + 4 B pending count per block
+        # source bytes read + destination bytes written + 16 B per piece record + 4 B count per block
         "k_external": (stage["cross"], 2 * pend_b + 16 * pend_n + 4 * n_blocks),
     }
-    per = {k: {"ms": round(ms, 4), "algorithmic_bytes": int(b),
-               "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1) if ms > 0 else None,
-               "frac": round(b / (ms / 1e3) / 1e9 / peak, 4) if ms > 0 else None,
-               "traffic": TRAFFIC.get((wname, k))} for k, (ms, b) in kern.items()}
-    if wname and stage["ans"] > 0:
-        instr = RANS_INSTR_PER_SYMBOL * pb["decoded"]
-        rate = instr / (stage["ans"] / 1e3)
-        per["k_rans"]["alu"] = {"bound": "alu", "instructions": int(instr), "achieved": round(rate / 1e12, 4),
-                                "peak": round(ISSUE_PEAK / 1e12, 4), "unit": "T warp-instr/s",
-                                "frac": round(rate / ISSUE_PEAK, 4)}
+    per = {}
+    for k, (ms, b) in kern.items():
+        per[k] = {"ms": round(ms, 4), "design_bytes": int(b),
+                  "design_gbs": round(b / (ms / 1e3) / 1e9, 1) if ms > 0 else None,
+                  "traffic": CAPTURED_DRAM.get((src, wname, k)), "traffic_source": "ncu one-kernel capture"}
+    instr = CAPTURED_RANS_INSTR_PER_SYMBOL.get((src, wname))
+    if instr and stage["ans"] > 0:
+        rate = instr * pb["decoded"] / (stage["ans"] / 1e3)
+        per["k_rans"]["alu"] = {"bound": "alu", "instr_per_symbol": round(instr, 4), "source": "ncu capture",
+                                "achieved": round(rate / 1e12, 4), "peak": round(ISSUE_PEAK / 1e12, 4),
+                                "unit": "T warp-instr/s", "frac": round(rate / ISSUE_PEAK, 4)}
     dom = max(kern, key=lambda k: kern[k][0])
-    ms, b = kern[dom]
-    achieved = b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    ms = kern[dom][0]
+    achieved = path_bytes / (ms / 1e3) / 1e9 if ms > 0 else 0.0
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get((wname, dom)), "peak_kind": peak_kind + " hbm_gbs",
-            "algorithmic_bytes": int(b), "kernels": per}
-    path_bytes = arc_len + size
+            "frac": round(achieved / peak, 4), "traffic": CAPTURED_DRAM.get((src, wname, dom)),
+            "peak_kind": peak_kind + " hbm_gbs", "algorithmic_bytes": int(path_bytes),
+            "algorithmic": "archive bytes read + output bytes written (1 + 1/ratio per output byte)",
+            "kernel_source": src, "kernels": per}
     path_gbs = path_bytes / (ms_step / 1e3) / 1e9
     path = {"bytes": path_bytes, "achieved": round(path_gbs, 1), "peak": peak, "frac": round(path_gbs / peak, 4),
             "frac_nominal_8tbs": round(path_gbs / 8000, 4)}

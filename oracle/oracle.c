@@ -244,7 +244,7 @@ static int blk_token(blk_t* bk, uint8_t cmd, uint32_t LL, uint32_t ML, const uin
     if (buf_put(&bk->s[ORC_CMD], cmd)) return -1;
     if (buf_leb(&bk->s[ORC_LEN], LL) || buf_leb(&bk->s[ORC_LEN], ML)) return -1;
     if (buf_reserve(&bk->s[ORC_LIT], LL)) return -1;
-    memcpy(bk->s[ORC_LIT].p + bk->s[ORC_LIT].n, lits, LL);
+    if (LL) memcpy(bk->s[ORC_LIT].p + bk->s[ORC_LIT].n, lits, LL);  /* (an empty buffer may have no storage yet) */
     bk->s[ORC_LIT].n += LL;
     if (is_new) {
         if (bk->n_new == bk->cap_new) {

@@ -79,8 +79,14 @@ int aceapex_ctx_destroy(aceapex_ctx* c) {
     c->items.release();
     c->need.release();
     c->ready.release();
+    c->lvl_tab.release();
+    c->lvl_off.release();
+    c->lvl_list.release();
     if (c->counters) cudaFree(c->counters);
     if (c->d_err) cudaFree(c->d_err);
+    for (auto& ev : c->pipe_ev) cudaEventDestroy(ev);
+    if (c->s_up) cudaStreamDestroy(c->s_up);
+    if (c->s_down) cudaStreamDestroy(c->s_down);
     for (auto& ev : c->ev)
         if (ev) cudaEventDestroy(ev);
     delete c;
@@ -231,8 +237,9 @@ int aceapex_archive_get_info(const aceapex_archive* A, aceapex_archive_info* inf
 // local parse + match pass, cross-block pass.  With `timed`, events bracket
 // the three stages.
 static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc, void* d_out, cudaStream_t st,
-                          bool timed) {
+                          bool timed, uint32_t lo = 0, uint32_t hi = 0xffffffffu) {
     const Plan& P = A->plan;
+    if (hi > P.n_blocks) hi = P.n_blocks;
     cudaError_t e;
     const size_t nb = std::max<size_t>(P.n_blocks, 1);
     if ((e = c->streams.ensure(P.scratch_bytes)) != cudaSuccess) return cuda_fail(c, e, "scratch allocation");
@@ -254,15 +261,15 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     J.spans = (SpanRec*)c->spans.p;
     J.total = P.total;
     J.n_blocks = P.n_blocks;
-    J.lo = 0;
-    J.hi = P.n_blocks;
+    J.lo = lo;  // blocks [lo, hi): item i is block lo + i (the whole archive, or one chunk of a pipelined decode)
+    J.hi = hi;
     J.min_match = P.min_match;
     J.item_base = 0;
     J.deps = A->d_deps;
-    J.order = A->d_order;
+    J.order = lo == 0 && hi == P.n_blocks ? A->d_order : nullptr;
     job.arcs = nullptr;
     job.n_arcs = 1;
-    job.n_items = P.n_blocks;
+    job.n_items = hi - lo;
     job.counters = c->counters;
     job.err = c->d_err;
     job.timeout_ns = (uint64_t)c->params.timeout_us * 1000ull;
@@ -270,9 +277,25 @@ static int enqueue_decode(aceapex_ctx* c, aceapex_archive* A, const void* d_arc,
     job.max_lenb = P.max_lenb;
     job.lists[0] = (JobDev::ListEnt*)c->lists.p;
     job.lists[1] = (JobDev::ListEnt*)c->lists.p + std::max<uint64_t>(P.span_slots, 1);
-    if (P.n_blocks == 0) return ACEAPEX_OK;
+    if (hi <= lo) return ACEAPEX_OK;
+    if ((P.flags & kFlagLevels) && !c->params.ignore_levels && c->params.variant != ACEAPEX_VARIANT_PLAIN) {
+        // level-ordered cross-block rounds: one row of the level table per block
+        const uint32_t Lg = std::max<uint32_t>(1, std::min<uint32_t>(P.max_level, kMaxLevel));
+        if ((e = c->lvl_tab.ensure(nb * (Lg + 1) * 4)) != cudaSuccess) return cuda_fail(c, e, "level-table allocation");
+        if ((e = c->lvl_off.ensure((nb * Lg + 2 * Lg + 1) * 4)) != cudaSuccess)
+            return cuda_fail(c, e, "level-offset allocation");
+        if ((e = c->lvl_list.ensure(std::max<uint64_t>(P.span_slots, 1) * sizeof(JobDev::ListEnt))) != cudaSuccess)
+            return cuda_fail(c, e, "level-list allocation");
+        job.lvl_tab = (uint32_t*)c->lvl_tab.p;
+        job.lvl_off = (uint32_t*)c->lvl_off.p;
+        job.lvl_list = (JobDev::ListEnt*)c->lvl_list.p;
+        job.lvl_cap = (uint32_t)std::max<uint64_t>(P.span_slots, 1);
+        job.lvl_min_pieces = lvl_auto_min_pieces(c);
+        job.n_levels = Lg;
+        job.flags |= kJobLevels;
+    }
     LaunchPlan lp;
-    int rc = launch_plan(c, c->params, P.max_tok, P.max_lenb, &lp, 0, true);
+    int rc = launch_plan(c, c->params, P.max_tok, P.max_lenb, &lp, job.flags, true);
     if (rc) return rc;
     if (lp.fused_groups) {
         if ((e = c->ready.ensure(nb * 4)) != cudaSuccess) return cuda_fail(c, e, "ready-flag allocation");
@@ -293,7 +316,8 @@ int acx::launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_t
     lp->grid_plain = c->occ_plain * c->n_sms;
     lp->grid_local = 0;
     if (lp->variant != ACEAPEX_VARIANT_PLAIN) {
-        const size_t lsm = local_smem_bytes(max_tok, max_lenb, (job_flags & kJobNeed) != 0);
+        const size_t lsm =
+            local_smem_bytes(max_tok, max_lenb, (job_flags & kJobNeed) != 0, (job_flags & kJobLevels) != 0);
         if (lsm > 227 * 1024) return fail(c, ACEAPEX_E_CORRUPT, "block too large for the local pass");
         int occ = std::max(1, local_occupancy(lsm));
         if (p.ctas_per_sm) occ = std::min<int>(occ, (int)p.ctas_per_sm);
@@ -301,9 +325,10 @@ int acx::launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_t
     }
     // the fused variant: entropy stage and local pass in one kernel when the
     // job is one whole archive and a CTA holds the tables and a workspace
-    if (whole_single && lp->variant == ACEAPEX_VARIANT_FUSED && !job_flags) {
-        const int G = fused_groups(max_tok, max_lenb);
-        if (G > 0 && fused_occupancy(G, max_tok, max_lenb) >= 1) {
+    if (whole_single && lp->variant == ACEAPEX_VARIANT_FUSED && !(job_flags & (kJobIndex | kJobNeed))) {
+        const bool lvl = (job_flags & kJobLevels) != 0;
+        const int G = fused_groups(max_tok, max_lenb, lvl);
+        if (G > 0 && fused_occupancy(G, max_tok, max_lenb, lvl) >= 1) {
             lp->fused_groups = G;
             lp->grid_fused = c->n_sms;
         }
@@ -343,6 +368,8 @@ int acx::enqueue_job(aceapex_ctx* c, const JobDev& job_in, const LaunchPlan& lp,
         if ((e = launch_local(job, lp.grid_local, st)) != cudaSuccess) return cuda_fail(c, e, "local launch");
     }
     if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    if ((job.flags & kJobLevels) && (e = launch_level_list(job, st)) != cudaSuccess)
+        return cuda_fail(c, e, "level-list launch");
     if (!(job.flags & kJobIndex) && (e = launch_external(job, lp.grid_ext, st)) != cudaSuccess)
         return cuda_fail(c, e, "external launch");
     if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return cuda_fail(c, e, "event");
@@ -418,6 +445,73 @@ int aceapex_decode_all(aceapex_ctx* c, aceapex_archive* A, void* d_out, uint64_t
     return rc;
 }
 
+}  // extern "C"
+
+// The end-to-end decode of an archive held in host memory, as a pipeline over
+// chunks of kHostChunk blocks: the payload bytes of chunk k are uploaded on
+// one stream, its decode runs on the caller's stream as soon as they have
+// landed, and its output is downloaded on a third stream while chunk k + 1
+// decodes.  A chunk's cross-block sources lie in its own or earlier blocks
+// (every source precedes its destination), all final when its decode runs.
+static constexpr uint32_t kHostChunk = 2048;  // blocks (32 MiB of output)
+
+static int host_pipeline(aceapex_ctx* c, aceapex_archive* A, const uint8_t* h_arc, uint64_t arc_len, uint8_t* h_out,
+                         cudaStream_t st) {
+    const Plan& P = A->plan;
+    cudaError_t e;
+    if (!c->s_up) {
+        if ((e = cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&c->s_down, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(c, e, "decode_host: streams");
+    }
+    const uint32_t n_chunks = (P.n_blocks + kHostChunk - 1) / kHostChunk;
+    while (c->pipe_ev.size() < 2 * (size_t)n_chunks + 1) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "decode_host: events");
+        c->pipe_ev.push_back(ev);
+    }
+    cudaEvent_t* ev_up = c->pipe_ev.data();
+    cudaEvent_t* ev_dec = ev_up + n_chunks;
+    cudaEvent_t ev_start = ev_dec[n_chunks];
+    // the upload and download streams start after what the caller queued before
+    if ((e = cudaEventRecord(ev_start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(c->s_up, ev_start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(c->s_down, ev_start, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "decode_host: stream order");
+    for (uint32_t k = 0; k < n_chunks; k++) {
+        const uint32_t lo = k * kHostChunk, hi = std::min(P.n_blocks, lo + kHostChunk);
+        // the chunk's payload bytes (whatever their order in the archive)
+        uint64_t a0 = ~0ull, a1 = 0;
+        for (uint32_t b = lo; b < hi; b++) {
+            const BlockDev& bd = P.blk[b];
+            uint64_t end = 48;
+            for (int q = 0; q < 4; q++) end = std::max<uint64_t>(end, (uint64_t)bd.s_body[q] + bd.s_enc[q]);
+            if (bd.lvl_body) end = std::max<uint64_t>(end, (uint64_t)bd.lvl_body + bd.n_tok);
+            a0 = std::min<uint64_t>(a0, bd.payload);
+            a1 = std::max<uint64_t>(a1, std::min<uint64_t>(arc_len, (bd.payload + end + 15) & ~15ull));
+        }
+        if (a1 > a0 && (e = cudaMemcpyAsync((uint8_t*)c->in_arc.p + a0, h_arc + a0, a1 - a0, cudaMemcpyHostToDevice,
+                                            c->s_up)) != cudaSuccess)
+            return cuda_fail(c, e, "decode_host: archive upload");
+        if ((e = cudaEventRecord(ev_up[k], c->s_up)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ev_up[k], 0)) != cudaSuccess)
+            return cuda_fail(c, e, "decode_host: upload order");
+        const int rc = enqueue_decode(c, A, c->in_arc.p, c->out_buf.p, st, false, lo, hi);
+        if (rc) return rc;
+        if ((e = cudaEventRecord(ev_dec[k], st)) != cudaSuccess || (e = cudaStreamWaitEvent(c->s_down, ev_dec[k], 0)) != cudaSuccess)
+            return cuda_fail(c, e, "decode_host: decode order");
+        const uint64_t o0 = (uint64_t)lo * kBlock, o1 = std::min<uint64_t>(P.total, (uint64_t)hi * kBlock);
+        if ((e = cudaMemcpyAsync(h_out + o0, (uint8_t*)c->out_buf.p + o0, o1 - o0, cudaMemcpyDeviceToHost, c->s_down)) !=
+            cudaSuccess)
+            return cuda_fail(c, e, "decode_host: output download");
+    }
+    // the caller's stream ends after the last download
+    if ((e = cudaEventRecord(ev_up[0], c->s_down)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ev_up[0], 0)) != cudaSuccess)
+        return cuda_fail(c, e, "decode_host: completion order");
+    return ACEAPEX_OK;
+}
+
+extern "C" {
+
 int aceapex_decode_host(aceapex_ctx* c, aceapex_archive* A, const void* h_arc, uint64_t arc_len, void* h_out,
                         uint64_t out_cap, void* stream, aceapex_stats* stats) {
     if (!c || !h_arc || !h_out) return fail(c, ACEAPEX_E_ARG, "decode_host: null argument");
@@ -435,12 +529,8 @@ int aceapex_decode_host(aceapex_ctx* c, aceapex_archive* A, const void* h_arc, u
     if (out_cap < A->plan.total) rc = fail(c, ACEAPEX_E_ARG, "decode_host: output buffer too small");
     else if ((e = c->out_buf.ensure(A->plan.total + 16)) != cudaSuccess) rc = cuda_fail(c, e, "output buffer");
     if (rc == ACEAPEX_OK && stats && (e = cudaEventRecord(c->ev[0], st)) != cudaSuccess) rc = cuda_fail(c, e, "event");
-    if (rc == ACEAPEX_OK && (e = cudaMemcpyAsync(c->in_arc.p, h_arc, arc_len, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        rc = cuda_fail(c, e, "archive upload");
-    if (rc == ACEAPEX_OK) rc = enqueue_decode(c, A, c->in_arc.p, c->out_buf.p, st, false);
-    if (rc == ACEAPEX_OK &&
-        (e = cudaMemcpyAsync(h_out, c->out_buf.p, A->plan.total, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        rc = cuda_fail(c, e, "output download");
+    if (rc == ACEAPEX_OK)
+        rc = host_pipeline(c, A, (const uint8_t*)h_arc, arc_len, (uint8_t*)h_out, st);
     if (rc == ACEAPEX_OK && stats && (e = cudaEventRecord(c->ev[3], st)) != cudaSuccess) rc = cuda_fail(c, e, "event");
     if (rc == ACEAPEX_OK) rc = ctx_read_status(c, st);
     if (rc == ACEAPEX_OK && stats) {

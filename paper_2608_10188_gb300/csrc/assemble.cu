@@ -78,6 +78,7 @@ __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t 
 constexpr int kExtThreads = 1024;  // one CTA per SM: grid barriers stay cheap
 constexpr uint32_t kRound0WaitNs = 4000;  // wait of a round-0 piece for its sources when they are many
 constexpr uint32_t kWaitAllPerLane = 16;   // pieces per grid lane up to which round 0 waits without limit
+constexpr uint32_t kLevelWaitNs = 20000;   // wait of a piece handed out in level order
 
 // Are the bytes a piece reads final?  (period 0: [src, src+len); otherwise the
 // residues phase.. of the period window [src, src+period), one or two ranges.)
@@ -100,7 +101,7 @@ constexpr int kCopyBatch = 8;
 __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec rec, SpanRec* wrec, uint64_t* wdst,
                            int lane) {
     const uint64_t src = (uint64_t)rec.x | ((uint64_t)(rec.y & 0xff) << 32);
-    const uint32_t phase = rec.y >> 8, period = rec.w, o = rec.z & 0xffff, len = rec.z >> 16;
+    const uint32_t phase = (rec.y >> 8) & 0xffff, period = rec.w, o = rec.z & 0xffff, len = rec.z >> 16;
     const bool ready = has && piece_final(L, src, phase, period, len);
     const uint32_t rmask = __ballot_sync(ACX_FULL, ready);
     if (!rmask) return false;
@@ -127,7 +128,7 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec re
                 if ((uint32_t)lane < (r.z >> 16)) {
                     const uint64_t rs = (uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32);
                     const uint32_t rp = r.w;
-                    const uint64_t q = rp ? rs + ((r.y >> 8) + (uint32_t)lane) % rp : rs + lane;
+                    const uint64_t q = rp ? rs + (((r.y >> 8) & 0xffff) + (uint32_t)lane) % rp : rs + lane;
                     v[u >> 2] |= (uint32_t)__ldcg(g + out_off(L, q)) << (8 * (u & 3));
                 }
             }
@@ -226,16 +227,17 @@ __device__ void report_stalled(const JobDev& job, uint32_t in, uint32_t n, uint3
     }
 }
 
-// One pass over work list `in` (n entries) by warps w0, w0 + nw, ...: every
-// piece is attempted once; the unfinished ones go to list `out`.
-__device__ void round_pass(const JobDev& job, uint32_t in, uint32_t out, uint32_t n, uint32_t w0, uint32_t nw,
+// One pass over a list of n pieces (a work list, or a level's segment of the
+// level list) by warps w0, w0 + nw, ...: every piece is attempted once; the
+// unfinished ones go to work list `out`.
+__device__ void round_pass(const JobDev& job, const ListEnt* src, uint32_t out, uint32_t n, uint32_t w0, uint32_t nw,
                            SpanRec* wrec, uint64_t* wdst, ListEnt* sbuf, int lane) {
     uint32_t sn = 0;
     for (uint32_t i0 = w0 * 32; i0 < n; i0 += nw * 32) {
         const uint32_t i = i0 + lane;
         const bool has = i < n;
         ListEnt e{0, 0};
-        if (has) e = job.lists[in][i];
+        if (has) e = src[i];
         // (the lanes' pieces may come from several archives: one archive at a time)
         const int arc_i = has ? find_arc(job, e.y) : -1;
         bool done = false;
@@ -265,7 +267,7 @@ __device__ void solo_rounds(const JobDev& job, uint32_t in, uint32_t n, uint32_t
     const uint32_t warp = threadIdx.x >> 5, nw = kExtThreads / 32;
     for (;;) {
         const uint32_t out = in ^ 1u;
-        round_pass(job, in, out, n, warp, nw, wrec, wdst, sbuf, lane);
+        round_pass(job, job.lists[in], out, n, warp, nw, wrec, wdst, sbuf, lane);
         __syncthreads();  // every append of this round is visible to the CTA
         if (threadIdx.x == 0) {
             n_next = *((volatile uint32_t*)&job.counters[kListCnt + out]);
@@ -289,6 +291,138 @@ __device__ void solo_rounds(const JobDev& job, uint32_t in, uint32_t n, uint32_t
     }
 }
 
+// The level list of a level-ordered decode (whole single-archive jobs with
+// kJobLevels), built between the local pass and the cross-block pass, so
+// that round l walks a contiguous segment with one piece per lane however
+// unevenly the level's pieces are spread over the blocks.
+//   lvl_off[(l-1) * n + b]: offset of item b's level-l pieces in level l's
+//     segment (k_level_scan: one CTA per level, an exclusive scan over items);
+//   lvl_off[Lg * n + l - 1]: level l's total; lvl_off[Lg * n + Lg + l - 1]:
+//     its segment's base (l = 1 .. Lg + 1, the last being the list's length);
+//   lvl_list[base(l) + offset + k] = {span slot, item} of the item's k-th
+//     level-l piece in output order (k_level_fill: one warp per item, reading
+//     each piece's level from its record).
+constexpr int kScanThreads = 1024;
+// Does the cross-block pass hand pieces out in level order?  Only in jobs
+// with level tables, and under the automatic policy only when pieces are
+// many per lane of the pass: with few, output order with waits that last as
+// long as needed resolves the chains at the latency of one copy per level and
+// needs no list.  Every kernel after the local pass reads the same final
+// count, so they all decide alike.
+__device__ __forceinline__ bool use_level_order(const JobDev& job) {
+    if (!job.lvl_tab) return false;
+    if (job.wait_ns != 0) return true;
+    return *((volatile const uint32_t*)&job.counters[kStatPending]) > job.lvl_min_pieces;
+}
+
+// A decode whose local pass timed out left blocks unprocessed, so their level
+// rows, piece counts and records may be stale: the passes after it do nothing.
+__device__ __forceinline__ bool local_pass_timed_out(const JobDev& job) {
+    return *((volatile const int*)job.err) == kErrTimeout;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_level_scan(JobDev job) {
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    if (local_pass_timed_out(job) || !use_level_order(job)) return;
+    const uint32_t l = blockIdx.x + 1, Lg = job.n_levels, n = job.n_items;
+    const uint32_t per = (n + kScanThreads - 1) / kScanThreads;
+    const uint32_t i0 = min(n, threadIdx.x * per), i1 = min(n, i0 + per);
+    auto cnt = [&](uint32_t b) {
+        const uint32_t* row = job.lvl_tab + (uint64_t)(job.one.lo + b) * (Lg + 1);
+        return row[l] - row[l - 1];
+    };
+    uint32_t s = 0;
+    for (uint32_t b = i0; b < i1; b++) s += cnt(b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(ACX_FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+    for (int w = 0; w < kScanThreads / 32; w++) {
+        if (w < warp) pre += wsum[w];
+        tot += wsum[w];
+    }
+    uint32_t off = pre + inc - s;
+    uint32_t* out = job.lvl_off + (uint64_t)(l - 1) * n;
+    for (uint32_t b = i0; b < i1; b++) {
+        out[b] = off;
+        off += cnt(b);
+    }
+    if (threadIdx.x == 0) job.lvl_off[(uint64_t)Lg * n + (l - 1)] = tot;  // level l's total
+}
+
+__global__ void __launch_bounds__(256) k_level_fill(JobDev job) {
+    __shared__ uint32_t base[kMaxLevel + 1];
+    __shared__ uint32_t cursor[8][kMaxLevel + 1];  // per warp: the block's entries written so far, per level
+    if (local_pass_timed_out(job) || !use_level_order(job)) return;
+    const uint32_t Lg = job.n_levels, n = job.n_items;
+    const uint32_t* tot = job.lvl_off + (uint64_t)Lg * n;
+    if (threadIdx.x == 0) {
+        uint32_t c = 0;
+        for (uint32_t l = 1; l <= Lg; l++) {
+            base[l - 1] = c;
+            c += tot[l - 1];
+        }
+        base[Lg] = c;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)  // segment bases, read by the cross-block pass
+        for (uint32_t l = threadIdx.x; l <= Lg; l += blockDim.x)
+            job.lvl_off[(uint64_t)Lg * n + Lg + l] = base[l];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1;
+    uint32_t* cur = cursor[warp];
+    const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t b = blockIdx.x * (blockDim.x >> 5) + warp; b < n; b += nw) {
+        const uint32_t blk = job.one.lo + b;
+        const uint32_t* row = job.lvl_tab + (uint64_t)blk * (Lg + 1);
+        const uint32_t total = row[Lg];
+        if (total == 0) continue;  // no pending pieces
+        const BlockDev& bd = job.one.blk[blk];
+        const uint32_t sb = bd.span_base;
+        if (total > bd.n_tok + kSpanSlack) {  // more pieces than the block's slots: not this decode's row
+            if (lane == 0) set_err(job.err, kErrCorrupt, kStageLimits << 24, blk);
+            continue;
+        }
+        for (uint32_t l = lane; l <= Lg; l += 32) cur[l] = 0;
+        __syncwarp();
+        // the block's pieces in output order, each to its level's segment
+        bool bad = false;
+        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            const bool has = k < total;
+            const uint32_t l = has ? min(max(job.one.spans[sb + k].y >> 24, 1u), Lg) : 0u;
+            const uint32_t peers = __match_any_sync(ACX_FULL, has ? l : 0xffffffffu);
+            if (has) {
+                const uint32_t r = cur[l] + __popc(peers & lt);
+                const uint64_t at = (uint64_t)base[l - 1] + job.lvl_off[(uint64_t)(l - 1) * n + b] + r;
+                if (r >= row[l] - row[l - 1] || at >= job.lvl_cap) bad = true;
+                else job.lvl_list[at] = JobDev::ListEnt{sb + k, b};
+            }
+            __syncwarp();
+            if (has && (peers & lt) == 0) cur[l] += __popc(peers);  // the group's first lane
+            __syncwarp();
+        }
+        if (__any_sync(ACX_FULL, bad) && lane == 0) set_err(job.err, kErrCorrupt, kStageLimits << 24, blk);
+    }
+}
+
+uint32_t lvl_auto_min_pieces_for(int ext_ctas) { return kWaitAllPerLane * (uint32_t)ext_ctas * kExtThreads; }
+
+cudaError_t launch_level_list(const JobDev& job, cudaStream_t st) {
+    k_level_scan<<<job.n_levels, kScanThreads, 0, st>>>(job);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint32_t grid = std::max(1u, std::min(4096u, (job.n_items + 7) / 8));
+    k_level_fill<<<grid, 256, 0, st>>>(job);
+    return cudaGetLastError();
+}
+
 // Cross-block pass in rounds.  Round 0 walks every block's pending spans (in
 // ascending order); each later round walks the spans the previous round could
 // not finish.  A span is attempted once per round and never waited on, so
@@ -308,25 +442,41 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint64_t deadline = gtimer() + job.timeout_ns;
+    if (local_pass_timed_out(job)) return;  // (every CTA returns: no barrier is entered)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const uint64_t t = gtimer();
         job.counters[kTrace] = 0;
         job.counters[kTrace + 1] = (uint32_t)t;
         job.counters[kTrace + 2] = (uint32_t)(t >> 32);
     }
-    // round 0: pieces handed out in ascending order (the warp takes blocks from
-    // a ticket, its idle lanes take the block's next pieces); a lane waits a
-    // short while for sources that are about to be finished by lower pieces,
-    // then defers its piece to the rounds below.
+    // round 0: pieces handed out in order; a lane waits a short while for
+    // sources that lower pieces are about to finish, then defers its piece to
+    // the rounds below.  The order is the output order (warps take blocks from
+    // a ticket, idle lanes take the block's next pieces), or, for a
+    // level-ordered job, the level list's (warps take 32 entries at a time):
+    // every level's pieces come after all pieces of the levels below, so with
+    // true level hints a lane only waits for pieces already handed out (the
+    // paper's waves, without a barrier between them).
     {
+        const bool lv = use_level_order(job);
+        uint32_t n_lv = 0;
+        if (lv) {
+            n_lv = job.lvl_off[(uint64_t)job.n_levels * job.n_items + 2 * job.n_levels];  // the list's length
+            if (n_lv > job.lvl_cap) {
+                if (threadIdx.x == 0) set_err(job.err, kErrCorrupt, kStageLimits << 24, 0);
+                n_lv = 0;
+            }
+        }
         // wait_ns 0 (automatic): in output order, waiting pieces cost little
         // while pieces are few per lane of the grid; with many (long, wide
         // chains, e.g. text) waiting lanes would clog the hand-out, so a piece
-        // that waited kRound0WaitNs goes to the rounds
+        // that waited kRound0WaitNs goes to the rounds; in level order a piece
+        // waits at most kLevelWaitNs
         uint64_t wait_ns;
         if (job.wait_ns == 0) {
             const uint64_t pieces = *((volatile uint32_t*)&job.counters[kStatPending]);
-            wait_ns = pieces <= kWaitAllPerLane * (uint64_t)gridDim.x * blockDim.x ? ~0ull : kRound0WaitNs;
+            wait_ns = lv ? kLevelWaitNs
+                         : pieces <= kWaitAllPerLane * (uint64_t)gridDim.x * blockDim.x ? ~0ull : kRound0WaitNs;
         } else {
             wait_ns = job.wait_ns == 0xffffffffu ? ~0ull : job.wait_ns;
         }
@@ -346,8 +496,15 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             uint32_t idle = __ballot_sync(ACX_FULL, !has);
             while (idle && !exhausted) {
                 if (next >= cnt) {
-                    if (lane == 0) item = atomicAdd(&job.counters[2], 1u);
+                    if (lane == 0) item = atomicAdd(&job.counters[2], lv ? 32u : 1u);
                     item = __shfl_sync(ACX_FULL, item, 0);
+                    if (lv) {  // the next 32 entries of the level list
+                        if (item >= n_lv) { exhausted = true; break; }
+                        base = item;
+                        cnt = min(32u, n_lv - item);
+                        next = 0;
+                        continue;
+                    }
                     if (item >= job.n_items) { exhausted = true; break; }
                     arc = find_arc(job, item);
                     J = load_arc(job, arc);
@@ -362,12 +519,21 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
                 const uint32_t avail = cnt - next;
                 const uint32_t r = __popc(idle & lt_mask);
                 if ((idle >> lane & 1) && r < avail) {
-                    l_span = base + next + r;
+                    if (lv) {
+                        const ListEnt e = job.lvl_list[base + next + r];
+                        l_span = e.x;
+                        l_item = e.y;
+                        l_blk = J.lo + e.y;  // a whole-archive job: item i is block lo + i, in slot lo + i
+                        l_dsl = l_blk;
+                        l_arc = 0;
+                    } else {
+                        l_span = base + next + r;
+                        l_blk = blk;
+                        l_dsl = dsl;
+                        l_item = item;
+                        l_arc = arc;
+                    }
                     rec = J.spans[l_span];
-                    l_blk = blk;
-                    l_dsl = dsl;
-                    l_item = item;
-                    l_arc = arc;
                     t0 = gtimer();
                     has = true;
                 }
@@ -425,14 +591,15 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             if (blockIdx.x == 0) solo_rounds(job, in, n, round, deadline, wrec, wdst, sbuf, lane);
             return;
         }
-        round_pass(job, in, out, n, gwarp, nwarps, wrec, wdst, sbuf, lane);
+        round_pass(job, job.lists[in], out, n, gwarp, nwarps, wrec, wdst, sbuf, lane);
     }
 }
 
-size_t local_smem_bytes(uint32_t T, uint32_t LB, bool need) { return loc_layout(T, LB, need).total; }
+size_t local_smem_bytes(uint32_t T, uint32_t LB, bool need, bool lvl) { return loc_layout(T, LB, need, lvl).total; }
 
 cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st) {
-    const size_t sm = local_smem_bytes(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0);
+    const size_t sm = local_smem_bytes(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0,
+                                       (job.flags & kJobLevels) != 0);
     cudaError_t e = cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // a small job (a seek, a serving tick) needs no more CTAs than ticket runs

@@ -37,6 +37,12 @@ __device__ __forceinline__ void set_err_arc(const JobDev& job, int a, int code, 
     if (job.arc_err && a >= 0) atomicCAS(job.arc_err + a, 0, code);
 }
 
+// Limit of a wait for a bulk copy from global memory into shared memory.
+// Copies complete by themselves, so this bound only guards against a broken
+// device; the caller's timeout (JobDev::timeout_ns) bounds the waits on other
+// work (pieces, barriers, published blocks).
+constexpr uint64_t kCopyWaitNs = 2000000000ull;
+
 __device__ __forceinline__ uint64_t gtimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -173,7 +179,8 @@ __device__ __forceinline__ uint32_t range_mask(uint32_t w, uint32_t s, uint32_t 
 // Cut a pending match (destination offset o in its block, absolute source src,
 // length ml, distance d = destination - source) into pieces of at most kPiece
 // bytes at slots out[0..); returns the number of pieces.
-__device__ __forceinline__ uint32_t emit_pieces(SpanRec* out, uint32_t o, uint64_t src, uint32_t ml, uint64_t d) {
+__device__ __forceinline__ uint32_t emit_pieces(SpanRec* out, uint32_t o, uint64_t src, uint32_t ml, uint64_t d,
+                                                uint32_t level = 0) {
     uint32_t k = 0;
     for (uint32_t q = 0; q < ml; q += kPiece, k++) {
         const uint32_t len = ml - q < kPiece ? ml - q : kPiece;
@@ -186,7 +193,8 @@ __device__ __forceinline__ uint32_t emit_pieces(SpanRec* out, uint32_t o, uint64
             period = (uint32_t)d;
             phase = q % period;
         }
-        out[k] = SpanRec{(uint32_t)s, (uint32_t)(s >> 32) | (phase << 8), (o + q) | (len << 16), period};
+        out[k] = SpanRec{(uint32_t)s, (uint32_t)(s >> 32) | (phase << 8) | (level << 24), (o + q) | (len << 16),
+                         period};
     }
     return k;
 }

@@ -37,14 +37,14 @@ struct FusedLayout {
 
 // Shared memory of a fused CTA with G local groups whose workspaces hold
 // blocks of up to T tokens and LB length bytes.
-__host__ __device__ inline FusedLayout fused_layout(uint32_t T, uint32_t LB, int G) {
+__host__ __device__ inline FusedLayout fused_layout(uint32_t T, uint32_t LB, int G, bool lvl) {
     FusedLayout F;
     F.tab = 0;                                           // 4 x 4096 decode entries
     F.ring = 4 * kM * 4;                                 // (R + 1) x 2 KiB: R rings, 2 KiB-aligned inside
     F.bar = F.ring + (kFusedRansWarps + 1) * 2 * kRingWords;  // R x (kSlots + 1) mbarriers
     const uint32_t end = F.bar + kFusedRansWarps * (kSlots + 1) * 8;
     F.loc = (end + 127) & ~127u;
-    F.loc_stride = loc_layout(T, LB, false).total;       // 128-byte multiple
+    F.loc_stride = loc_layout(T, LB, false, lvl).total;  // 128-byte multiple
     F.total = F.loc + (uint32_t)G * F.loc_stride;
     return F;
 }
@@ -55,7 +55,7 @@ __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
 
 __global__ void __launch_bounds__(kFusedMaxThreads, 1) k_fused(JobDev job, int G) {
     extern __shared__ __align__(128) uint8_t sm[];
-    const FusedLayout F = fused_layout(job.max_tok, job.max_lenb, G);
+    const FusedLayout F = fused_layout(job.max_tok, job.max_lenb, G, (job.flags & kJobLevels) != 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const ArcJob& J = job.one;
     {
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1) k_fused(JobDev job, int G
     if (warp < kFusedRansWarps && lane <= kSlots) mbar_init(&bars[lane], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
-    const uint64_t deadline = gtimer() + job.timeout_ns;
+    const uint64_t deadline = gtimer() + kCopyWaitNs;  // the entropy warps wait only for their copies
     if (warp < kFusedRansWarps) {
         const uint32_t ring_s =
             ((smem_u32(sm + F.ring) + kRingMask) & ~(uint32_t)kRingMask) + (uint32_t)warp * (2 * kRingWords);
@@ -98,14 +98,14 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1) k_fused(JobDev job, int G
     local_worker(job, sm + F.loc + g * F.loc_stride, 1 + g, threadIdx.x - 32 * (kFusedRansWarps + kLocWarps * g));
 }
 
-int fused_groups(uint32_t max_tok, uint32_t max_lenb) {
+int fused_groups(uint32_t max_tok, uint32_t max_lenb, bool lvl) {
     for (int G = kFusedMaxGroups; G >= 1; G--)
-        if (fused_layout(max_tok, max_lenb, G).total <= 227u * 1024) return G;
+        if (fused_layout(max_tok, max_lenb, G, lvl).total <= 227u * 1024) return G;
     return 0;
 }
 
 cudaError_t launch_fused(const JobDev& job, int G, int grid, cudaStream_t st) {
-    const FusedLayout F = fused_layout(job.max_tok, job.max_lenb, G);
+    const FusedLayout F = fused_layout(job.max_tok, job.max_lenb, G, (job.flags & kJobLevels) != 0);
     cudaError_t e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F.total);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg{};
@@ -121,8 +121,8 @@ cudaError_t launch_fused(const JobDev& job, int G, int grid, cudaStream_t st) {
     return cudaLaunchKernelEx(&cfg, k_fused, job, G);
 }
 
-int fused_occupancy(int G, uint32_t max_tok, uint32_t max_lenb) {
-    const FusedLayout F = fused_layout(max_tok, max_lenb, G);
+int fused_occupancy(int G, uint32_t max_tok, uint32_t max_lenb, bool lvl) {
+    const FusedLayout F = fused_layout(max_tok, max_lenb, G, lvl);
     if (cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F.total) != cudaSuccess)
         return 0;
     int n = 0;

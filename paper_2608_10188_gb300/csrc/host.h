@@ -69,9 +69,12 @@ struct aceapex_ctx {
     acx::DevBuf streams, npend, pmap, spans, lists, arcs, in_arc, out_buf;
     acx::DevBuf slot_out, items, need;   // range decodes: decoded closure blocks, work items, wanted bytes
     acx::DevBuf ready;                   // fused decodes: per block, its streams are decoded
+    acx::DevBuf lvl_tab, lvl_off, lvl_list;  // level-ordered decodes: per block level counts, the level list
     uint32_t* counters = nullptr;  // device
     int* d_err = nullptr;          // device
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t s_up = nullptr, s_down = nullptr;  // decode_host: upload and download streams
+    std::vector<cudaEvent_t> pipe_ev;              // decode_host: per chunk, uploaded and decoded
     int occ_rans = 0, occ_ext = 0, occ_plain = 0;
 };
 
@@ -114,6 +117,7 @@ struct LaunchPlan {
 // which the default variant may do with the fused entropy + local kernel.
 int launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_tok, uint32_t max_lenb, LaunchPlan* lp,
                 uint32_t job_flags = 0, bool whole_single = false);
+inline uint32_t lvl_auto_min_pieces(const aceapex_ctx* c) { return lvl_auto_min_pieces_for(c->occ_ext * c->n_sms); }
 // Synchronise st and return (and clear) the context's device error status.
 int ctx_read_status(aceapex_ctx* c, cudaStream_t st);
 

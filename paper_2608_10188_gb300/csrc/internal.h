@@ -34,14 +34,18 @@ struct BlockDev {
     uint32_t span_base;    // first pending-span slot of the block (n_tok + kSpanSlack slots per block)
     uint32_t dep_off;      // the block's dependency list: deps[dep_off, dep_off + n_deps) (archives with lists)
     uint32_t n_deps;
+    uint32_t lvl_body;     // payload offset of the block's level body (archives with levels), else 0
+    uint32_t pad[3];
 };
 static_assert(sizeof(BlockDev) % 16 == 0, "BlockDev alignment");
 
 // A pending piece: at most kPiece bytes of a match whose source chain leaves
 // its block, left for the cross-block pass.  Long matches are cut into pieces
 // so every piece is one lane's small copy.
-//   x = source bits 0..31, y = source bits 32..39 | phase << 8,
+//   x = source bits 0..31, y = source bits 32..39 | phase << 8 | level << 24,
 //   z = destination offset in the block | length << 16, w = period.
+// (phase < period < 16384; level: the token's level byte in level-ordered
+// jobs, a scheduling hint, else 0.)
 // period 0: byte j comes from source + j; otherwise from
 // source + ((phase + j) mod period), source being the start of the match's
 // period window (the periodic fill of a self-overlapping match).
@@ -123,6 +127,9 @@ constexpr uint32_t kJobIndex = 1;
 // undefined) and cuts pieces only for wanted matches, so a block's sources
 // outside its wanted bytes' chains are never read.
 constexpr uint32_t kJobNeed = 2;
+// kJobLevels: the job's archive has level bodies and the local pass sorts
+// each block's pending pieces by level (JobDev::lvl_tab).
+constexpr uint32_t kJobLevels = 4;
 
 struct JobDev {
     ArcJob one;               // the archive when arcs == nullptr
@@ -145,6 +152,23 @@ struct JobDev {
     };
     ListEnt* lists[2];        // cross-block work lists
     uint32_t* ready;          // fused decodes: per item, nonzero once its streams are decoded (else nullptr)
+    // Level-ordered cross-block rounds (whole single-archive jobs over an
+    // archive with level bodies, else nullptr / 0): the local pass writes
+    // each block's pending pieces sorted by level (a piece's level is its
+    // token's, at least 1) and lvl_tab[b * (n_levels + 1) + l] = the number
+    // of the block's pieces of level <= l; cross-block round l takes level l.
+    uint32_t* lvl_tab;
+    uint32_t n_levels;        // highest level of the archive (<= kMaxLevel)
+    // The level list (k_level_scan, k_level_fill): level l's pieces at
+    // lvl_list[base(l) ..], base(l) = lvl_off[Lg * n_items + Lg + l - 1]
+    // (Lg = n_levels); lvl_off also holds per level and item the item's offset
+    // in its level ((l-1) * n_items + item) and the level totals
+    // (Lg * n_items + l - 1): Lg * n_items + 2 * Lg + 1 words.
+    uint32_t* lvl_off;
+    ListEnt* lvl_list;
+    uint32_t lvl_cap;         // entries lvl_list holds
+    uint32_t lvl_min_pieces;  // automatic policy (wait_ns 0): level order only above this many pending pieces
 };
+constexpr uint32_t kMaxLevel = 255;
 
 }  // namespace acx

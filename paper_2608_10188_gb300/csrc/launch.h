@@ -17,15 +17,21 @@ cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st);
 // Cooperative launch (every CTA resident); recorded as a cooperative kernel
 // node when the stream is being captured into a graph.
 cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st);
+// The level list of a level-ordered job (kJobLevels): a per-level scan over
+// the items, then one warp per item writes its pieces' entries.
+cudaError_t launch_level_list(const JobDev& job, cudaStream_t st);
+// Pending pieces above which the automatic policy takes a level-ordered job's
+// pieces in level order: 16 per thread of the cross-block pass's grid.
+uint32_t lvl_auto_min_pieces_for(int ext_ctas);
 cudaError_t launch_plain(const JobDev& job, int grid, cudaStream_t st);
 // Fused entropy stage + local pass of a whole single-archive job (job.ready
 // set, its flags cleared): G local groups per CTA, one CTA per SM
 // (cooperative).  fused_groups: the most groups whose workspaces fit a CTA
 // for blocks of max_tok tokens and max_lenb length bytes (0: none fits).
 cudaError_t launch_fused(const JobDev& job, int G, int grid, cudaStream_t st);
-int fused_groups(uint32_t max_tok, uint32_t max_lenb);
-int fused_occupancy(int G, uint32_t max_tok, uint32_t max_lenb);
-size_t local_smem_bytes(uint32_t T, uint32_t LB, bool need = false);
+int fused_groups(uint32_t max_tok, uint32_t max_lenb, bool lvl);
+int fused_occupancy(int G, uint32_t max_tok, uint32_t max_lenb, bool lvl);
+size_t local_smem_bytes(uint32_t T, uint32_t LB, bool need = false, bool lvl = false);
 int rans_occupancy();
 // Grid of a persistent kernel for a job that can use `need` CTAs at most:
 // no more than `full`, and no fewer than one per SM, so that a mid-size job

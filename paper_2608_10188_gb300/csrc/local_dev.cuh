@@ -11,10 +11,14 @@ constexpr int kLocWarps = kLocThreads / 32;
 constexpr uint64_t kRefTag = 1ull << 63;  // history map entry "copy input entry k"
 
 struct LocLayout {
-    uint32_t out, pend, tsrc, tpos, tll, tml, tlit, tcmd, tstat, lenb, soff, slit, scan, bar, misc, need, total;
+    uint32_t out, pend, tsrc, tpos, tll, tml, tlit, tcmd, tstat, lenb, soff, slit, scan, bar, misc, need, tlvl, tlvk,
+        lhist, total;
 };
 
-__host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB, bool need) {
+// Shared-memory workspace of one local group for blocks of up to T tokens
+// and LB length bytes; need: jobs with wanted-byte intervals; lvl: jobs that
+// sort pieces by level (the token levels and a level histogram).
+__host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB, bool need, bool lvl = false) {
     LocLayout L;
     uint32_t o = 0;
     auto take = [&](uint32_t bytes, uint32_t align) {
@@ -40,6 +44,9 @@ __host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB, bool ne
     L.bar = take(8, 8);
     L.misc = take(64, 16);
     L.need = need ? take(kBlock / 8, 16) : 0;  // wanted-byte bitmap (jobs with kJobNeed)
+    L.tlvl = lvl ? take(T16 + 16, 16) : 0;       // token levels as staged (jobs with kJobLevels)
+    L.tlvk = lvl ? take(T16, 16) : 0;            // the block's token levels, kept past the next block's staging
+    L.lhist = lvl ? take(4 * (kMaxLevel + 2), 16) : 0;
     L.total = (o + 127) & ~127u;
     return L;
 }
@@ -185,7 +192,7 @@ __device__ __forceinline__ void copy_run(uint8_t* __restrict__ sout, const uint8
 // padded) into the stream buffers (one thread).  Nothing is issued for a
 // block beyond the job's shared-memory limits (the caller treats it as bad).
 __device__ __forceinline__ void stage_streams(const JobDev& job, uint32_t item, uint8_t* tcmd, uint8_t* lenb, uint8_t* soff,
-                              uint8_t* slit, uint64_t* bar) {
+                              uint8_t* slit, uint8_t* tlvl, uint64_t* bar) {
     const ArcJob J = load_arc(job, find_arc(job, item));
     const ItemRef ir = item_ref(J, item - J.item_base);
     const BlockDev& bd = J.blk[ir.blk];
@@ -194,10 +201,13 @@ __device__ __forceinline__ void stage_streams(const JobDev& job, uint32_t item, 
     const uint8_t* scr = J.scratch + ir.scratch;
     const uint32_t sz[4] = {(n + 15) & ~15u, (LB + 15) & ~15u, (5 * n_new + 15) & ~15u, (n_lit + 15) & ~15u};
     uint8_t* dsts[4] = {tcmd, lenb, soff, slit};
+    // the level body (stored in the payload, 16-aligned and padded) beside them
+    const uint32_t lsz = (job.flags & kJobLevels) && bd.lvl_body ? sz[0] : 0;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic use of the buffers
-    mbar_arrive_tx(bar, sz[0] + sz[1] + sz[2] + sz[3]);
+    mbar_arrive_tx(bar, sz[0] + sz[1] + sz[2] + sz[3] + lsz);
     for (int q = 0; q < 4; q++)
         if (sz[q]) tma_load_1d(dsts[q], scr + bd.s_off[q], sz[q], bar);
+    if (lsz) tma_load_1d(tlvl, J.arc + bd.payload + bd.lvl_body, lsz, bar);
 }
 
 // Item -> ticket order of the local pass: tickets are items, except in a
@@ -225,7 +235,11 @@ __device__ __forceinline__ bool wait_ready(const uint32_t* ready, uint32_t item,
 // group of a fused CTA) over the job's tickets, with its workspace at sm and
 // named barrier bid; tid is the thread's index in its group.
 __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uint32_t bid, int tid) {
-    const LocLayout L = loc_layout(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0);
+    const bool lvl = (job.flags & kJobLevels) != 0;
+    const LocLayout L = loc_layout(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0, lvl);
+    uint8_t* tlvl = sm + L.tlvl;                                      // valid in kJobLevels jobs
+    uint8_t* tlvk = sm + L.tlvk;
+    uint32_t* lhist = reinterpret_cast<uint32_t*>(sm + L.lhist);
     uint8_t* sout = sm + L.out;
     uint32_t* need = reinterpret_cast<uint32_t*>(sm + L.need);  // valid in kJobNeed jobs
     uint32_t* pend = reinterpret_cast<uint32_t*>(sm + L.pend);
@@ -243,7 +257,8 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
     volatile uint32_t* misc = reinterpret_cast<volatile uint32_t*>(sm + L.misc);
     const int lane = tid & 31, warp = tid >> 5;
-    const uint64_t deadline = gtimer() + job.timeout_ns;
+    const uint64_t deadline = gtimer() + job.timeout_ns;       // waits on published blocks (fused decodes)
+    const uint64_t copy_deadline = gtimer() + kCopyWaitNs;    // waits on this group's own bulk copies
     if (tid == 0) mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     grp_sync(bid);
@@ -287,7 +302,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
         // ---- stage the four decoded streams with 1-D TMA bulk copies (unless
         //      they were prefetched during the previous block) ----
         if (!bad && tid == 0 && !prefetched && (!job.ready || wait_ready(job.ready, item, deadline)))
-            stage_streams(job, item, tcmd, lenb, soff, slit, bar);
+            stage_streams(job, item, tcmd, lenb, soff, slit, tlvl, bar);
         for (uint32_t i = tid; i < kBlock / 32; i += kLocThreads) pend[i] = 0;
         if (tid == 0) misc[1] = 0;
         // wanted bytes of this item (all when it names none)
@@ -307,7 +322,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
         if (!bad) {
             uint32_t spins = 0;
             while (!mbar_try_wait(bar, phase & 1))
-                if ((++spins & 1023) == 0 && gtimer() > deadline) { timed_out = true; break; }
+                if ((++spins & 1023) == 0 && gtimer() > copy_deadline) { timed_out = true; break; }
             phase++;
         }
         if (grp_or(bid, timed_out)) {
@@ -501,6 +516,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
                     st = tsrc[i] >= B ? 1 : 2;
                 }
                 tstat[i] = st;
+                if (lvl) tlvk[i] = tlvl[i];  // the staging buffer takes the next block's levels below
             }
             grp_sync(bid);
             // ---- the stream buffers are free from here on: start the next item's
@@ -518,7 +534,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
                 const bool go = pf_item < job.n_items && (!job.ready || ld_acquire_u32(job.ready + pf_item) != 0);
                 if (go) {
                     if (job.ready) asm volatile("fence.proxy.async.global;" ::: "memory");
-                    stage_streams(job, pf_item, tcmd, lenb, soff, slit, bar);
+                    stage_streams(job, pf_item, tcmd, lenb, soff, slit, tlvl, bar);
                 }
                 misc[2] = go;
             }
@@ -588,17 +604,51 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
             block_scan3(v3, tot3, scanbuf, bid, tid);
             npend = tot3[0];
             pbytes = tot3[1];
-            uint32_t k = v3[0];
-            for (uint32_t i = i0; i < i1; i++) {
-                if (!tstat[i]) continue;
-                const uint32_t o = tpos[i] + tll[i];
-                k += emit_pieces(J.spans + ir.span_base + k, o, tsrc[i], tml[i], B + o - tsrc[i]);
+            if (lvl) {
+                // the block's row of the level table (pieces of level <= l,
+                // a piece's level being its token's level byte clamped to
+                // [1, n_levels]); the pieces themselves stay in output order
+                // and carry their level, and the level list is built from
+                // them (k_level_fill)
+                const uint32_t Lg = job.n_levels;
+                for (uint32_t l = tid; l <= Lg; l += kLocThreads) lhist[l] = 0;
+                grp_sync(bid);
+                for (uint32_t i = i0; i < i1; i++)
+                    if (tstat[i]) atomicAdd(&lhist[min(max((uint32_t)tlvk[i], 1u), Lg)], pieces_of(tml[i]));
+                grp_sync(bid);
+                if (warp == 0) {
+                    uint32_t carry = 0;
+                    uint32_t* row = job.lvl_tab + (uint64_t)ir.slot * (Lg + 1);
+                    for (uint32_t l0 = 0; l0 <= Lg; l0 += 32) {
+                        const uint32_t l = l0 + lane;
+                        uint32_t inc = l <= Lg ? lhist[l] : 0;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t y = __shfl_up_sync(ACX_FULL, inc, o);
+                            if (lane >= o) inc += y;
+                        }
+                        if (l <= Lg) row[l] = carry + inc;
+                        carry += __shfl_sync(ACX_FULL, inc, 31);
+                    }
+                }
+            }
+            {
+                uint32_t k = v3[0];
+                for (uint32_t i = i0; i < i1; i++) {
+                    if (!tstat[i]) continue;
+                    const uint32_t o = tpos[i] + tll[i];
+                    const uint32_t lv = lvl ? min(max((uint32_t)tlvk[i], 1u), job.n_levels) : 0u;
+                    k += emit_pieces(J.spans + ir.span_base + k, o, tsrc[i], tml[i], B + o - tsrc[i], lv);
+                }
             }
         }
         grp_sync(bid);
         if (bad) {
             if (tid == 0) set_err_arc(job, a, kErrCorrupt, stage << 24, b);
             npend = 0;
+            if (lvl)  // an empty row: the level rounds take nothing from this block
+                for (uint32_t l = tid; l <= job.n_levels; l += kLocThreads)
+                    job.lvl_tab[(uint64_t)ir.slot * (job.n_levels + 1) + l] = 0;
         }
         // ---- write the block (pending bytes are filled by the cross-block pass) ----
         uint8_t* gout = J.out + (uint64_t)ir.slot * kBlock;

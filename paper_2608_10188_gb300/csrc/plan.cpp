@@ -7,6 +7,7 @@
 // entries of the four global frequency tables.
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -66,6 +67,7 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why) {
     P->deps.clear();
     P->max_tok = 1;
     P->max_lenb = 1;
+    P->max_level = 0;
     P->tokens = 0;
     uint64_t scratch = 0;
     for (uint32_t b = 0; b < P->n_blocks; b++) {
@@ -126,6 +128,8 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why) {
         if (has_levels) {  // the level body: n_tok stored bytes after the four stream bodies
             if (off + n_tok > plen) return fail("level body out of bounds");
             P->lvl_off[b] = (uint32_t)off;
+            bd.lvl_body = (uint32_t)off;
+            for (uint32_t k = 0; k < n_tok; k++) P->max_level = std::max<uint32_t>(P->max_level, pay[off + k]);
             off = up16(off + n_tok);
         }
         if (off != plen) return fail("payload length mismatch");

@@ -21,6 +21,7 @@ struct Plan {
     // Level bodies (flags bit1: one cross-block level per token, a scheduling
     // hint): block b's at payload offset lvl_off[b]; empty without them.
     std::vector<uint32_t> lvl_off;
+    uint32_t max_level = 0;       // highest level byte of the level bodies (0 without them)
 };
 constexpr uint32_t kFlagLevels = 2;
 

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
         S.arc = -1;
     }
     __syncthreads();
-    const uint64_t deadline = gtimer() + job.timeout_ns;
+    const uint64_t deadline = gtimer() + kCopyWaitNs;  // the entropy stage waits only for its copies
     uint32_t seq = 0, sphase = 0;
     uint32_t* tickets = job.counters + 3;
     const uint32_t ring_s = ring_addr(S, warp);

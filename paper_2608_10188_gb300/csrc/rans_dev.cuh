@@ -356,7 +356,8 @@ __device__ __forceinline__ void rans_block(const JobDev& job, int a, const ArcJo
         }
     }
     if (!ok && lane == 0) {
-        set_err_arc(job, a, kErrCorrupt, (kStageRans << 24) | fs, b);
+        // a stream fails on a format violation, or on a copy that never landed
+        set_err_arc(job, a, gtimer() > deadline ? kErrTimeout : kErrCorrupt, (kStageRans << 24) | fs, b);
         if (job.flags & kJobIndex) J.npend[ir.slot] = 1;  // per-item status of a parse-only job
     }
 }

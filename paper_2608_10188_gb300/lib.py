@@ -40,7 +40,8 @@ class EncParams(ctypes.Structure):
 
 class DecParams(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("timeout_us", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("rans_ctas_per_sm", ctypes.c_uint32), ("queue_chunk", ctypes.c_uint32), ("wait_ns", ctypes.c_uint32)]
+                ("rans_ctas_per_sm", ctypes.c_uint32), ("queue_chunk", ctypes.c_uint32), ("wait_ns", ctypes.c_uint32),
+                ("ignore_levels", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -217,17 +218,19 @@ class Context:
     """aceapex_ctx on one CUDA device."""
 
     def __init__(self, device: int = 0, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0,
-                 rans_ctas_per_sm: int = 0, queue_chunk: int = 0, wait_ns: int = 0):
+                 rans_ctas_per_sm: int = 0, queue_chunk: int = 0, wait_ns: int = 0, ignore_levels: bool = False):
         L = load()
         self._L = L
-        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm, queue_chunk, wait_ns)
+        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm, queue_chunk, wait_ns,
+                                int(ignore_levels))
         h = ctypes.c_void_p()
         _check(L.aceapex_ctx_create(device, ctypes.byref(self.params), ctypes.byref(h)), None, "ctx_create")
         self.h = h
 
     def set_params(self, variant: int = VARIANT_FAST, timeout_us: int = 0, ctas_per_sm: int = 0,
-                   rans_ctas_per_sm: int = 0, queue_chunk: int = 0, wait_ns: int = 0):
-        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm, queue_chunk, wait_ns)
+                   rans_ctas_per_sm: int = 0, queue_chunk: int = 0, wait_ns: int = 0, ignore_levels: bool = False):
+        self.params = DecParams(variant, timeout_us, ctas_per_sm, rans_ctas_per_sm, queue_chunk, wait_ns,
+                                int(ignore_levels))
         _check(self._L.aceapex_ctx_set_params(self.h, ctypes.byref(self.params)), self.h, "set_params")
 
     def close(self):

@@ -111,6 +111,69 @@ def test_level_bodies_do_not_change_the_decode(acx, ctx, dna4m, text4m, kind, va
     assert np.array_equal(out, want)
 
 
+def _rewrite_levels(arc, f):
+    """The archive with every block's level body replaced by f(levels, block)
+    (the level bytes are scheduling hints: the decoded bytes must not change)."""
+    import struct
+    a = bytearray(arc)
+    nb = struct.unpack_from("<I", a, 24)[0]
+    off_idx = struct.unpack_from("<Q", a, 40)[0]
+    for b in range(nb):
+        poff, plen, ntok = struct.unpack_from("<QII", a, off_idx + 40 * b)
+        off = 48
+        for s_ in range(4):
+            enc = struct.unpack_from("<I", a, poff + 12 * s_ + 4)[0]
+            off = (off + enc + 15) & ~15
+        lv = np.frombuffer(bytes(a[poff + off:poff + off + ntok]), np.uint8)
+        a[poff + off:poff + off + ntok] = np.asarray(f(lv, b), np.uint8).tobytes()
+    return bytes(a)
+
+
+@pytest.mark.parametrize("kind", ["dna", "text"])
+def test_level_rounds_with_true_and_wrong_hints(acx, dna4m, text4m, kind):
+    """Level-ordered cross-block pass (paper, Depth Does Not Govern Latency:
+    the waves): pieces are handed out level by level; with hints that are too
+    low, zero, too high or random the pieces that are not ready in time go to
+    the work lists and the decode is still the oracle's, byte for byte."""
+    from gpu_util import gpu_decode
+    # 8 MiB: with one local CTA per SM every CTA takes several blocks, so the
+    # next block's streams are staged while a block still sorts its pieces
+    data = synth.corpus(kind, (8 << 20) + 999, 12)
+    arc = acx.encode(data, levels=True, max_depth=0xFFFFFFFF)
+    rng = np.random.default_rng(3)
+    hints = {"true": lambda lv, b: lv, "lowered": lambda lv, b: np.maximum(lv.astype(int) - 1, 0),
+             "zero": lambda lv, b: np.zeros_like(lv), "raised": lambda lv, b: np.minimum(lv.astype(int) + 3, 255),
+             "random": lambda lv, b: rng.integers(0, 8, lv.size), "inverted": lambda lv, b: lv.max(initial=0) - lv}
+    # an explicit round-0 wait: level order whatever the pieces per lane
+    ctx = acx.Context(0, timeout_us=2_000_000, ctas_per_sm=1, wait_ns=20_000)
+    try:
+        for name, f in hints.items():
+            a2 = _rewrite_levels(arc, f)
+            want = oracle.decode(a2)
+            assert np.array_equal(want, data), name
+            rc, out = gpu_decode(ctx, a2)
+            assert rc == 0, (name, ctx.last_error())
+            assert np.array_equal(out, want), name
+        # true hints, pieces waiting without limit: in level order the lowest
+        # unfinished piece always has final sources, so the first round
+        # finishes every piece (scrambled levels could stall here instead)
+        strict = acx.Context(0, timeout_us=500_000, ctas_per_sm=1, wait_ns=0xFFFFFFFF)
+        try:
+            rc, out, st = gpu_decode(strict, arc, stats=True)
+            assert rc == 0, strict.last_error()
+            assert np.array_equal(out, data)
+            assert st["pending_spans"] > 0 and st["wait_polls"] == 0, st
+        finally:
+            strict.close()
+        # the level bodies ignored: the round-0 hand-out
+        ctx.set_params(ignore_levels=True, timeout_us=2_000_000, ctas_per_sm=1)
+        rc, out = gpu_decode(ctx, arc)
+        assert rc == 0 and np.array_equal(out, data)
+    finally:
+        ctx.close()
+
+
+
 @pytest.mark.parametrize("variant", [FAST, PLAIN])
 def test_edge_sizes_and_ragged_tail(acx, ctx, variant):
     from gpu_util import gpu_decode
