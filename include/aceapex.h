@@ -108,7 +108,8 @@ typedef struct {
                              short of timeout_us (pieces are handed out in output order, so the lowest
                              unfinished one always has final sources and the first round finishes them all);
                              0 = automatic: no limit while the pending pieces are at most 16 per thread of the
-                             pass's grid, else 4000 (many pieces with long chains would clog the hand-out) */
+                             pass's grid and 256 per block, else 4000 (many pieces with long chains would clog
+                             the hand-out), or, for an archive with level bodies, level order with 20000 */
     uint32_t ignore_levels; /* 0: a whole-archive decode of an archive with level bodies (flags bit1) takes
                                the cross-block matches level by level (paper, "Depth Does Not Govern
                                Latency": one round per wave, every piece attempted once, a piece whose
@@ -359,11 +360,12 @@ int aceapex_server_destroy(aceapex_server* server);
  * the output to h_out (host pointer, out_cap >= total size).  Device buffers
  * are context scratch.  `arc` must be an archive opened from the same bytes
  * (its plan is reused); pass NULL to open a temporary one.  The call is a
- * pipeline over chunks of 2048 blocks: a chunk's payload bytes go up on a
- * context stream, the chunk decodes on `stream` once they have landed (its
- * sources lie in its own or earlier blocks), and its output comes down on a
- * second context stream while the next chunk decodes.  The call returns when
- * the last bytes are in h_out; work queued on `stream` before it runs first.
+ * pipeline over chunks of blocks (512, then 1536, then 4096 each): a chunk's
+ * payload bytes go up on a context stream, the chunk decodes on `stream` once
+ * they have landed (its sources lie in its own or earlier blocks), and its
+ * output comes down on a second context stream while the next chunk decodes.
+ * The call returns when the last bytes are in h_out; work queued on `stream`
+ * before it runs first.
  */
 int aceapex_decode_host(aceapex_ctx* ctx, aceapex_archive* arc, const void* h_arc, uint64_t arc_len,
                         void* h_out, uint64_t out_cap, void* stream, aceapex_stats* stats);

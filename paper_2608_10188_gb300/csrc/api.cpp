@@ -448,12 +448,18 @@ int aceapex_decode_all(aceapex_ctx* c, aceapex_archive* A, void* d_out, uint64_t
 }  // extern "C"
 
 // The end-to-end decode of an archive held in host memory, as a pipeline over
-// chunks of kHostChunk blocks: the payload bytes of chunk k are uploaded on
-// one stream, its decode runs on the caller's stream as soon as they have
-// landed, and its output is downloaded on a third stream while chunk k + 1
-// decodes.  A chunk's cross-block sources lie in its own or earlier blocks
-// (every source precedes its destination), all final when its decode runs.
-static constexpr uint32_t kHostChunk = 2048;  // blocks (32 MiB of output)
+// chunks of blocks: the payload bytes of chunk k are uploaded on one stream,
+// its decode runs on the caller's stream as soon as they have landed, and its
+// output is downloaded on a third stream while chunk k + 1 decodes.  A
+// chunk's cross-block sources lie in its own or earlier blocks (every source
+// precedes its destination), all final when its decode runs.  The download
+// is the slowest leg (the host link carries about 190 GB/s, the decode about
+// 280), so the first chunk is small, to start it early, and the later ones
+// large, to keep the per-launch costs of the decode low.
+static uint32_t host_chunk_end(uint32_t lo, uint32_t n_blocks) {
+    const uint32_t hi = lo == 0 ? 512 : lo < 2048 ? 2048 : lo + 4096;
+    return std::min(hi, n_blocks);
+}
 
 static int host_pipeline(aceapex_ctx* c, aceapex_archive* A, const uint8_t* h_arc, uint64_t arc_len, uint8_t* h_out,
                          cudaStream_t st) {
@@ -464,7 +470,8 @@ static int host_pipeline(aceapex_ctx* c, aceapex_archive* A, const uint8_t* h_ar
             (e = cudaStreamCreateWithFlags(&c->s_down, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(c, e, "decode_host: streams");
     }
-    const uint32_t n_chunks = (P.n_blocks + kHostChunk - 1) / kHostChunk;
+    uint32_t n_chunks = 0;
+    for (uint32_t lo = 0; lo < P.n_blocks; lo = host_chunk_end(lo, P.n_blocks)) n_chunks++;
     while (c->pipe_ev.size() < 2 * (size_t)n_chunks + 1) {
         cudaEvent_t ev;
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
@@ -478,8 +485,8 @@ static int host_pipeline(aceapex_ctx* c, aceapex_archive* A, const uint8_t* h_ar
     if ((e = cudaEventRecord(ev_start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(c->s_up, ev_start, 0)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(c->s_down, ev_start, 0)) != cudaSuccess)
         return cuda_fail(c, e, "decode_host: stream order");
-    for (uint32_t k = 0; k < n_chunks; k++) {
-        const uint32_t lo = k * kHostChunk, hi = std::min(P.n_blocks, lo + kHostChunk);
+    for (uint32_t k = 0, lo = 0; k < n_chunks; k++, lo = host_chunk_end(lo, P.n_blocks)) {
+        const uint32_t hi = host_chunk_end(lo, P.n_blocks);
         // the chunk's payload bytes (whatever their order in the archive)
         uint64_t a0 = ~0ull, a1 = 0;
         for (uint32_t b = lo; b < hi; b++) {

@@ -77,7 +77,9 @@ __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t 
 
 constexpr int kExtThreads = 1024;  // one CTA per SM: grid barriers stay cheap
 constexpr uint32_t kRound0WaitNs = 4000;  // wait of a round-0 piece for its sources when they are many
-constexpr uint32_t kWaitAllPerLane = 16;   // pieces per grid lane up to which round 0 waits without limit
+constexpr uint32_t kWaitAllPerLane = 16;   // pieces per grid lane up to which round 0 waits without limit,
+constexpr uint32_t kWaitAllPerItem = 256;  // ... and per block: a warp holding a block's pieces on long chains
+                                           // would stall its hand-out
 constexpr uint32_t kLevelWaitNs = 20000;   // wait of a piece handed out in level order
 
 // Are the bytes a piece reads final?  (period 0: [src, src+len); otherwise the
@@ -309,10 +311,14 @@ constexpr int kScanThreads = 1024;
 // long as needed resolves the chains at the latency of one copy per level and
 // needs no list.  Every kernel after the local pass reads the same final
 // count, so they all decide alike.
+__device__ __forceinline__ bool few_pieces(const JobDev& job, uint64_t lanes) {
+    const uint64_t pieces = *((volatile const uint32_t*)&job.counters[kStatPending]);
+    return pieces <= kWaitAllPerLane * lanes && pieces <= (uint64_t)kWaitAllPerItem * job.n_items;
+}
 __device__ __forceinline__ bool use_level_order(const JobDev& job) {
     if (!job.lvl_tab) return false;
     if (job.wait_ns != 0) return true;
-    return *((volatile const uint32_t*)&job.counters[kStatPending]) > job.lvl_min_pieces;
+    return !few_pieces(job, job.lvl_min_pieces / kWaitAllPerLane);
 }
 
 // A decode whose local pass timed out left blocks unprocessed, so their level
@@ -474,9 +480,7 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
         // waits at most kLevelWaitNs
         uint64_t wait_ns;
         if (job.wait_ns == 0) {
-            const uint64_t pieces = *((volatile uint32_t*)&job.counters[kStatPending]);
-            wait_ns = lv ? kLevelWaitNs
-                         : pieces <= kWaitAllPerLane * (uint64_t)gridDim.x * blockDim.x ? ~0ull : kRound0WaitNs;
+            wait_ns = lv ? kLevelWaitNs : few_pieces(job, (uint64_t)gridDim.x * blockDim.x) ? ~0ull : kRound0WaitNs;
         } else {
             wait_ns = job.wait_ns == 0xffffffffu ? ~0ull : job.wait_ns;
         }

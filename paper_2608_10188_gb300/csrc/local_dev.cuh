@@ -284,6 +284,21 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
             item = ticket_item(job, cnext++);
             cleft--;
         }
+        // the next block's ticket: its atomic goes out now and is read at the
+        // prefetch point, so its latency hides behind this block's work
+        uint32_t pre_claim = 0;
+        bool claimed = cleft == 0;  // group-uniform
+        if (claimed && tid == 0) pre_claim = atomicAdd(&job.counters[1], chunk);
+        // a block that ends before the prefetch point (corrupt, or a parse-only
+        // job) hands the claimed tickets on to the next iteration
+        auto settle_claim = [&]() {
+            if (!claimed) return;
+            if (tid == 0) misc[0] = pre_claim;
+            grp_sync(bid);
+            cnext = misc[0];
+            cleft = chunk;
+            claimed = false;
+        };
         if (item >= job.n_items) return;
         const int a = find_arc(job, item);
         const ArcJob J = load_arc(job, a);
@@ -490,6 +505,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
                 J.npend[ir.slot] = 1;  // per-item status of a parse-only job
             }
             grp_sync(bid);
+            settle_claim();
             continue;
         }
 
@@ -506,7 +522,11 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
             }
             for (uint32_t i = warp; i < n; i += kLocWarps)
                 if (tll[i] > kLaneBytes) copy_run(sout, slit, tlit[i], tpos[i], tll[i], lane);
-            // ---- every match byte starts unresolved; external sources are pending for good ----
+            // ---- every match byte starts unresolved; external sources are pending for good;
+            //      the in-block matches are listed (the literal positions are dead now) ----
+            uint16_t* act_list = tlit;
+            if (tid == 0) misc[3] = 0;
+            grp_sync(bid);
             for (uint32_t i = tid; i < n; i += kLocThreads) {
                 const uint32_t ml = tml[i];
                 uint8_t st = 0;  // 0: none/done, 1: unresolved in-block, 2: pending
@@ -514,6 +534,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
                     const uint32_t s = tpos[i] + tll[i];
                     pend_update_smem(pend, s, s + ml, true);
                     st = tsrc[i] >= B ? 1 : 2;
+                    if (st == 1) act_list[atomicAdd((uint32_t*)&misc[3], 1u)] = (uint16_t)i;
                 }
                 tstat[i] = st;
                 if (lvl) tlvk[i] = tlvl[i];  // the staging buffer takes the next block's levels below
@@ -521,12 +542,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
             grp_sync(bid);
             // ---- the stream buffers are free from here on: start the next item's
             //      copies, so that they land while this block finishes ----
-            if (cleft == 0) {
-                if (tid == 0) misc[0] = atomicAdd(&job.counters[1], chunk);
-                grp_sync(bid);
-                cnext = misc[0];
-                cleft = chunk;
-            }
+            settle_claim();
             pf_item = ticket_item(job, cnext++);
             cleft--;
             if (tid == 0) {
@@ -538,14 +554,16 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
                 }
                 misc[2] = go;
             }
-            // ---- in-block matches: rounds of ready periodic fills; each warp
-            //      works on four matches at once, eight lanes per match ----
+            // ---- in-block matches: rounds of ready periodic fills over the
+            //      listed matches; each warp works on four matches at once,
+            //      eight lanes per match ----
+            const uint32_t n_act = misc[3];
             for (;;) {
                 bool progress = false, left = false;
                 const uint32_t g = lane >> 3, sl = lane & 7;
                 const uint32_t gmask = 0xffu << (8 * g);
-                for (uint32_t base = warp * 4; base < n; base += kLocWarps * 4) {
-                    const uint32_t i = base + g;
+                for (uint32_t base = warp * 4; base < n_act; base += kLocWarps * 4) {
+                    const uint32_t i = base + g < n_act ? act_list[base + g] : n;
                     const bool act = i < n && tstat[i] == 1;  // the same for the group's lanes
                     uint32_t ml = 0, o = 0, so = 0, d = 1, we = 0;
                     bool busy = false;
@@ -679,6 +697,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
             }
         }
         grp_sync(bid);
+        settle_claim();
     }
 }
 

@@ -1,8 +1,9 @@
 """End-to-end decode from host memory (aceapex_decode_host), a pipeline over
-chunks of 2048 blocks: uploads, chunk decodes and downloads on three streams.
-Archives of one chunk, several chunks and a ragged last chunk decode to the
-oracle's bytes, with and without level-ordered cross-block passes, history
-and history-free, on an opened archive and on a temporary one.  (-m gpu)"""
+chunks of blocks (512, 1536, then 4096 each): uploads, chunk decodes and
+downloads on three streams.  Archives of one chunk, several chunks and a
+ragged last chunk decode to the oracle's bytes, with and without
+level-ordered cross-block passes, history and history-free, on an opened
+archive and on a temporary one.  (-m gpu)"""
 import numpy as np
 import pytest
 
@@ -26,9 +27,9 @@ def acx():
 
 
 @pytest.mark.parametrize("kind,size,kw", [
-    ("dna", 3 * 2048 * BLOCK + 5 * BLOCK + 123, {}),                  # 4 chunks, ragged last one
-    ("text", 2 * 2048 * BLOCK + 77, {"levels": True}),                # 3 chunks, level order
-    ("dna", 2048 * BLOCK, {"no_rep": True}),                          # exactly one chunk
+    ("dna", 6144 * BLOCK + 5 * BLOCK + 123, {}),                      # 4 chunks, ragged last one
+    ("text", 2048 * BLOCK + 77, {"levels": True}),                    # 3 chunks, level order
+    ("dna", 512 * BLOCK, {"no_rep": True}),                           # exactly one chunk
     ("text", 100_000, {"no_rep": True, "levels": True}),              # less than a chunk
 ])
 def test_host_pipeline_matches_oracle(acx, kind, size, kw):
