@@ -32,7 +32,7 @@ constexpr int kFusedMaxGroups = 3;
 constexpr int kFusedMaxThreads = 32 * (kFusedRansWarps + kLocWarps * kFusedMaxGroups);
 
 struct FusedLayout {
-    uint32_t tab, ring, bar, loc, loc_stride, total;
+    uint32_t tab, ring, bar, stage, loc, loc_stride, total;
 };
 
 // Shared memory of a fused CTA with G local groups whose workspaces hold
@@ -42,7 +42,8 @@ __host__ __device__ inline FusedLayout fused_layout(uint32_t T, uint32_t LB, int
     F.tab = 0;                                           // 4 x 4096 decode entries
     F.ring = 4 * kM * 4;                                 // (R + 1) x 2 KiB: R rings, 2 KiB-aligned inside
     F.bar = F.ring + (kFusedRansWarps + 1) * 2 * kRingWords;  // R x (kSlots + 1) mbarriers
-    const uint32_t end = F.bar + kFusedRansWarps * (kSlots + 1) * 8;
+    F.stage = F.bar + kFusedRansWarps * (kSlots + 1) * 8;  // R x kStageBytes symbol stages (16-aligned)
+    const uint32_t end = F.stage + kFusedRansWarps * kStageBytes;
     F.loc = (end + 127) & ~127u;
     F.loc_stride = loc_layout(T, LB, false, lvl).total;  // 128-byte multiple
     F.total = F.loc + (uint32_t)G * F.loc_stride;
@@ -80,8 +81,8 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1) k_fused(JobDev job, int G
             const uint32_t tk = __shfl_sync(ACX_FULL, t0, 0);
             if (tk >= n_a) break;
             const uint32_t item = J.order ? J.order[tk] : tk;
-            rans_block(job, 0, J, item_ref(J, item), tab0_s, ring_s, &bars[0], &bars[kSlots], seq, sphase, lane,
-                       deadline);
+            rans_block(job, 0, J, item_ref(J, item), tab0_s, ring_s, smem_u32(sm + F.stage) + warp * kStageBytes,
+                       &bars[0], &bars[kSlots], seq, sphase, lane, deadline);
             // publish: every lane's stream stores, then the flag (a corrupt
             // block is published too; its local pass finds it corrupt)
             __syncwarp();

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kRansWarps * 32) k_rans(JobDev job) {
             cleft--;
             if (tk >= n_a) break;
             rans_block(job, a, J, item_ref(J, J.order ? J.order[tk] : tk), smem_u32(&S.tab[0][0]), ring_s,
-                       &S.bar[warp][0], &S.sbar[warp], seq, sphase, lane, deadline);
+                       smem_u32(&S.stage[warp][0]), &S.bar[warp][0], &S.sbar[warp], seq, sphase, lane, deadline);
         }
         __syncthreads();
         if (threadIdx.x == 0) {

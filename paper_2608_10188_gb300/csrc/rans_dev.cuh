@@ -28,12 +28,14 @@ constexpr int kRingWords = 1024;   // 2 KiB of 16-bit words per warp
 constexpr int kRingMask = 2 * kRingWords - 1;  // byte offset within a ring
 constexpr int kChunkWords = 256;   // one TMA chunk = 512 B
 constexpr int kSlots = kRingWords / kChunkWords;
-constexpr int kGroupSyms = 8;      // full steps between ring checks, times the states per lane
+constexpr int kGroupSyms = 16;     // full steps between ring checks, times the states per lane
+constexpr int kStageBytes = 32 * kGroupSyms;  // a warp's symbols of one group, staged for 16-byte stores
 
 struct RansSmem {
     uint32_t tab[4][kM];                               // 64 KiB
     uint16_t ringspace[(kRansWarps + 1) * kRingWords];  // the warps' rings, 2 KiB-aligned in the shared window
     uint64_t bar[kRansWarps][kSlots];
+    alignas(16) uint8_t stage[kRansWarps][kStageBytes];
     uint64_t sbar[kRansWarps];                         // short-stream staging barrier of each warp
     int arc;                                           // archive whose tables are loaded
     int next_arc;
@@ -95,7 +97,8 @@ __device__ __forceinline__ void rans_renorm(uint32_t& x, uint32_t& rb, uint32_t 
 template <int S>
 __device__ __forceinline__ bool rans_stream(uint32_t tab_s, const uint8_t* __restrict__ body, uint32_t enc,
                                             uint32_t n, uint32_t K, uint8_t* __restrict__ out, uint32_t ring_s,
-                                            uint64_t* bar, uint32_t& seq, int lane, uint64_t deadline) {
+                                            uint32_t stage_s, uint64_t* bar, uint32_t& seq, int lane,
+                                            uint64_t deadline) {
     const uint32_t hdr = (4 * K + 15) & ~15u;
     if (enc < hdr || ((enc - hdr) & 1)) return false;
     const uint32_t W = (enc - hdr) >> 1;
@@ -138,23 +141,28 @@ __device__ __forceinline__ bool rans_stream(uint32_t tab_s, const uint8_t* __res
         }
     };
     if (K == 32 * S) {
-        // Fast path: groups of full steps (every lane valid), symbols stored
-        // at immediate offsets; a group reads at most 32 * kGroupSyms words.
+        // Fast path: groups of full steps (every lane valid); a group reads
+        // at most 32 * kGroupSyms words.  Its symbols (kStageBytes
+        // consecutive bytes of the stream) are staged in shared memory and
+        // go out as one 16-byte store per lane.
         constexpr int U = kGroupSyms / S;
         const uint32_t full_groups = ok ? (n / K) / U : 0;
-        uint8_t* op = out + lane;
+        const uint32_t st_lane = stage_s + lane;
         for (uint32_t g = 0; g < full_groups; g++, t0 += U) {
             advance(32 * kGroupSyms);
             if (!ok) break;
-            uint8_t* og = op + t0 * (32 * S);
             uint32_t rb = ((rbase + p) * 2) & kRingMask;
 #pragma unroll
             for (int u = 0; u < U; u++) {
 #pragma unroll
-                for (int s = 0; s < S; s++) og[(u * S + s) * 32] = (uint8_t)rans_sym(tab_s, x[s]);
+                for (int s = 0; s < S; s++) sts_u8(st_lane + (u * S + s) * 32, rans_sym(tab_s, x[s]));
 #pragma unroll
                 for (int s = 0; s < S; s++) rans_renorm(x[s], rb, ring_s, lt_mask, p);
             }
+            __syncwarp();
+            const uint4 v = lds_u128(stage_s + 16 * lane);
+            reinterpret_cast<uint4*>(out + (size_t)t0 * (32 * S))[lane] = v;  // (out is 16-aligned)
+            __syncwarp();
             if (p > W) { ok = false; break; }
         }
     }
@@ -206,14 +214,14 @@ __device__ __forceinline__ bool rans_stream(uint32_t tab_s, const uint8_t* __res
 // lanes): out of line, so that they do not raise the kernel's register
 // pressure.
 static __device__ __noinline__ bool rans_stream2(uint32_t tab_s, const uint8_t* body, uint32_t enc, uint32_t n, uint32_t K,
-                                          uint8_t* out, uint32_t ring_s, uint64_t* bar, uint32_t& seq, int lane,
-                                          uint64_t deadline) {
-    return rans_stream<2>(tab_s, body, enc, n, K, out, ring_s, bar, seq, lane, deadline);
+                                          uint8_t* out, uint32_t ring_s, uint32_t stage_s, uint64_t* bar,
+                                          uint32_t& seq, int lane, uint64_t deadline) {
+    return rans_stream<2>(tab_s, body, enc, n, K, out, ring_s, stage_s, bar, seq, lane, deadline);
 }
 static __device__ __noinline__ bool rans_stream4(uint32_t tab_s, const uint8_t* body, uint32_t enc, uint32_t n, uint32_t K,
-                                          uint8_t* out, uint32_t ring_s, uint64_t* bar, uint32_t& seq, int lane,
-                                          uint64_t deadline) {
-    return rans_stream<4>(tab_s, body, enc, n, K, out, ring_s, bar, seq, lane, deadline);
+                                          uint8_t* out, uint32_t ring_s, uint32_t stage_s, uint64_t* bar,
+                                          uint32_t& seq, int lane, uint64_t deadline) {
+    return rans_stream<4>(tab_s, body, enc, n, K, out, ring_s, stage_s, bar, seq, lane, deadline);
 }
 
 // The short streams of a block (cmd, len, off) decoded concurrently by one
@@ -323,11 +331,13 @@ __device__ __forceinline__ void copy_stored(const uint8_t* __restrict__ src, uin
 // scratch: the three short streams together when they fit the warp, then the
 // rest one by one (the literal stream is skipped by a parse-only job).
 // tab0_s is the shared address of the four decode tables; bar (kSlots
-// barriers), sbar and the ring are the warp's own.  A corrupt stream sets the
+// barriers), sbar, the ring and the symbol stage (kStageBytes, 16-aligned)
+// are the warp's own.  A corrupt stream sets the
 // job's (and the archive's) error status.
 __device__ __forceinline__ void rans_block(const JobDev& job, int a, const ArcJob& J, const ItemRef& ir,
-                                           uint32_t tab0_s, uint32_t ring_s, uint64_t* bar, uint64_t* sbar,
-                                           uint32_t& seq, uint32_t& sphase, int lane, uint64_t deadline) {
+                                           uint32_t tab0_s, uint32_t ring_s, uint32_t stage_s, uint64_t* bar,
+                                           uint64_t* sbar, uint32_t& seq, uint32_t& sphase, int lane,
+                                           uint64_t deadline) {
     const uint32_t b = ir.blk;
     if (J.items && J.slot && lane == 0) J.slot[b] = ir.slot;  // read by the cross-block pass
     const BlockDev& bd = J.blk[b];
@@ -348,9 +358,9 @@ __device__ __forceinline__ void rans_block(const JobDev& job, int a, const ArcJo
         if (bd.rans_mask & (1u << s)) {
             const uint32_t K = bd.s_K[s];
             const uint32_t tb = tab0_s + s * kM * 4;
-            if (K <= 32) ok = rans_stream<1>(tb, body, bd.s_enc[s], n, K, o, ring_s, bar, seq, lane, deadline);
-            else if (K == 64) ok = rans_stream2(tb, body, bd.s_enc[s], n, K, o, ring_s, bar, seq, lane, deadline);
-            else ok = rans_stream4(tb, body, bd.s_enc[s], n, K, o, ring_s, bar, seq, lane, deadline);
+            if (K <= 32) ok = rans_stream<1>(tb, body, bd.s_enc[s], n, K, o, ring_s, stage_s, bar, seq, lane, deadline);
+            else if (K == 64) ok = rans_stream2(tb, body, bd.s_enc[s], n, K, o, ring_s, stage_s, bar, seq, lane, deadline);
+            else ok = rans_stream4(tb, body, bd.s_enc[s], n, K, o, ring_s, stage_s, bar, seq, lane, deadline);
         } else {
             copy_stored(body, o, n, lane);
         }
