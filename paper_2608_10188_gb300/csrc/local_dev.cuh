@@ -8,7 +8,6 @@ namespace acx {
 
 constexpr int kLocThreads = 128;
 constexpr int kLocWarps = kLocThreads / 32;
-constexpr uint64_t kRefTag = 1ull << 63;  // history map entry "copy input entry k"
 
 struct LocLayout {
     uint32_t out, pend, tsrc, tpos, tll, tml, tlit, tcmd, tstat, lenb, soff, slit, scan, bar, misc, need, tlvl, tlvk,
@@ -52,7 +51,7 @@ __host__ __device__ inline LocLayout loc_layout(uint32_t T, uint32_t LB, bool ne
 }
 
 // Literal runs up to this many bytes are copied by one thread (a byte at a
-// time, every thread of the CTA on its own run); longer ones by a warp.
+// time, every thread of the CTA on its own run); longer ones by eight lanes.
 constexpr uint32_t kLaneBytes = 32;
 
 // Does the match at [o, o + ml) of a block touch a wanted byte?
@@ -112,45 +111,42 @@ __device__ __forceinline__ void block_scan3(uint32_t v[3], uint32_t tot[3], uint
     grp_sync(bid);
 }
 
-struct HMap {
-    uint64_t e[4];
-};
-__device__ __forceinline__ HMap hmap_identity() {
-    HMap m;
-#pragma unroll
-    for (int k = 0; k < 4; k++) m.e[k] = kRefTag | k;
+// The four-entry distance history ("The Last Sequential Element") as a map
+// from the history before a run of tokens to the history after it, packed in
+// 64 bits: entry k (bits 16k..16k+15) is kHRef | j, "entry j of the history
+// before the run", or the index in the block of the NEW token whose distance
+// it holds (a block that passes the token checks has at most kBlock / 4 + 1
+// tokens, so an index never reaches kHRef).  Maps compose associatively,
+// which makes the history a prefix scan.
+typedef uint64_t HMap;
+constexpr uint32_t kHRef = 0x8000;
+constexpr HMap kHIdentity = 0x8003800280018000ull;
+
+// The map followed by token i with command cmd: a NEW token pushes its own
+// distance in front; a repeat of entry j moves that entry to the front.
+__device__ __forceinline__ HMap hmap_step(HMap m, uint8_t cmd, uint32_t i) {
+    if (cmd == kNew) return (m << 16) | i;
+    if (cmd >= 2 && cmd <= 4) {  // entry j = cmd - 1 >= 1 (a repeat of entry 0 changes nothing)
+        const uint32_t s = 16 * (cmd - 1);
+        const uint64_t low = m & ((1ull << s) - 1);   // entries 0 .. j-1
+        const uint64_t e = (m >> s) & 0xffff;          // entry j
+        const uint64_t high = s == 48 ? 0ull : m & (~0ull << (s + 16));
+        return high | (low << 16) | e;
+    }
     return m;
 }
-// (first f, then g)
-__device__ __forceinline__ HMap hmap_compose(const HMap& f, const HMap& g) {
-    HMap r;
+// (first f, then g): an entry of g that names entry j of its input takes f's entry j
+__device__ __forceinline__ HMap hmap_compose(HMap f, HMap g) {
+    const uint32_t flo = (uint32_t)f, fhi = (uint32_t)(f >> 32);
+    uint32_t v[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        const uint64_t x = g.e[k];
-        const uint32_t j = (uint32_t)x & 3;
-        // f.e[j] by selects, so that the maps stay in registers
-        uint64_t v = f.e[0];
-        v = j == 1 ? f.e[1] : v;
-        v = j == 2 ? f.e[2] : v;
-        v = j == 3 ? f.e[3] : v;
-        r.e[k] = (x & kRefTag) ? v : x;
+        const uint32_t x = (uint32_t)(g >> (16 * k)) & 0xffff;
+        const uint32_t j = x & 3;
+        const uint32_t fj = (j & 2 ? fhi : flo) >> (16 * (j & 1));
+        v[k] = (x & kHRef) ? fj & 0xffff : x;
     }
-    return r;
-}
-__device__ __forceinline__ HMap hmap_token(uint8_t cmd, uint64_t d_new) {
-    HMap m = hmap_identity();
-    if (cmd == kNew) {
-        m.e[0] = d_new;
-        m.e[1] = kRefTag | 0;
-        m.e[2] = kRefTag | 1;
-        m.e[3] = kRefTag | 2;
-    } else if (cmd >= 1 && cmd <= 4) {
-        const int j = cmd - 1;  // move entry j to the front
-        m.e[0] = kRefTag | j;
-#pragma unroll
-        for (int k = 1; k <= 3; k++) m.e[k] = kRefTag | (k <= j ? k - 1 : k);
-    }
-    return m;
+    return (uint64_t)(v[0] | (v[1] << 16)) | ((uint64_t)(v[2] | (v[3] << 16)) << 32);
 }
 
 __device__ __forceinline__ bool pend_clear_smem(const uint32_t* pend, uint32_t s, uint32_t e) {
@@ -167,24 +163,28 @@ __device__ __forceinline__ void pend_update_smem(uint32_t* pend, uint32_t s, uin
     }
 }
 
-// Literal run: out[b, b+L) = lit[a, a+L) (both in shared memory), one warp,
-// 4-byte funnel-shifted words in the middle, bytes at the ragged ends.
-__device__ __forceinline__ void copy_run(uint8_t* __restrict__ sout, const uint8_t* __restrict__ lit, uint32_t a,
-                                         uint32_t b, uint32_t L, int lane) {
-    if (!L) return;
+// Literal run: out[b, b+L) = lit[a, a+L) (both in shared memory), by the
+// eight lanes sl = 0..7 of a lane group: 16-byte stores in the middle, each
+// from five funnel-shifted source words, bytes at the ragged ends.  Source
+// words may reach 3 bytes past the run (the literal buffer is padded).
+__device__ __forceinline__ void copy_run8(uint8_t* __restrict__ sout, const uint8_t* __restrict__ lit, uint32_t a,
+                                          uint32_t b, uint32_t L, uint32_t sl) {
     const uint32_t e = b + L;
-    const uint32_t w0 = (b + 3) >> 2, w1 = e >> 2;  // whole words [w0, w1)
-    if (w0 >= w1) {
-        for (uint32_t x = b + lane; x < e; x += 32) sout[x] = lit[a + (x - b)];
+    const uint32_t q0 = (b + 15) >> 4, q1 = e >> 4;  // whole 16-byte chunks [q0, q1)
+    if (q0 >= q1) {
+        for (uint32_t x = b + sl; x < e; x += 8) sout[x] = lit[a + (x - b)];
         return;
     }
-    if (lane < (int)(4 * w0 - b)) sout[b + lane] = lit[a + lane];
-    if (lane < (int)(e - 4 * w1)) sout[4 * w1 + lane] = lit[a + (4 * w1 + lane - b)];
+    for (uint32_t x = b + sl; x < 16 * q0; x += 8) sout[x] = lit[a + (x - b)];
+    for (uint32_t x = 16 * q1 + sl; x < e; x += 8) sout[x] = lit[a + (x - b)];
     const uint32_t* lw = reinterpret_cast<const uint32_t*>(lit);
-    for (uint32_t w = w0 + lane; w < w1; w += 32) {
-        const uint32_t src = a + (4 * w - b);
-        const uint32_t lo = lw[src >> 2], hi = lw[(src >> 2) + 1];
-        reinterpret_cast<uint32_t*>(sout)[w] = __funnelshift_r(lo, hi, 8 * (src & 3));
+    const uint32_t s0 = a + 16 * q0 - b;  // source of chunk q0
+    const uint32_t sh = 8 * (s0 & 3);
+    for (uint32_t q = q0 + sl; q < q1; q += 8) {
+        const uint32_t w = (s0 >> 2) + 4 * (q - q0);
+        const uint32_t x0 = lw[w], x1 = lw[w + 1], x2 = lw[w + 2], x3 = lw[w + 3], x4 = lw[w + 4];
+        reinterpret_cast<uint4*>(sout)[q] = make_uint4(__funnelshift_r(x0, x1, sh), __funnelshift_r(x1, x2, sh),
+                                                       __funnelshift_r(x2, x3, sh), __funnelshift_r(x3, x4, sh));
     }
 }
 
@@ -197,7 +197,7 @@ __device__ __forceinline__ void stage_streams(const JobDev& job, uint32_t item, 
     const ItemRef ir = item_ref(J, item - J.item_base);
     const BlockDev& bd = J.blk[ir.blk];
     const uint32_t n = bd.n_tok, LB = bd.s_raw[kLen], n_new = bd.n_new, n_lit = bd.s_raw[kLit];
-    if (n > job.max_tok || LB > job.max_lenb || n_new > job.max_tok) return;
+    if (n > job.max_tok || LB > job.max_lenb || n_new > job.max_tok || n_lit > kBlock) return;
     const uint8_t* scr = J.scratch + ir.scratch;
     const uint32_t sz[4] = {(n + 15) & ~15u, (LB + 15) & ~15u, (5 * n_new + 15) & ~15u, (n_lit + 15) & ~15u};
     uint8_t* dsts[4] = {tcmd, lenb, soff, slit};
@@ -308,7 +308,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
         const uint64_t B = (uint64_t)b * kBlock;
         const uint32_t R = bd.raw_len, n = bd.n_tok, LB = bd.s_raw[kLen], n_lit = bd.s_raw[kLit];
         const uint32_t n_new = bd.n_new;
-        bool bad = n > job.max_tok || LB > job.max_lenb || n_new > job.max_tok;
+        bool bad = n > job.max_tok || LB > job.max_lenb || n_new > job.max_tok || n_lit > kBlock;
         int stage = bad ? kStageLimits : 0;
         auto mark = [&](bool cond, int st) {
             if (cond && !bad) { bad = true; stage = st; }
@@ -431,31 +431,30 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
         // ---- the 4-entry history as a monoid scan (blocks with repeat codes only) ----
         if (any_rep && !bad) {
             HMap* hbuf = reinterpret_cast<HMap*>(sout);  // the block buffer is free until literal placement
-            HMap agg = hmap_identity();
-            for (uint32_t i = i0; i < i1; i++)
-                agg = hmap_compose(agg, hmap_token(tcmd[i], B + tpos[i] + tll[i] - tsrc[i]));
+            HMap agg = kHIdentity;
+            for (uint32_t i = i0; i < i1; i++) agg = hmap_step(agg, tcmd[i], i);
             // inclusive scan of the maps: shuffles inside each warp, then the
             // warps' totals (earlier maps act first)
             HMap inc = agg;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                HMap prev;
-#pragma unroll
-                for (int k = 0; k < 4; k++) prev.e[k] = __shfl_up_sync(ACX_FULL, inc.e[k], o);
+                const HMap prev = __shfl_up_sync(ACX_FULL, inc, o);
                 if (lane >= o) inc = hmap_compose(prev, inc);
             }
             if (lane == 31) hbuf[warp] = inc;
             grp_sync(bid);
-            HMap pre = hmap_identity();
+            HMap pre = kHIdentity;
             for (int w = 0; w < warp; w++) pre = hmap_compose(pre, hbuf[w]);
-            HMap ex;
-#pragma unroll
-            for (int k = 0; k < 4; k++) ex.e[k] = __shfl_up_sync(ACX_FULL, inc.e[k], 1);
+            const HMap ex = __shfl_up_sync(ACX_FULL, inc, 1);
             if (lane > 0) pre = hmap_compose(pre, ex);
+            // the history before this thread's tokens: the block starts from
+            // (1, 2, 3, 4); a NEW token's entry is its distance
             uint64_t h[4];
-            const uint64_t h0[4] = {1, 2, 3, 4};  // initial history, reset per block
 #pragma unroll
-            for (int k = 0; k < 4; k++) h[k] = (pre.e[k] & kRefTag) ? h0[pre.e[k] & 3] : pre.e[k];
+            for (int k = 0; k < 4; k++) {
+                const uint32_t x = (uint32_t)(pre >> (16 * k)) & 0xffff;
+                h[k] = (x & kHRef) ? (uint64_t)((x & 3) + 1) : B + tpos[x] + tll[x] - tsrc[x];
+            }
             for (uint32_t i = i0; i < i1; i++) {
                 const uint8_t c = tcmd[i];
                 const uint64_t dst = B + tpos[i] + tll[i];
@@ -512,7 +511,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
         uint32_t npend = 0, pbytes = 0;
         if (!bad) {
             // ---- literal placement: a thread copies a tiny run (<= kLaneBytes)
-            //      by itself, all threads at once; a warp copies each longer one ----
+            //      by itself, all threads at once; eight lanes copy each longer one ----
             for (uint32_t i = tid; i < n; i += kLocThreads) {
                 const uint32_t ll = tll[i];
                 if (ll <= kLaneBytes) {
@@ -520,8 +519,8 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
                     for (uint32_t k = 0; k < ll; k++) sout[lb + k] = slit[la + k];
                 }
             }
-            for (uint32_t i = warp; i < n; i += kLocWarps)
-                if (tll[i] > kLaneBytes) copy_run(sout, slit, tlit[i], tpos[i], tll[i], lane);
+            for (uint32_t i = warp * 4 + (lane >> 3); i < n; i += kLocWarps * 4)
+                if (tll[i] > kLaneBytes) copy_run8(sout, slit, tlit[i], tpos[i], tll[i], lane & 7);
             // ---- every match byte starts unresolved; external sources are pending for good;
             //      the in-block matches are listed (the literal positions are dead now) ----
             uint16_t* act_list = tlit;

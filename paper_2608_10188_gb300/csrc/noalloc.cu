@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_plan_small(const uint8_t* a, uint64_t l
                 ok = ok && off + n_tok <= plen;
                 off = (off + n_tok + 15) & ~(uint64_t)15;
             }
-            ok = ok && off == plen && bd.s_raw[kCmd] == n_tok && bd.s_raw[kOff] % 5 == 0;
+            ok = ok && off == plen && bd.s_raw[kCmd] == n_tok && bd.s_raw[kOff] % 5 == 0 && bd.s_raw[kLit] <= raw;
             // every token but a closing literal run has a match of at least
             // min_match bytes: more tokens than that cannot sum to the block
             // (the regular decode finds such a block corrupt too)

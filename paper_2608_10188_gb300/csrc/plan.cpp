@@ -135,6 +135,8 @@ int build_plan(const uint8_t* a, uint64_t len, Plan* P, std::string* why) {
         if (off != plen) return fail("payload length mismatch");
         if (bd.s_raw[kCmd] != n_tok) return fail("token count mismatch");
         if (bd.s_raw[kOff] % 5) return fail("offset stream not a multiple of 5");
+        // the literals are output bytes of the block (the local pass stages them in a block-sized buffer)
+        if (bd.s_raw[kLit] > raw) return fail("literal stream longer than the block");
         bd.n_new = bd.s_raw[kOff] / 5;
         bd.scratch = scratch;
         bd.span_base = (uint32_t)P->span_slots;

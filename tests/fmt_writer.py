@@ -116,3 +116,20 @@ def build_archive(blocks, *, min_match=4, flags=0, expected=None, fnv=None, raw_
         arc += b"".join(struct.pack("<I", i) for i in dep_ids)
     arc += b"\0" * (off_payload - len(arc))
     return arc + bytes(payload)
+
+
+def inflate_literal_stream(arc: bytes, extra: int = BLOCK) -> bytes:
+    """The archive with the raw length of the first entropy-coded literal
+    stream raised by `extra` bytes: every structural bound still holds (the
+    descriptor's stream stays inside the payload), but the block claims more
+    literals than it has bytes, which no valid block can."""
+    a = bytearray(arc)
+    nb = struct.unpack_from("<I", a, 24)[0]
+    off_idx = struct.unpack_from("<Q", a, 40)[0]
+    for b in range(nb):
+        poff = struct.unpack_from("<Q", a, off_idx + 40 * b)[0]
+        d = poff + 12 * 3  # the literal stream's descriptor
+        if a[d + 8] == 1:  # rANS: its raw length is free of its encoded length
+            struct.pack_into("<I", a, d, struct.unpack_from("<I", a, d)[0] + extra)
+            return bytes(a)
+    raise ValueError("no entropy-coded literal stream")

@@ -91,6 +91,12 @@ def test_host_validation_rejects_structural_corruption(acx):
     bad[0] ^= 1  # magic
     with pytest.raises(acx.AceapexError):
         acx.archive_check(bytes(bad))
+    # a block that claims more literal bytes than it holds
+    from fmt_writer import inflate_literal_stream
+    big = inflate_literal_stream(bytes(arc))
+    with pytest.raises(acx.AceapexError):
+        acx.archive_check(big)
+    assert oracle.decode_status(big, verify=False)[0] == oracle.E_CORRUPT
     # a hand-built archive with a token-level fault passes the structural
     # check (it is caught by the kernels) but not the oracle
     toks = [[{"cmd": 0, "lits": b"ACGT", "ml": 4, "src": 4}]]

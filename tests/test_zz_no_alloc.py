@@ -19,6 +19,7 @@ import pytest
 
 import oracle
 import synth
+from fmt_writer import inflate_literal_stream
 
 pytestmark = pytest.mark.gpu
 
@@ -130,6 +131,7 @@ def _corruptions(acx):
     for j in range(max(1, enc // 2), min(enc, enc // 2 + 8)):  # scramble block 9's command stream
         a[poff + 48 + j] ^= 0xA7
     out.append(("command stream", a))
+    out.append(("literal stream longer than the block", bytearray(inflate_literal_stream(bytes(good)))))
     # an archive with dependency lists, one of which misses a block that its matches read
     dl = bytearray(acx.encode(data, deps=True))
     idx2 = struct.unpack_from("<Q", dl, 40)[0]
@@ -159,7 +161,7 @@ def test_noalloc_agrees_with_decode_all_on_corrupt_archives(acx):
         assert want == acx.lib.E_CORRUPT, (name, want)
         assert got == want, (name, got, want)
         names.append(name)
-    assert len(names) == 7
+    assert len(names) == 8
     # a good archive still decodes after the corrupt ones
     data = synth.dna(20 * BLOCK, 9)
     arc_h = np.frombuffer(acx.encode(data), dtype=np.uint8).copy()
