@@ -298,9 +298,12 @@ int aceapex_shard_range(uint64_t total, int n_ranks, int rank, uint64_t* start, 
  * dependency closure (the match index is built at creation if the archive
  * has none), and decodes each tick's union of closures, minus the bytes the
  * cache keeps, with one launch sequence into cache slots followed by one
- * gather into the requests' buffers.  Requests that arrive while a tick runs
- * join the next one, which is queued right behind it on the server's stream.
- * Admission is by memory: a request waits while its closure needs more free
+ * gather into the requests' buffers.  Ticks go to `streams` lanes (each a
+ * stream with its own context and scratch, up to two ticks deep), so that a
+ * tick formed while others run starts on the device beside them; a tick
+ * that reads a block another unfinished tick decodes, or decodes a block
+ * another unfinished tick reads, waits for that tick's completion.
+ * Requests that arrive while ticks run join the next tick.  Admission is by memory: a request waits while its closure needs more free
  * or evictable slots than there are, and completes with ACEAPEX_E_BUSY if it
  * could never fit.  Blocks read by unfinished ticks are pinned; the others
  * are evicted least recently used first.  The archive must stay open while
@@ -311,6 +314,7 @@ typedef struct {
     uint64_t cache_bytes;        /* decoded-block cache (device memory; default 4 GiB) */
     uint32_t max_tick_blocks;    /* blocks one tick decodes at most (default 16384) */
     uint32_t max_tick_requests;  /* requests one tick gathers at most (default 4096) */
+    uint32_t streams;            /* tick lanes, 1..16 (default 2) */
 } aceapex_server_params;
 typedef struct {
     uint64_t id;
@@ -326,6 +330,10 @@ typedef struct {
     double closure_mean, closure_p50, closure_p99;
     double seconds;           /* first arrival -> last completion */
     double gbs;               /* bytes delivered / seconds */
+    uint64_t tick_overlaps;   /* pairs of ticks whose device work overlapped in time */
+    uint64_t tick_waits;      /* ticks that waited for a tick on another lane */
+    double tick_host_ms;      /* host time forming the launched ticks (walks, admission, launches) */
+    double walk_ms;           /* ... of which closure walks */
 } aceapex_server_stats;
 
 /* ctx: its device and decoder parameters are used (the server creates its own

@@ -7,9 +7,13 @@
 // closure minus what the cache already holds (paper, Random Access at Scale),
 // and decodes the union with one launch sequence: the block decodes write
 // into cache slots, then one gather copies every admitted region to its
-// destination.  Ticks run back to back on the server's stream, so requests
-// that arrive while a tick is on the GPU join the next one (continuous
-// batching); the host prepares tick k+1 while tick k runs.
+// destination.  Ticks go to K lanes, each a stream with its own context,
+// scratch and staging, up to two ticks deep; a new tick takes the lane with
+// the fewest ticks in flight.  Ticks on different lanes run on the device at
+// the same time unless one reads or writes a block that the other decodes,
+// or decodes a block that the other reads: then the later one waits for the
+// earlier one's completion event.  Requests that arrive while ticks run join
+// the next tick (continuous batching); the host prepares it while they run.
 //
 // Cache: slots of 16 KiB (cache_bytes / 16 KiB of them), each with its
 // pending count and bitmap.  A block's kept bytes are the wanted bytes of its
@@ -48,8 +52,8 @@ struct ReqLater {  // min-heap on (arrival, id)
     bool operator()(const Req& a, const Req& b) const { return a.at_ns != b.at_ns ? a.at_ns > b.at_ns : a.id > b.id; }
 };
 
-// Host staging and device copies of one tick's tables (two sets: the host
-// fills one while the other's copies may still be pending on the stream).
+// Host staging and device copies of one tick's tables (two sets per lane:
+// the host fills one while the other's copies may still be pending).
 struct TickBufs {
     ItemDev* h_items = nullptr;
     uint32_t* h_need = nullptr;
@@ -59,13 +63,35 @@ struct TickBufs {
     DevBuf d_items, d_need, d_gather;
 };
 
-struct Tick {
-    int set = 0;
-    cudaEvent_t done = nullptr;
-    std::vector<Req> reqs;
-    std::vector<uint32_t> used;       // pinned blocks
-    std::vector<uint32_t> decoded;    // blocks written by this tick
+// A stream of ticks with its own context (counters, error words), scratch
+// and staging.
+struct Lane {
+    aceapex_ctx* c = nullptr;
+    cudaStream_t st = nullptr;
+    DevBuf streams, spans, lists;
+    TickBufs bufs[2];
+    uint64_t formed = 0;  // ticks formed on this lane (their staging alternates)
+    int inflight = 0;
 };
+
+struct Tick {
+    int lane = 0, set = 0;
+    uint64_t seq = 0;
+    cudaEvent_t start = nullptr, done = nullptr;
+    std::vector<Req> reqs;
+    std::vector<uint32_t> used;       // pinned blocks (sorted)
+    std::vector<uint32_t> decoded;    // blocks written by this tick (sorted)
+    std::vector<uint64_t> after;      // ticks in flight at launch that this one reads or writes after
+};
+
+bool sorted_meet(const std::vector<uint32_t>& a, const std::vector<uint32_t>& b) {
+    size_t i = 0, j = 0;
+    while (i < a.size() && j < b.size()) {
+        if (a[i] == b[j]) return true;
+        if (a[i] < b[j]) i++; else j++;
+    }
+    return false;
+}
 
 cudaError_t host_grow(void** p, size_t* cap, size_t need, size_t elem) {
     if (need <= *cap) return cudaSuccess;
@@ -91,11 +117,13 @@ struct aceapex_server {
     uint32_t* npend = nullptr;
     uint32_t* pmap = nullptr;
     uint32_t* d_slot = nullptr;
-    DevBuf streams, spans, lists;
-    cudaStream_t st = nullptr;
-    TickBufs bufs[2];
+    std::vector<Lane> lanes;
     std::deque<Tick> inflight;
     std::vector<cudaEvent_t> free_events;
+    cudaEvent_t t0_ev = nullptr;               // the device clock's origin (recorded at creation)
+    std::deque<std::pair<float, float>> spans_ms;  // device intervals of the last completed ticks
+    std::deque<std::pair<uint64_t, int>> failed;   // recent failed ticks (seq, status)
+    uint64_t seq_next = 1;
     // host cache state
     std::vector<uint32_t> slot_of;   // block -> slot or kNoSlot
     std::vector<Ivs> valid;          // block -> kept bytes (resident blocks)
@@ -141,6 +169,8 @@ struct aceapex_server {
     std::vector<double> lat_us;
     std::vector<uint32_t> closures;
     uint64_t n_ok = 0, n_err = 0, n_busy = 0, bytes = 0, ticks = 0, blk_decoded = 0, blk_hit = 0;
+    uint64_t tick_overlaps = 0, tick_waits = 0;
+    int64_t form_ns = 0, walk_ns = 0;  // host time spent forming the launched ticks, and in their closure walks
     int64_t first_arrival = -1, last_done = 0;
 
     int64_t now() const {
@@ -176,8 +206,9 @@ struct aceapex_server {
         return s->slot_of[b] != kNoSlot ? &s->valid[b] : nullptr;
     }
     void run();
-    bool form_tick();
+    bool form_tick(int li);
     void finish_tick(Tick& t, int status);
+    cudaEvent_t take_event(cudaError_t* e);
     void complete(const Req& r, int status, int64_t t_done);
 };
 
@@ -209,12 +240,45 @@ void aceapex_server::complete(const Req& r, int status, int64_t t_done) {
 
 void aceapex_server::finish_tick(Tick& t, int status) {
     const int64_t tn = now();
+    // a tick that read or rewrote blocks after a failed one fails with it
+    for (uint64_t q : t.after)
+        for (const auto& f : failed)
+            if (f.first == q && status == ACEAPEX_OK) status = f.second;
+    if (status != ACEAPEX_OK) {
+        failed.emplace_back(t.seq, status);
+        if (failed.size() > 64) failed.pop_front();
+    }
     for (uint32_t b : t.used) unpin(b);
     if (status != ACEAPEX_OK)
         for (uint32_t b : t.decoded)
             if (pins[b] == 0) drop(b);
+    // device intervals: pairs of ticks (on different lanes) that ran at the same time
+    float s_ms = 0, e_ms = 0;
+    if (t.start && t.done && cudaEventElapsedTime(&s_ms, t0_ev, t.start) == cudaSuccess &&
+        cudaEventElapsedTime(&e_ms, t0_ev, t.done) == cudaSuccess) {
+        uint64_t ov = 0;
+        for (const auto& iv : spans_ms) ov += s_ms < iv.second && iv.first < e_ms;
+        spans_ms.emplace_back(s_ms, e_ms);
+        if (spans_ms.size() > 16) spans_ms.pop_front();
+        std::lock_guard<std::mutex> g(mu);
+        tick_overlaps += ov;
+    }
     for (const Req& r : t.reqs) complete(r, status, tn);
-    free_events.push_back(t.done);
+    if (t.start) free_events.push_back(t.start);
+    if (t.done) free_events.push_back(t.done);
+    lanes[t.lane].inflight--;
+}
+
+cudaEvent_t aceapex_server::take_event(cudaError_t* e) {
+    if (free_events.empty()) {
+        cudaEvent_t ev = nullptr;
+        *e = cudaEventCreate(&ev);
+        return *e == cudaSuccess ? ev : nullptr;
+    }
+    cudaEvent_t ev = free_events.back();
+    free_events.pop_back();
+    *e = cudaSuccess;
+    return ev;
 }
 
 // One closure walk per request, against the cache only (thread ti's state).
@@ -260,12 +324,18 @@ void aceapex_server::walk_all(const std::vector<Req>& reqs, std::vector<WalkOut>
     pool_done_cv.wait(g, [this] { return pool_busy == 0; });
 }
 
-// Admit the arrived requests that fit and launch one tick; false if nothing
-// was launched.
-bool aceapex_server::form_tick() {
+// Admit the arrived requests that fit and launch one tick on lane li; false
+// if nothing was launched.
+bool aceapex_server::form_tick(int li) {
     const Plan& P = A->plan;
-    const int set = (int)(ticks & 1);
-    TickBufs& B = bufs[set];
+    Lane& Ln = lanes[li];
+    aceapex_ctx* c = Ln.c;
+    cudaStream_t st = Ln.st;
+    const int set = (int)(Ln.formed & 1);
+    TickBufs& B = Ln.bufs[set];
+    DevBuf& streams = Ln.streams;
+    DevBuf& spans = Ln.spans;
+    DevBuf& lists = Ln.lists;
     TickState& T = walk;
     T.begin(P.n_blocks);
     std::vector<Req> admitted, cand;
@@ -281,6 +351,7 @@ bool aceapex_server::form_tick() {
     if (cand.empty()) return false;
     std::vector<WalkOut> outs;
     walk_all(cand, outs);
+    const int64_t t_walked = now();
     // admission in arrival order: a request joins while the cache can hold its
     // closure next to those admitted before it
     uint32_t avail = (uint32_t)(free_slots.size() + lru.size());
@@ -399,6 +470,26 @@ bool aceapex_server::form_tick() {
                 cudaSuccess)
             rc = cuda_fail(c, e, "server: tick upload");
     }
+    // order after the ticks in flight that decode a block this tick reads, or
+    // read a block this tick decodes (the same lane's are ordered by its stream)
+    Tick t;
+    t.lane = li;
+    t.set = set;
+    t.seq = seq_next++;
+    t.used.assign(T.used.begin(), T.used.end());
+    std::sort(t.used.begin(), t.used.end());
+    t.decoded = blocks;  // sorted
+    bool waited = false;
+    for (const Tick& u : inflight) {
+        if (!sorted_meet(t.used, u.decoded) && !sorted_meet(t.decoded, u.used)) continue;
+        t.after.push_back(u.seq);
+        if (u.lane != li && rc == ACEAPEX_OK) {
+            if ((e = cudaStreamWaitEvent(st, u.done, 0)) != cudaSuccess) rc = cuda_fail(c, e, "server: tick order");
+            waited = true;
+        }
+    }
+    if (rc == ACEAPEX_OK && (t.start = take_event(&e)) == nullptr) rc = cuda_fail(c, e, "event");
+    if (rc == ACEAPEX_OK && (e = cudaEventRecord(t.start, st)) != cudaSuccess) rc = cuda_fail(c, e, "event");
     if (rc == ACEAPEX_OK && nblk) {
         JobDev job{};
         ArcJob& Jb = job.one;
@@ -431,6 +522,9 @@ bool aceapex_server::form_tick() {
         job.lists[1] = job.lists[0] + std::max<uint64_t>(S.span_slots, 1);
         LaunchPlan lp;
         rc = launch_plan(c, c->params, S.max_tok, S.max_lenb, &lp, job.flags);
+        // the cross-block pass of a tick holds a 1024-thread CTA per 32 blocks
+        // at most, so that ticks on other lanes find SMs beside it
+        lp.grid_ext = std::min<int>(lp.grid_ext, (int)std::max<size_t>(1, (nblk + 31) / 32));
         if (rc == ACEAPEX_OK) rc = enqueue_job(c, job, lp, 4, c->d_err, 4, st, nullptr);
     } else if (rc == ACEAPEX_OK) {
         if ((e = cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), st)) != cudaSuccess) rc = cuda_fail(c, e, "server");
@@ -441,38 +535,28 @@ bool aceapex_server::form_tick() {
     if (rc == ACEAPEX_OK &&
         (e = cudaMemcpyAsync(B.h_err, c->d_err, 4 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         rc = cuda_fail(c, e, "server: status copy");
-    Tick t;
-    t.set = set;
     t.reqs.swap(admitted);
-    t.used.assign(T.used.begin(), T.used.end());
-    t.decoded = blocks;
-    if (rc == ACEAPEX_OK) {
-        if (free_events.empty()) {
-            cudaEvent_t ev;
-            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) rc = cuda_fail(c, e, "event");
-            else free_events.push_back(ev);
-        }
+    if (rc == ACEAPEX_OK && (t.done = take_event(&e)) == nullptr) rc = cuda_fail(c, e, "event");
+    if (rc == ACEAPEX_OK && (e = cudaEventRecord(t.done, st)) != cudaSuccess) rc = cuda_fail(c, e, "event");
+    Ln.formed++;
+    Ln.inflight++;
+    {
+        const int64_t t_end = now();
+        std::lock_guard<std::mutex> g(mu);
+        form_ns += t_end - tn;
+        walk_ns += t_walked - tn;
+        ticks++;
+        tick_waits += waited;
+        blk_decoded += nblk;
+        blk_hit += T.used.size() - T.sched.size();
     }
-    if (rc == ACEAPEX_OK) {
-        t.done = free_events.back();
-        free_events.pop_back();
-        if ((e = cudaEventRecord(t.done, st)) != cudaSuccess) {
-            free_events.push_back(t.done);
-            rc = cuda_fail(c, e, "event");
-        }
-    }
-    ticks++;
-    blk_decoded += nblk;
-    blk_hit += T.used.size() - T.sched.size();
     if (rc != ACEAPEX_OK) {
-        // the launch failed: nothing of this tick runs
-        cudaStreamSynchronize(st);
-        t.done = nullptr;
-        const int64_t tn2 = now();
-        for (uint32_t b : t.used) unpin(b);
-        for (uint32_t b : t.decoded)
-            if (pins[b] == 0) drop(b);
-        for (const Req& r : t.reqs) complete(r, rc, tn2);
+        // the launch failed: nothing more is launched; the server stops
+        cudaDeviceSynchronize();
+        if (t.start) free_events.push_back(t.start);
+        if (t.done) free_events.push_back(t.done);
+        t.start = t.done = nullptr;
+        finish_tick(t, rc);
         std::lock_guard<std::mutex> g(mu);
         fatal = rc;
         fatal_msg = c->err;
@@ -485,22 +569,28 @@ bool aceapex_server::form_tick() {
 void aceapex_server::run() {
     cudaSetDevice(c->device);
     while (!stop.load()) {
-        // completed ticks, in order
-        while (!inflight.empty()) {
-            Tick& t = inflight.front();
-            const cudaError_t q = cudaEventQuery(t.done);
-            if (q == cudaErrorNotReady) break;
+        // completed ticks, on any lane
+        for (auto it = inflight.begin(); it != inflight.end();) {
+            const cudaError_t q = cudaEventQuery(it->done);
+            if (q == cudaErrorNotReady) {
+                ++it;
+                continue;
+            }
             int status = ACEAPEX_OK;
             if (q != cudaSuccess) {
                 status = ACEAPEX_E_CUDA;
-            } else if (bufs[t.set].h_err[0]) {
-                status = bufs[t.set].h_err[0];
+            } else if (lanes[it->lane].bufs[it->set].h_err[0]) {
+                status = lanes[it->lane].bufs[it->set].h_err[0];
             }
-            finish_tick(t, status);
-            inflight.pop_front();
+            finish_tick(*it, status);
+            it = inflight.erase(it);
         }
+        // the lane with the fewest ticks in flight, two at most
+        int li = 0;
+        for (int k = 1; k < (int)lanes.size(); k++)
+            if (lanes[k].inflight < lanes[li].inflight) li = k;
         bool launched = false;
-        if (inflight.size() < 2 && !fatal) launched = form_tick();
+        if (lanes[li].inflight < 2 && !fatal) launched = form_tick(li);
         if (launched) continue;
         // nothing to launch: wait briefly for a completion or an arrival
         int64_t next_at = -1;
@@ -526,10 +616,10 @@ void aceapex_server::run() {
         }
     }
     // drain what is on the GPU
-    cudaStreamSynchronize(st);
+    for (Lane& L : lanes) cudaStreamSynchronize(L.st);
     while (!inflight.empty()) {
         Tick& t = inflight.front();
-        finish_tick(t, cudaEventQuery(t.done) == cudaSuccess ? bufs[t.set].h_err[0] : ACEAPEX_E_CUDA);
+        finish_tick(t, cudaEventQuery(t.done) == cudaSuccess ? lanes[t.lane].bufs[t.set].h_err[0] : ACEAPEX_E_CUDA);
         inflight.pop_front();
     }
 }
@@ -548,25 +638,31 @@ static void server_free(aceapex_server* s) {
     s->pool_cv.notify_all();
     for (auto& t : s->pool) t.join();
     if (s->c) cudaSetDevice(s->c->device);
-    if (s->st) cudaStreamSynchronize(s->st);
+    for (Lane& L : s->lanes)
+        if (L.st) cudaStreamSynchronize(L.st);
     for (auto& ev : s->free_events) cudaEventDestroy(ev);
-    for (auto& B : s->bufs) {
-        if (B.h_items) cudaFreeHost(B.h_items);
-        if (B.h_need) cudaFreeHost(B.h_need);
-        if (B.h_gather) cudaFreeHost(B.h_gather);
-        if (B.h_err) cudaFreeHost(B.h_err);
-        B.d_items.release();
-        B.d_need.release();
-        B.d_gather.release();
+    if (s->t0_ev) cudaEventDestroy(s->t0_ev);
+    for (size_t k = 0; k < s->lanes.size(); k++) {
+        Lane& L = s->lanes[k];
+        for (auto& B : L.bufs) {
+            if (B.h_items) cudaFreeHost(B.h_items);
+            if (B.h_need) cudaFreeHost(B.h_need);
+            if (B.h_gather) cudaFreeHost(B.h_gather);
+            if (B.h_err) cudaFreeHost(B.h_err);
+            B.d_items.release();
+            B.d_need.release();
+            B.d_gather.release();
+        }
+        L.streams.release();
+        L.spans.release();
+        L.lists.release();
+        if (L.st) cudaStreamDestroy(L.st);
+        if (k > 0 && L.c) aceapex_ctx_destroy(L.c);  // lane 0 runs on the server's own context
     }
-    s->streams.release();
-    s->spans.release();
-    s->lists.release();
     if (s->cache) cudaFree(s->cache);
     if (s->npend) cudaFree(s->npend);
     if (s->pmap) cudaFree(s->pmap);
     if (s->d_slot) cudaFree(s->d_slot);
-    if (s->st) cudaStreamDestroy(s->st);
     if (s->c) aceapex_ctx_destroy(s->c);
     delete s;
 }
@@ -583,6 +679,11 @@ int aceapex_server_create(aceapex_ctx* ctx, aceapex_archive* A, const aceapex_se
     if (!s->prm.cache_bytes) s->prm.cache_bytes = 4ull << 30;
     if (!s->prm.max_tick_blocks) s->prm.max_tick_blocks = 16384;
     if (!s->prm.max_tick_requests) s->prm.max_tick_requests = 4096;
+    if (!s->prm.streams) s->prm.streams = 2;
+    if (s->prm.streams > 16) {
+        delete s;
+        return fail(ctx, ACEAPEX_E_ARG, "server_create: more than 16 tick streams");
+    }
     s->A = A;
     const uint32_t nb = A->plan.n_blocks;
     s->n_slots = (uint32_t)std::min<uint64_t>(s->prm.cache_bytes / kBlock, 0xfffffff0u);
@@ -600,15 +701,28 @@ int aceapex_server_create(aceapex_ctx* ctx, aceapex_archive* A, const aceapex_se
         server_free(s);
         return rc;
     }
-    cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    s->lanes.resize(s->prm.streams);
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < s->lanes.size() && e == cudaSuccess && rc == 0; k++) {
+        Lane& L = s->lanes[k];
+        if (k == 0) L.c = s->c;
+        else rc = aceapex_ctx_create(ctx->device, &ctx->params, &L.c);
+        if (rc == 0) e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
+        for (auto& B : L.bufs)
+            if (rc == 0 && e == cudaSuccess) e = cudaHostAlloc((void**)&B.h_err, 4 * sizeof(int), cudaHostAllocDefault);
+    }
+    if (rc) {
+        server_free(s);
+        return fail(ctx, rc, "server_create: lane context");
+    }
+    if (e == cudaSuccess) e = cudaEventCreate(&s->t0_ev);
+    if (e == cudaSuccess) e = cudaEventRecord(s->t0_ev, s->lanes[0].st);
     if (e == cudaSuccess) e = cudaMalloc(&s->cache, (size_t)s->n_slots * kBlock);
     if (e == cudaSuccess) e = cudaMalloc(&s->npend, (size_t)s->n_slots * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->pmap, (size_t)s->n_slots * (kBlock / 8));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_slot, (size_t)std::max<uint32_t>(nb, 1) * 4);
     if (e == cudaSuccess) e = cudaMemset(s->d_slot, 0xff, (size_t)std::max<uint32_t>(nb, 1) * 4);
     if (e == cudaSuccess) e = cudaMemset(s->pmap, 0, (size_t)s->n_slots * (kBlock / 8));
-    for (auto& B : s->bufs)
-        if (e == cudaSuccess) e = cudaHostAlloc((void**)&B.h_err, 4 * sizeof(int), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         const bool oom = e == cudaErrorMemoryAllocation;
         server_free(s);
@@ -709,6 +823,10 @@ int aceapex_server_get_stats(aceapex_server* s, int reset, aceapex_server_stats*
     out->ticks = s->ticks;
     out->blocks_decoded = s->blk_decoded;
     out->blocks_hit = s->blk_hit;
+    out->tick_overlaps = s->tick_overlaps;
+    out->tick_waits = s->tick_waits;
+    out->tick_host_ms = (double)s->form_ns / 1e6;
+    out->walk_ms = (double)s->walk_ns / 1e6;
     if (!s->lat_us.empty()) {
         std::vector<double> v = s->lat_us;
         std::sort(v.begin(), v.end());
@@ -734,6 +852,8 @@ int aceapex_server_get_stats(aceapex_server* s, int reset, aceapex_server_stats*
         s->lat_us.clear();
         s->closures.clear();
         s->n_ok = s->n_err = s->n_busy = s->bytes = s->ticks = s->blk_decoded = s->blk_hit = 0;
+        s->tick_overlaps = s->tick_waits = 0;
+        s->form_ns = s->walk_ns = 0;
         s->first_arrival = -1;
         s->last_done = 0;
     }

@@ -85,7 +85,7 @@ class BatchItem(ctypes.Structure):
 
 class ServerParams(ctypes.Structure):
     _fields_ = [("cache_bytes", ctypes.c_uint64), ("max_tick_blocks", ctypes.c_uint32),
-                ("max_tick_requests", ctypes.c_uint32)]
+                ("max_tick_requests", ctypes.c_uint32), ("streams", ctypes.c_uint32)]
 
 
 class Completion(ctypes.Structure):
@@ -97,7 +97,9 @@ class ServerStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("completed", "failed", "refused", "bytes", "ticks", "blocks_decoded",
                                                "blocks_hit")] + \
                [(k, ctypes.c_double) for k in ("p50_us", "p99_us", "mean_us", "max_us", "closure_mean", "closure_p50",
-                                               "closure_p99", "seconds", "gbs")]
+                                               "closure_p99", "seconds", "gbs")] + \
+               [(k, ctypes.c_uint64) for k in ("tick_overlaps", "tick_waits")] + \
+               [(k, ctypes.c_double) for k in ("tick_host_ms", "walk_ms")]
 
 
 class TunePoint(ctypes.Structure):
@@ -419,11 +421,11 @@ class Server:
     archive with a bounded device cache of decoded blocks."""
 
     def __init__(self, ctx: Context, arc: Archive, cache_bytes: int = 0, max_tick_blocks: int = 0,
-                 max_tick_requests: int = 0):
+                 max_tick_requests: int = 0, streams: int = 0):
         self.ctx = ctx
         self.arc = arc
         self._L = ctx._L
-        p = ServerParams(cache_bytes, max_tick_blocks, max_tick_requests)
+        p = ServerParams(cache_bytes, max_tick_blocks, max_tick_requests, streams)
         h = ctypes.c_void_p()
         _check(self._L.aceapex_server_create(ctx.h, arc.h, ctypes.byref(p), ctypes.byref(h)), ctx.h, "server_create")
         self.h = h

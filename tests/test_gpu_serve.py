@@ -149,3 +149,66 @@ def test_admission_refuses_what_can_never_fit(acx, ctx, served):
     with pytest.raises(acx.AceapexError):
         srv.submit(len(ref) - 5, 10, out.data_ptr())
     srv.close()
+
+
+@pytest.fixture(scope="module")
+def segmented(acx, ctx):
+    """An 8 MiB genome encoded in 1 MiB segments (every source inside its
+    segment), so that requests in different segments have disjoint closures."""
+    import torch
+    data = synth.dna((8 << 20) + 777, 41)
+    arc = acx.encode(data, segment=1 << 20)
+    ref = oracle.decode(arc)
+    assert np.array_equal(ref, data)
+    h = np.frombuffer(arc, np.uint8).copy()
+    d = torch.from_numpy(h).to("cuda")
+    A = acx.Archive(ctx, d.data_ptr(), h, h.size)
+    yield ref, A
+    A.close()
+    del d
+
+
+def _one_per_tick(acx, ctx, A, ref, starts, lens, streams, cache_blocks):
+    arena = Arena(lens)
+    srv = acx.Server(ctx, A, cache_bytes=cache_blocks * BLOCK, max_tick_requests=1, streams=streams)
+    srv.submit_many(starts, lens, arena.ptrs())
+    assert srv.drain(60000) == 0, srv.last_error()
+    got = srv.poll(100000)
+    assert len(got) == len(starts) and all(c["status"] == 0 for c in got)
+    st = srv.stats()
+    srv.close()
+    check_all(ref, starts, lens, arena)
+    return st
+
+
+def test_ticks_on_two_lanes_overlap_on_the_device(acx, ctx, segmented):
+    """A burst of one-request ticks that alternate between segments: ticks
+    on the two lanes have disjoint closures, so they run side by side (their
+    device intervals overlap) and none waits for another; every request
+    equals the oracle's bytes.  One lane never overlaps two ticks."""
+    ref, A = segmented
+    rng = np.random.default_rng(5)
+    seg = 1 << 20
+    n = 48
+    starts = np.array([(i % 8) * seg + rng.integers(0, seg - 40000) for i in range(n)], dtype=np.uint64)
+    lens = rng.integers(4096, 32768, n).astype(np.uint64)
+    st2 = _one_per_tick(acx, ctx, A, ref, starts, lens, 2, 600)
+    assert st2["ticks"] == n
+    assert st2["tick_overlaps"] > 0, st2
+    st1 = _one_per_tick(acx, ctx, A, ref, starts, lens, 1, 600)
+    assert st1["tick_overlaps"] == 0 and st1["tick_waits"] == 0, st1
+
+
+def test_ticks_that_share_blocks_are_ordered(acx, ctx, segmented):
+    """One-request ticks on four lanes over one segment, with a cache small
+    enough to evict and decode blocks again: ticks that read blocks another
+    unfinished tick decodes (or decode blocks it reads) wait for it, and
+    every request still equals the oracle's bytes."""
+    ref, A = segmented
+    rng = np.random.default_rng(6)
+    seg = 1 << 20
+    n = 64
+    starts = (3 * seg + rng.integers(0, seg - 40000, n)).astype(np.uint64)
+    lens = rng.integers(1, 40000, n).astype(np.uint64)
+    st = _one_per_tick(acx, ctx, A, ref, starts, lens, 4, 96)
+    assert st["ticks"] == n and st["tick_waits"] > 0, st
