@@ -36,7 +36,7 @@
 
 namespace acx {
 
-__global__ void __launch_bounds__(kLocThreads, 5) k_local(JobDev job) {
+__global__ void __launch_bounds__(kLocThreads, 6) k_local(JobDev job) {
     extern __shared__ __align__(128) uint8_t sm[];
     local_worker(job, sm, 0, threadIdx.x);
 }
@@ -605,6 +605,8 @@ cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st) {
     const size_t sm = local_smem_bytes(job.max_tok, job.max_lenb, (job.flags & kJobNeed) != 0,
                                        (job.flags & kJobLevels) != 0);
     cudaError_t e = cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)  // the whole unified L1 as shared memory: CTAs per SM are set by their workspaces
+        e = cudaFuncSetAttribute(k_local, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     // a small job (a seek, a serving tick) needs no more CTAs than ticket runs
     const uint64_t runs = (job.n_items + (uint64_t)(job.chunk ? job.chunk : 1) - 1) / (job.chunk ? job.chunk : 1);
@@ -629,6 +631,7 @@ cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st) {
 
 int local_occupancy(size_t smem) {
     cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_local, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_local, kLocThreads, smem) != cudaSuccess) return 0;
     return n;

@@ -163,12 +163,15 @@ __device__ __forceinline__ void pend_update_smem(uint32_t* pend, uint32_t s, uin
     }
 }
 
-// Literal run: out[b, b+L) = lit[a, a+L) (both in shared memory), by the
+// Run copy out[b, b+L) = src[a, a+L) (both in shared memory, the two ranges
+// disjoint: a literal run, or an in-block match at distance >= L), by the
 // eight lanes sl = 0..7 of a lane group: 16-byte stores in the middle, each
 // from five funnel-shifted source words, bytes at the ragged ends.  Source
-// words may reach 3 bytes past the run (the literal buffer is padded).
-__device__ __forceinline__ void copy_run8(uint8_t* __restrict__ sout, const uint8_t* __restrict__ lit, uint32_t a,
-                                          uint32_t b, uint32_t L, uint32_t sl) {
+// words may reach 3 bytes past the run, still inside the buffer (the literal
+// buffer is padded; a match source ends at or before its destination, which
+// holds at least 4 bytes); those bytes are shifted out unused.
+__device__ __forceinline__ void copy_run8(uint8_t* sout, const uint8_t* lit, uint32_t a, uint32_t b, uint32_t L,
+                                          uint32_t sl) {
     const uint32_t e = b + L;
     const uint32_t q0 = (b + 15) >> 4, q1 = e >> 4;  // whole 16-byte chunks [q0, q1)
     if (q0 >= q1) {
@@ -581,7 +584,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
                     __threadfence_block();  // source reads after the readiness reads
                     if (ready) {
                         if (d >= ml) {
-                            for (uint32_t k = sl; k < ml; k += 8) sout[o + k] = sout[so + k];
+                            copy_run8(sout, sout, so, o, ml, sl);
                         } else {
                             // out[o+k] = out[so + (k mod d)]: the source window only, so lanes are independent
                             uint32_t r = sl % d;
