@@ -721,7 +721,8 @@ def serve_measure(args, dev):
                    "refused": st_all["refused"], "streams": args.serve_streams,
                    "tick_overlaps": st_all["tick_overlaps"], "tick_waits": st_all["tick_waits"],
                    "host_ms_per_tick": round(st_all["tick_host_ms"] / max(1, st_all["ticks"]), 4),
-                   "walk_ms_per_tick": round(st_all["walk_ms"] / max(1, st_all["ticks"]), 4)},
+                   "walk_ms_per_tick": round(st_all["walk_ms"] / max(1, st_all["ticks"]), 4),
+                   "launch_ms_per_tick": round(st_all["launch_ms"] / max(1, st_all["ticks"]), 4)},
         "verified": f"{smp.size} sampled requests equal the generator's bytes",
         "clocks": clk,
     }
@@ -885,6 +886,8 @@ def main():
         dist["pg"].barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    # the last timed decode's cross-block rounds: (round, list size, start µs)
+    trace = ctx.round_trace() if not args.shard else None
 
     dev_ms = sum(ms_total)
     if dist["pg"]:
@@ -968,7 +971,8 @@ def main():
             "stage_ms": {"ans": round(a_ms, 4), "local_parse_copy": round(s_ms, 4), "cross_block": round(x_ms, 4)},
             "cross_block_stats": {"pending_pieces": last_stats.get("pending_spans"),
                                   "pending_bytes": last_stats.get("pending_bytes"),
-                                  "rounds_after_first": last_stats.get("wait_polls")},
+                                  "rounds_after_first": last_stats.get("wait_polls"),
+                                  "round_trace": trace},
             "parse_stats": parse,
             "roofline": roof,
             "path_roofline": path_roof,

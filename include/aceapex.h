@@ -334,6 +334,7 @@ typedef struct {
     uint64_t tick_waits;      /* ticks that waited for a tick on another lane */
     double tick_host_ms;      /* host time forming the launched ticks (walks, admission, launches) */
     double walk_ms;           /* ... of which closure walks */
+    double launch_ms;         /* ... of which staging, ordering, copies and launches on the lane's stream */
 } aceapex_server_stats;
 
 /* ctx: its device and decoder parameters are used (the server creates its own

@@ -319,7 +319,11 @@ int acx::launch_plan(aceapex_ctx* c, const aceapex_dec_params& p, uint32_t max_t
         const size_t lsm =
             local_smem_bytes(max_tok, max_lenb, (job_flags & kJobNeed) != 0, (job_flags & kJobLevels) != 0);
         if (lsm > 227 * 1024) return fail(c, ACEAPEX_E_CORRUPT, "block too large for the local pass");
-        int occ = std::max(1, local_occupancy(lsm));
+        if (c->occ_local_smem != lsm) {  // (an occupancy query per launch costs the serving ticks host time)
+            c->occ_local = local_occupancy(lsm);
+            c->occ_local_smem = lsm;
+        }
+        int occ = std::max(1, c->occ_local);
         if (p.ctas_per_sm) occ = std::min<int>(occ, (int)p.ctas_per_sm);
         lp->grid_local = occ * c->n_sms;
     }

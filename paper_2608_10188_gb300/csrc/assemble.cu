@@ -92,14 +92,16 @@ __device__ __forceinline__ bool piece_final(const ArcJob& L, uint64_t src, uint3
     return src_final(L, src + phase, src + period) && src_final(L, src, src + (phase + len - period));
 }
 
+constexpr int kCopyBatch = 8;
 // A warp's attempt at its lanes' pieces (lane `has` a piece `rec` of the
 // block in output slot `dslot`, all of archive L).  Each lane checks its own
 // piece; the ready pieces are then copied by the whole warp, lane i moving
 // byte i (one coalesced request per piece), eight pieces' loads in flight
-// before their stores; after one fence (the release) the owners clear the
-// pieces' pending bits with relaxed atomic ANDs.  Returns true on the lanes
+// before their stores (plain pieces of a whole-archive job from addresses
+// their owners publish); after one
+// fence (the release) the owners clear the pieces' pending bits with relaxed
+// atomic ANDs.  Returns true on the lanes
 // whose piece is done.
-constexpr int kCopyBatch = 8;
 __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec rec, SpanRec* wrec, uint64_t* wdst,
                            int lane) {
     const uint64_t src = (uint64_t)rec.x | ((uint64_t)(rec.y & 0xff) << 32);
@@ -107,46 +109,78 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec re
     const bool ready = has && piece_final(L, src, phase, period, len);
     const uint32_t rmask = __ballot_sync(ACX_FULL, ready);
     if (!rmask) return false;
-    __threadfence();  // acquire: the bitmap reads above are ordered before the source reads below
-    wrec[lane] = rec;
-    wdst[lane] = (uint64_t)dslot * kBlock + o;
-    __syncwarp();
+    fence_acq_rel_gpu();  // acquire: the bitmap reads above are ordered before the source reads below
     uint8_t* g = L.out;
     uint32_t m = rmask;
-    while (m) {
-        int ls[kCopyBatch];
-#pragma unroll
-        for (int u = 0; u < kCopyBatch; u++) {
-            ls[u] = m ? __ffs(m) - 1 : -1;
-            if (m) m &= m - 1;
+    if (!L.slot && __all_sync(ACX_FULL, !ready || period == 0)) {
+        // plain pieces of a whole-archive job (the common case): each ready
+        // lane publishes its source and destination addresses and length
+        const uint8_t** wsa = reinterpret_cast<const uint8_t**>(wrec);  // [lane]: source address
+        uint8_t** wda = reinterpret_cast<uint8_t**>(wrec) + 32;         // [lane]: destination address
+        if (ready) {
+            wsa[lane] = g + src;
+            wda[lane] = g + (uint64_t)dslot * kBlock + o;
+            wdst[lane] = len;
         }
-        uint32_t v[(kCopyBatch + 3) / 4];
+        __syncwarp();
+        while (m) {
+            int ls[kCopyBatch];
 #pragma unroll
-        for (int u = 0; u < (kCopyBatch + 3) / 4; u++) v[u] = 0;
+            for (int u = 0; u < kCopyBatch; u++) {
+                ls[u] = m ? __ffs(m) - 1 : -1;
+                if (m) m &= m - 1;
+            }
+            uint32_t v[(kCopyBatch + 3) / 4];
 #pragma unroll
-        for (int u = 0; u < kCopyBatch; u++) {
-            if (ls[u] >= 0) {
-                const SpanRec r = wrec[ls[u]];
-                if ((uint32_t)lane < (r.z >> 16)) {
-                    const uint64_t rs = (uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32);
-                    const uint32_t rp = r.w;
-                    const uint64_t q = rp ? rs + (((r.y >> 8) & 0xffff) + (uint32_t)lane) % rp : rs + lane;
-                    v[u >> 2] |= (uint32_t)__ldcg(g + out_off(L, q)) << (8 * (u & 3));
+            for (int u = 0; u < (kCopyBatch + 3) / 4; u++) v[u] = 0;
+#pragma unroll
+            for (int u = 0; u < kCopyBatch; u++)
+                if (ls[u] >= 0 && (uint32_t)lane < (uint32_t)wdst[ls[u]])
+                    v[u >> 2] |= (uint32_t)__ldcg(wsa[ls[u]] + lane) << (8 * (u & 3));
+#pragma unroll
+            for (int u = 0; u < kCopyBatch; u++)
+                if (ls[u] >= 0 && (uint32_t)lane < (uint32_t)wdst[ls[u]])
+                    wda[ls[u]][lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
+        }
+    } else {
+        wrec[lane] = rec;
+        wdst[lane] = (uint64_t)dslot * kBlock + o;
+        __syncwarp();
+    while (m) {
+            int ls[kCopyBatch];
+#pragma unroll
+            for (int u = 0; u < kCopyBatch; u++) {
+                ls[u] = m ? __ffs(m) - 1 : -1;
+                if (m) m &= m - 1;
+            }
+            uint32_t v[(kCopyBatch + 3) / 4];
+#pragma unroll
+            for (int u = 0; u < (kCopyBatch + 3) / 4; u++) v[u] = 0;
+#pragma unroll
+            for (int u = 0; u < kCopyBatch; u++) {
+                if (ls[u] >= 0) {
+                    const SpanRec r = wrec[ls[u]];
+                    if ((uint32_t)lane < (r.z >> 16)) {
+                        const uint64_t rs = (uint64_t)r.x | ((uint64_t)(r.y & 0xff) << 32);
+                        const uint32_t rp = r.w;
+                        const uint64_t q = rp ? rs + (((r.y >> 8) & 0xffff) + (uint32_t)lane) % rp : rs + lane;
+                        v[u >> 2] |= (uint32_t)__ldcg(g + out_off(L, q)) << (8 * (u & 3));
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < kCopyBatch; u++) {
-            if (ls[u] >= 0) {
-                const uint32_t rl = wrec[ls[u]].z >> 16;
-                if ((uint32_t)lane < rl) g[wdst[ls[u]] + lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
+            for (int u = 0; u < kCopyBatch; u++) {
+                if (ls[u] >= 0) {
+                    const uint32_t rl = wrec[ls[u]].z >> 16;
+                    if ((uint32_t)lane < rl) g[wdst[ls[u]] + lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
+                }
             }
         }
     }
     // release: every lane's stores (to other lanes' pieces too) happen before
     // the warp's fence, and the fence before any owner clears its bits
     __syncwarp();
-    __threadfence();
+    fence_acq_rel_gpu();
     if (ready) {
         uint32_t* pm = L.pmap + (uint64_t)dslot * (kBlock / 32);
         for (uint32_t w = o >> 5; w <= ((o + len - 1) >> 5); w++) red_and_relaxed(pm + w, ~range_mask(w, o, o + len));
@@ -500,9 +534,19 @@ __global__ void __launch_bounds__(kExtThreads) k_external(JobDev job) {
             uint32_t idle = __ballot_sync(ACX_FULL, !has);
             while (idle && !exhausted) {
                 if (next >= cnt) {
-                    if (lane == 0) item = atomicAdd(&job.counters[2], lv ? 32u : 1u);
-                    item = __shfl_sync(ACX_FULL, item, 0);
-                    if (lv) {  // the next 32 entries of the level list
+                    if (lv) {
+                        // the next 32 entries of the level list: chunk t * kLvStripes + k
+                        // from stripe k's counter, so that the hand-out is not one
+                        // counter's atomics in a row (the order stays the list's, up to
+                        // how far the stripes drift apart)
+                        const uint32_t k = (threadIdx.x >> 5) & (kLvStripes - 1);  // (with 32 warps a CTA: every stripe in every CTA)
+                        if (lane == 0) item = atomicAdd(&job.counters[kLvTickets + k], 1u);
+                        item = (__shfl_sync(ACX_FULL, item, 0) * kLvStripes + k) * 32;
+                    } else {
+                        if (lane == 0) item = atomicAdd(&job.counters[2], 1u);
+                        item = __shfl_sync(ACX_FULL, item, 0);
+                    }
+                    if (lv) {
                         if (item >= n_lv) { exhausted = true; break; }
                         base = item;
                         cnt = min(32u, n_lv - item);

@@ -85,6 +85,11 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// Acquire-release fence at GPU scope: with relaxed loads before it, an
+// acquire pattern; with relaxed writes after it, a release pattern (neither
+// needs the sequentially consistent fence that __threadfence() is).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // Atomic AND without ordering of its own: after a fence (fence + strong write
 // is a release pattern), several of them share that one fence.
 __device__ __forceinline__ void red_and_relaxed(uint32_t* p, uint32_t v) {

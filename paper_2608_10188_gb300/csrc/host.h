@@ -76,6 +76,8 @@ struct aceapex_ctx {
     cudaStream_t s_up = nullptr, s_down = nullptr;  // decode_host: upload and download streams
     std::vector<cudaEvent_t> pipe_ev;              // decode_host: per chunk, uploaded and decoded
     int occ_rans = 0, occ_ext = 0, occ_plain = 0;
+    size_t occ_local_smem = 0;  // the local pass's CTAs per SM for its last workspace size
+    int occ_local = 0;
 };
 
 struct aceapex_archive {

@@ -108,6 +108,8 @@ struct ArcJob {
 constexpr uint32_t kMaxArcsPerJob = 3000;  // rANS tickets [3, 3 + n_arcs) stay below kTrace
 constexpr uint32_t kTrace = 3800;        // [kTrace + 3r]: cross-block round r list size, start time lo, hi
 constexpr uint32_t kTraceRounds = 64;
+constexpr uint32_t kLvStripes = 8;       // level-order hand-out: striped ticket counters
+constexpr uint32_t kLvTickets = 4000;    // [kLvTickets, + kLvStripes): their counts
 constexpr uint32_t kListCnt = 4086;      // [kListCnt + 0/1]: entries of the two cross-block work lists
 constexpr uint32_t kBarCount = 4088;     // grid barrier arrivals
 constexpr uint32_t kBarGen = 4089;       // grid barrier generation

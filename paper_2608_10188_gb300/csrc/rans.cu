@@ -12,6 +12,7 @@ namespace acx {
 __global__ void k_prologue(uint32_t* counters, uint32_t n_counters, int* errs, uint32_t n_errs) {
     for (uint32_t i = threadIdx.x; i < n_counters; i += blockDim.x) counters[i] = 0;
     for (uint32_t i = threadIdx.x; i < n_errs; i += blockDim.x) errs[i] = 0;
+    if (threadIdx.x < kLvStripes) counters[kLvTickets + threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         counters[kStatPending] = 0;
         counters[kStatPolls] = 0;

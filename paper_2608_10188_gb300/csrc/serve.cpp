@@ -170,7 +170,7 @@ struct aceapex_server {
     std::vector<uint32_t> closures;
     uint64_t n_ok = 0, n_err = 0, n_busy = 0, bytes = 0, ticks = 0, blk_decoded = 0, blk_hit = 0;
     uint64_t tick_overlaps = 0, tick_waits = 0;
-    int64_t form_ns = 0, walk_ns = 0;  // host time spent forming the launched ticks, and in their closure walks
+    int64_t form_ns = 0, walk_ns = 0, launch_ns = 0;  // host time forming the launched ticks; in their walks; in their launches
     int64_t first_arrival = -1, last_done = 0;
 
     int64_t now() const {
@@ -444,6 +444,7 @@ bool aceapex_server::form_tick(int li) {
     cudaError_t e;
     int rc = ACEAPEX_OK;
     const size_t nblk = blocks.size(), nreq = admitted.size();
+    const int64_t t_launch = now();
     if ((e = host_grow((void**)&B.h_items, &B.cap_items, std::max<size_t>(nblk, 1), sizeof(ItemDev))) != cudaSuccess ||
         (e = host_grow((void**)&B.h_need, &B.cap_need, std::max<size_t>(need.size(), 1), sizeof(uint32_t))) != cudaSuccess ||
         (e = host_grow((void**)&B.h_gather, &B.cap_gather, nreq, sizeof(GatherReq))) != cudaSuccess ||
@@ -545,6 +546,7 @@ bool aceapex_server::form_tick(int li) {
         std::lock_guard<std::mutex> g(mu);
         form_ns += t_end - tn;
         walk_ns += t_walked - tn;
+        launch_ns += t_end - t_launch;
         ticks++;
         tick_waits += waited;
         blk_decoded += nblk;
@@ -827,6 +829,7 @@ int aceapex_server_get_stats(aceapex_server* s, int reset, aceapex_server_stats*
     out->tick_waits = s->tick_waits;
     out->tick_host_ms = (double)s->form_ns / 1e6;
     out->walk_ms = (double)s->walk_ns / 1e6;
+    out->launch_ms = (double)s->launch_ns / 1e6;
     if (!s->lat_us.empty()) {
         std::vector<double> v = s->lat_us;
         std::sort(v.begin(), v.end());
@@ -853,7 +856,7 @@ int aceapex_server_get_stats(aceapex_server* s, int reset, aceapex_server_stats*
         s->closures.clear();
         s->n_ok = s->n_err = s->n_busy = s->bytes = s->ticks = s->blk_decoded = s->blk_hit = 0;
         s->tick_overlaps = s->tick_waits = 0;
-        s->form_ns = s->walk_ns = 0;
+        s->form_ns = s->walk_ns = s->launch_ns = 0;
         s->first_arrival = -1;
         s->last_done = 0;
     }

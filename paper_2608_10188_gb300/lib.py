@@ -99,7 +99,7 @@ class ServerStats(ctypes.Structure):
                [(k, ctypes.c_double) for k in ("p50_us", "p99_us", "mean_us", "max_us", "closure_mean", "closure_p50",
                                                "closure_p99", "seconds", "gbs")] + \
                [(k, ctypes.c_uint64) for k in ("tick_overlaps", "tick_waits")] + \
-               [(k, ctypes.c_double) for k in ("tick_host_ms", "walk_ms")]
+               [(k, ctypes.c_double) for k in ("tick_host_ms", "walk_ms", "launch_ms")]
 
 
 class TunePoint(ctypes.Structure):
@@ -170,6 +170,8 @@ def load(path: str | None = None):
     L.aceapex_autotune.argtypes = [vp, c.POINTER(BatchItem), c.c_int, c.c_int, c.POINTER(TunePoint), c.c_int,
                                    c.POINTER(c.c_int), c.POINTER(DecParams)]
     L.aceapex_batch_decode.argtypes = [vp, c.POINTER(BatchItem), c.c_int, vp, c.POINTER(Stats)]
+    L.acx_debug_counters.argtypes = [vp, vp, u32]
+    L.acx_debug_counters.restype = c.c_int
     for name in EXPORTED:
         if name not in ("aceapex_status_string", "aceapex_last_error", "aceapex_free", "aceapex_server_now_ns",
                         "aceapex_server_last_error"):
@@ -251,6 +253,23 @@ class Context:
 
     def sync(self, stream: int = 0) -> int:
         return self._L.aceapex_sync(self.h, stream)
+
+    def round_trace(self):
+        """Diagnostics of the last whole decode on this context: the
+        cross-block pass's rounds as (round, pieces in its list, start in µs
+        after round 0 began); round 0 has no list."""
+        import numpy as np
+        cn = np.zeros(4096, np.uint32)
+        if self._L.acx_debug_counters(self.h, cn.ctypes.data, cn.size) != 0:
+            return None
+        base, rows = 3800, []  # the trace words of the counter block
+        t0 = int(cn[base + 1]) | (int(cn[base + 2]) << 32)
+        for r in range(64):
+            t = int(cn[base + 3 * r + 1]) | (int(cn[base + 3 * r + 2]) << 32)
+            if t == 0 or t < t0:
+                break
+            rows.append((r, int(cn[base + 3 * r]), round((t - t0) / 1e3, 1)))
+        return rows
 
 
 class Archive:
