@@ -97,11 +97,10 @@ constexpr int kCopyBatch = 8;
 // block in output slot `dslot`, all of archive L).  Each lane checks its own
 // piece; the ready pieces are then copied by the whole warp, lane i moving
 // byte i (one coalesced request per piece), eight pieces' loads in flight
-// before their stores (plain pieces of a whole-archive job from addresses
-// their owners publish); after one
-// fence (the release) the owners clear the pieces' pending bits with relaxed
-// atomic ANDs.  Returns true on the lanes
-// whose piece is done.
+// before their stores (in a whole-archive job from addresses that the
+// pieces' owners publish); after one fence (the release) the owners clear
+// the pieces' pending bits with relaxed atomic ANDs.  Returns true on the
+// lanes whose piece is done.
 __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec rec, SpanRec* wrec, uint64_t* wdst,
                            int lane) {
     const uint64_t src = (uint64_t)rec.x | ((uint64_t)(rec.y & 0xff) << 32);
@@ -112,41 +111,52 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec re
     fence_acq_rel_gpu();  // acquire: the bitmap reads above are ordered before the source reads below
     uint8_t* g = L.out;
     uint32_t m = rmask;
-    if (!L.slot && __all_sync(ACX_FULL, !ready || period == 0)) {
-        // plain pieces of a whole-archive job (the common case): each ready
-        // lane publishes its source and destination addresses and length
-        const uint8_t** wsa = reinterpret_cast<const uint8_t**>(wrec);  // [lane]: source address
-        uint8_t** wda = reinterpret_cast<uint8_t**>(wrec) + 32;         // [lane]: destination address
+    if (!L.slot) {
+        // a whole-archive job (blocks at their own offsets): each ready lane
+        // publishes its piece's source and destination addresses, length and
+        // period in the slot of its rank among the ready lanes, and the warp
+        // walks the slots in order
+        const uint8_t** wsa = reinterpret_cast<const uint8_t**>(wrec);  // [rank]: source address
+        uint8_t** wda = reinterpret_cast<uint8_t**>(wrec) + 32;         // [rank]: destination address
+        uint32_t* wln = reinterpret_cast<uint32_t*>(wdst);              // [rank]: length
+        uint32_t* wpp = wln + 32;                                        // [rank]: phase | period << 16
         if (ready) {
-            wsa[lane] = g + src;
-            wda[lane] = g + (uint64_t)dslot * kBlock + o;
-            wdst[lane] = len;
+            const uint32_t r = __popc(rmask & ((1u << lane) - 1));
+            wsa[r] = g + src;
+            wda[r] = g + (uint64_t)dslot * kBlock + o;
+            wln[r] = len;
+            wpp[r] = period ? phase | period << 16 : 0u;
         }
         __syncwarp();
-        while (m) {
-            int ls[kCopyBatch];
-#pragma unroll
-            for (int u = 0; u < kCopyBatch; u++) {
-                ls[u] = m ? __ffs(m) - 1 : -1;
-                if (m) m &= m - 1;
-            }
+        const uint32_t nr = __popc(rmask);
+        for (uint32_t b0 = 0; b0 < nr; b0 += kCopyBatch) {
             uint32_t v[(kCopyBatch + 3) / 4];
 #pragma unroll
             for (int u = 0; u < (kCopyBatch + 3) / 4; u++) v[u] = 0;
+            uint32_t mine = 0;  // bit u: this lane moves a byte of piece b0 + u
 #pragma unroll
             for (int u = 0; u < kCopyBatch; u++)
-                if (ls[u] >= 0 && (uint32_t)lane < (uint32_t)wdst[ls[u]])
-                    v[u >> 2] |= (uint32_t)__ldcg(wsa[ls[u]] + lane) << (8 * (u & 3));
+                if (b0 + u < nr && (uint32_t)lane < wln[b0 + u]) {
+                    // byte k of a periodic piece reads residue (phase + k) mod period
+                    const uint32_t pp = wpp[b0 + u];
+                    uint32_t k = lane;
+                    if (pp) {
+                        const uint32_t per = pp >> 16;
+                        k += pp & 0xffff;
+                        k = k < per ? k : per >= 32 ? k - per : k % per;
+                    }
+                    v[u >> 2] |= (uint32_t)__ldcg(wsa[b0 + u] + k) << (8 * (u & 3));
+                    mine |= 1u << u;
+                }
 #pragma unroll
             for (int u = 0; u < kCopyBatch; u++)
-                if (ls[u] >= 0 && (uint32_t)lane < (uint32_t)wdst[ls[u]])
-                    wda[ls[u]][lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
+                if (mine >> u & 1) wda[b0 + u][lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
         }
     } else {
         wrec[lane] = rec;
         wdst[lane] = (uint64_t)dslot * kBlock + o;
         __syncwarp();
-    while (m) {
+        while (m) {
             int ls[kCopyBatch];
 #pragma unroll
             for (int u = 0; u < kCopyBatch; u++) {
