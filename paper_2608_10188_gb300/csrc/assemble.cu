@@ -93,6 +93,7 @@ __device__ __forceinline__ bool piece_final(const ArcJob& L, uint64_t src, uint3
 }
 
 constexpr int kCopyBatch = 8;
+constexpr int kPlainBatch = 8;  // loads in flight before their stores, published-address copies (16: no faster)
 // A warp's attempt at its lanes' pieces (lane `has` a piece `rec` of the
 // block in output slot `dslot`, all of archive L).  Each lane checks its own
 // piece; the ready pieces are then copied by the whole warp, lane i moving
@@ -129,28 +130,49 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec re
         }
         __syncwarp();
         const uint32_t nr = __popc(rmask);
-        for (uint32_t b0 = 0; b0 < nr; b0 += kCopyBatch) {
-            uint32_t v[(kCopyBatch + 3) / 4];
+        if (!__any_sync(ACX_FULL, ready && period != 0)) {
+            // no periodic piece: the walk is branch-free (predicated loads and stores)
+            for (uint32_t b0 = 0; b0 < nr; b0 += kPlainBatch) {
+                uint32_t v[kPlainBatch / 4];
 #pragma unroll
-            for (int u = 0; u < (kCopyBatch + 3) / 4; u++) v[u] = 0;
-            uint32_t mine = 0;  // bit u: this lane moves a byte of piece b0 + u
+                for (int u = 0; u < kPlainBatch / 4; u++) v[u] = 0;
+                uint32_t mine = 0;  // bit u: this lane moves a byte of piece b0 + u
 #pragma unroll
-            for (int u = 0; u < kCopyBatch; u++)
-                if (b0 + u < nr && (uint32_t)lane < wln[b0 + u]) {
-                    // byte k of a periodic piece reads residue (phase + k) mod period
-                    const uint32_t pp = wpp[b0 + u];
-                    uint32_t k = lane;
-                    if (pp) {
-                        const uint32_t per = pp >> 16;
-                        k += pp & 0xffff;
-                        k = k < per ? k : per >= 32 ? k - per : k % per;
-                    }
-                    v[u >> 2] |= (uint32_t)__ldcg(wsa[b0 + u] + k) << (8 * (u & 3));
-                    mine |= 1u << u;
+                for (int u = 0; u < kPlainBatch; u++) {
+                    const uint32_t i = (b0 + u) & 31;
+                    const bool p = b0 + u < nr && (uint32_t)lane < wln[i];
+                    const uint32_t b = p ? (uint32_t)__ldcg(wsa[i] + lane) : 0u;
+                    v[u >> 2] |= b << (8 * (u & 3));
+                    mine |= (uint32_t)p << u;
                 }
 #pragma unroll
-            for (int u = 0; u < kCopyBatch; u++)
-                if (mine >> u & 1) wda[b0 + u][lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
+                for (int u = 0; u < kPlainBatch; u++)
+                    if (mine >> u & 1) wda[(b0 + u) & 31][lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
+            }
+        } else {
+            for (uint32_t b0 = 0; b0 < nr; b0 += kPlainBatch) {
+                uint32_t v[kPlainBatch / 4];
+#pragma unroll
+                for (int u = 0; u < kPlainBatch / 4; u++) v[u] = 0;
+                uint32_t mine = 0;
+#pragma unroll
+                for (int u = 0; u < kPlainBatch; u++)
+                    if (b0 + u < nr && (uint32_t)lane < wln[b0 + u]) {
+                        // byte k of a periodic piece reads residue (phase + k) mod period
+                        const uint32_t pp = wpp[b0 + u];
+                        uint32_t k = lane;
+                        if (pp) {
+                            const uint32_t per = pp >> 16;
+                            k += pp & 0xffff;
+                            k = k < per ? k : per >= 32 ? k - per : k % per;
+                        }
+                        v[u >> 2] |= (uint32_t)__ldcg(wsa[b0 + u] + k) << (8 * (u & 3));
+                        mine |= 1u << u;
+                    }
+#pragma unroll
+                for (int u = 0; u < kPlainBatch; u++)
+                    if (mine >> u & 1) wda[b0 + u][lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
+            }
         }
     } else {
         wrec[lane] = rec;
