@@ -119,60 +119,41 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec re
         // walks the slots in order
         const uint8_t** wsa = reinterpret_cast<const uint8_t**>(wrec);  // [rank]: source address
         uint8_t** wda = reinterpret_cast<uint8_t**>(wrec) + 32;         // [rank]: destination address
-        uint32_t* wln = reinterpret_cast<uint32_t*>(wdst);              // [rank]: length
-        uint32_t* wpp = wln + 32;                                        // [rank]: phase | period << 16
+        uint32_t* wln = reinterpret_cast<uint32_t*>(wdst);              // [rank]: length | phase << 8
+        uint32_t* wpp = wln + 32;                                        // [rank]: period | M << 16
         if (ready) {
             const uint32_t r = __popc(rmask & ((1u << lane) - 1));
             wsa[r] = g + src;
             wda[r] = g + (uint64_t)dslot * kBlock + o;
-            wln[r] = len;
-            wpp[r] = period ? phase | period << 16 : 0u;
+            wln[r] = len | phase << 8;
+            // a period below 32 takes the residue by a multiply-shift: for
+            // x < 64, (x * ceil(2048 / p)) >> 11 is floor(x / p)
+            wpp[r] = period | (period && period < 32 ? ((2047 + period) / period) << 16 : 0u);
         }
         __syncwarp();
         const uint32_t nr = __popc(rmask);
-        if (!__any_sync(ACX_FULL, ready && period != 0)) {
-            // no periodic piece: the walk is branch-free (predicated loads and stores)
-            for (uint32_t b0 = 0; b0 < nr; b0 += kPlainBatch) {
-                uint32_t v[kPlainBatch / 4];
+        // the walk is branch-free: predicated loads and stores, selects for
+        // the residue of a periodic piece (byte k reads (phase + k) mod period;
+        // phase < period, so with a period of 32 or more one subtraction does)
+        for (uint32_t b0 = 0; b0 < nr; b0 += kPlainBatch) {
+            uint32_t v[kPlainBatch / 4];
 #pragma unroll
-                for (int u = 0; u < kPlainBatch / 4; u++) v[u] = 0;
-                uint32_t mine = 0;  // bit u: this lane moves a byte of piece b0 + u
+            for (int u = 0; u < kPlainBatch / 4; u++) v[u] = 0;
+            uint32_t mine = 0;  // bit u: this lane moves a byte of piece b0 + u
 #pragma unroll
-                for (int u = 0; u < kPlainBatch; u++) {
-                    const uint32_t i = (b0 + u) & 31;
-                    const bool p = b0 + u < nr && (uint32_t)lane < wln[i];
-                    const uint32_t b = p ? (uint32_t)__ldcg(wsa[i] + lane) : 0u;
-                    v[u >> 2] |= b << (8 * (u & 3));
-                    mine |= (uint32_t)p << u;
-                }
-#pragma unroll
-                for (int u = 0; u < kPlainBatch; u++)
-                    if (mine >> u & 1) wda[(b0 + u) & 31][lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
+            for (int u = 0; u < kPlainBatch; u++) {
+                const uint32_t i = (b0 + u) & 31;
+                const uint32_t a = wln[i], pp = wpp[i];
+                const uint32_t per = pp & 0xffff, M = pp >> 16, x = (uint32_t)lane + (a >> 8);
+                const uint32_t k = M ? x - per * ((x * M) >> 11) : (per && x >= per ? x - per : x);
+                const bool p = b0 + u < nr && (uint32_t)lane < (a & 0xff);
+                const uint32_t b = p ? (uint32_t)__ldcg(wsa[i] + k) : 0u;
+                v[u >> 2] |= b << (8 * (u & 3));
+                mine |= (uint32_t)p << u;
             }
-        } else {
-            for (uint32_t b0 = 0; b0 < nr; b0 += kPlainBatch) {
-                uint32_t v[kPlainBatch / 4];
 #pragma unroll
-                for (int u = 0; u < kPlainBatch / 4; u++) v[u] = 0;
-                uint32_t mine = 0;
-#pragma unroll
-                for (int u = 0; u < kPlainBatch; u++)
-                    if (b0 + u < nr && (uint32_t)lane < wln[b0 + u]) {
-                        // byte k of a periodic piece reads residue (phase + k) mod period
-                        const uint32_t pp = wpp[b0 + u];
-                        uint32_t k = lane;
-                        if (pp) {
-                            const uint32_t per = pp >> 16;
-                            k += pp & 0xffff;
-                            k = k < per ? k : per >= 32 ? k - per : k % per;
-                        }
-                        v[u >> 2] |= (uint32_t)__ldcg(wsa[b0 + u] + k) << (8 * (u & 3));
-                        mine |= 1u << u;
-                    }
-#pragma unroll
-                for (int u = 0; u < kPlainBatch; u++)
-                    if (mine >> u & 1) wda[b0 + u][lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
-            }
+            for (int u = 0; u < kPlainBatch; u++)
+                if (mine >> u & 1) wda[(b0 + u) & 31][lane] = (uint8_t)(v[u >> 2] >> (8 * (u & 3)));
         }
     } else {
         wrec[lane] = rec;
