@@ -212,7 +212,11 @@ int aceapex_archive_get_info(const aceapex_archive* arc, aceapex_archive_info* i
  * size) — the paper's full device-resident decode (Table 2: ANS + parse +
  * copy).  Enqueued on `stream`; the _async variant returns after enqueueing
  * (errors accumulate in the context until aceapex_sync), the plain variant
- * synchronises the stream and returns the decode status.
+ * synchronises the stream and returns the decode status.  The cross-block
+ * pass is a cooperative launch; the library orders all of its cooperative
+ * launches on a device (each waits, on its stream, for the previous one to
+ * complete), so decodes on different streams or contexts overlap in their
+ * other stages only.  (Launches recorded into a CUDA graph are not ordered.)
  */
 int aceapex_decode_all(aceapex_ctx* ctx, aceapex_archive* arc, void* d_out, uint64_t out_cap, void* stream,
                        aceapex_stats* stats);

@@ -31,6 +31,8 @@
 //   empty, each round finishing at least the lowest span.
 #include <algorithm>
 
+#include <mutex>
+
 #include "launch.h"
 #include "local_dev.cuh"
 
@@ -44,8 +46,9 @@ __global__ void __launch_bounds__(kLocThreads, 6) k_local(JobDev job) {
 // ---- cross-block pass --------------------------------------------------------------------
 // Are the bytes [s, e) (absolute) final?  The local pass writes every
 // block's pending-byte bitmap; a clear bit means a final byte.  The loads are
-// relaxed: a caller that goes on to read the bytes issues one fence first
-// (strong read + fence = acquire pattern), so a failed poll costs no fence.
+// acquire loads: a lane that sees its piece's source bits clear is ordered
+// after the release that cleared them, and the warp barrier before the copy
+// carries that order to the lanes that read the bytes (no fence per attempt).
 // A range of at most 32 bytes (every piece) covers at most two bitmap words,
 // possibly of two blocks: both are loaded before either is tested.
 __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t e) {
@@ -58,8 +61,8 @@ __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t 
         const uint32_t* p1 = L.pmap + s1 * (kBlock / 32) + (o1 >> 5);
         const uint32_t lo0 = 0xffffffffu << (o0 & 31);         // bits from o0 on in its word
         const uint32_t hi1 = 0xffffffffu >> (31 - (o1 & 31));  // bits up to o1 in its word
-        if (p0 == p1) return (ld_relaxed_u32(p0) & lo0 & hi1) == 0;
-        const uint32_t w0 = ld_relaxed_u32(p0), w1 = ld_relaxed_u32(p1);
+        if (p0 == p1) return (ld_acquire_u32(p0) & lo0 & hi1) == 0;
+        const uint32_t w0 = ld_acquire_u32(p0), w1 = ld_acquire_u32(p1);
         return ((w0 & lo0) | (w1 & hi1)) == 0;
     }
     for (uint64_t a = s >> 14; a <= (e - 1) >> 14; a++) {
@@ -70,7 +73,7 @@ __device__ __forceinline__ bool src_final(const ArcJob& L, uint64_t s, uint64_t 
         if (sl == kNoSlot) return false;
         const uint32_t* pm = L.pmap + sl * (kBlock / 32);
         for (uint32_t w = lo >> 5; w <= ((hi - 1) >> 5); w++)
-            if (ld_relaxed_u32(pm + w) & range_mask(w, lo, hi)) return false;  // pairs with the fenced clears
+            if (ld_acquire_u32(pm + w) & range_mask(w, lo, hi)) return false;  // pairs with the released clears
     }
     return true;
 }
@@ -109,7 +112,6 @@ __device__ bool try_pieces(bool has, const ArcJob& L, uint32_t dslot, SpanRec re
     const bool ready = has && piece_final(L, src, phase, period, len);
     const uint32_t rmask = __ballot_sync(ACX_FULL, ready);
     if (!rmask) return false;
-    fence_acq_rel_gpu();  // acquire: the bitmap reads above are ordered before the source reads below
     uint8_t* g = L.out;
     uint32_t m = rmask;
     if (!L.slot) {
@@ -672,18 +674,62 @@ cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Cooperative launches (the cross-block pass, the fused decode) run one at a
+// time on a device.  A cooperative grid waits at its grid barriers (and its
+// lanes on one another's pieces) for CTAs that must all be resident; two such
+// grids launched on different streams, each holding part of the SMs, could
+// wait for CTAs that cannot start until the other grid ends.  So every
+// cooperative launch of the process waits for the completion event of the
+// previous one on the same device and records it anew.  A stream that is
+// being captured into a graph is left alone (its graph runs its passes on one
+// stream).
+namespace {
+std::mutex g_coop_mu;
+constexpr int kCoopDevices = 64;
+cudaEvent_t g_coop_ev[kCoopDevices] = {};
+}  // namespace
+
+cudaError_t coop_ordered(cudaStream_t st, cudaError_t (*launch)(void*), void* arg) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    if (cs != cudaStreamCaptureStatusNone || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kCoopDevices)
+        return launch(arg);
+    std::lock_guard<std::mutex> g(g_coop_mu);
+    cudaEvent_t& ev = g_coop_ev[dev];
+    if (!ev) {
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            ev = nullptr;
+            return e;
+        }
+    } else if ((e = cudaStreamWaitEvent(st, ev, 0)) != cudaSuccess) {
+        return e;
+    }
+    if ((e = launch(arg)) != cudaSuccess) return e;
+    return cudaEventRecord(ev, st);
+}
+
 cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kExtThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_external, job);
+    struct Arg {
+        const JobDev* job;
+        int grid;
+        cudaStream_t st;
+    } a{&job, grid, st};
+    return coop_ordered(st, [](void* p) -> cudaError_t {
+        const Arg* a = static_cast<const Arg*>(p);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(a->grid);
+        cfg.blockDim = dim3(kExtThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = a->st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_external, *a->job);
+    }, &a);
 }
 
 int local_occupancy(size_t smem) {

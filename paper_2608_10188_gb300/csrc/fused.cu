@@ -109,17 +109,26 @@ cudaError_t launch_fused(const JobDev& job, int G, int grid, cudaStream_t st) {
     const FusedLayout F = fused_layout(job.max_tok, job.max_lenb, G, (job.flags & kJobLevels) != 0);
     cudaError_t e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F.total);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(32 * (kFusedRansWarps + kLocWarps * G));
-    cfg.dynamicSmemBytes = F.total;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_fused, job, G);
+    struct Arg {
+        const JobDev* job;
+        int G, grid;
+        size_t smem;
+        cudaStream_t st;
+    } a{&job, G, grid, F.total, st};
+    return coop_ordered(st, [](void* p) -> cudaError_t {
+        const Arg* a = static_cast<const Arg*>(p);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(a->grid);
+        cfg.blockDim = dim3(32 * (kFusedRansWarps + kLocWarps * a->G));
+        cfg.dynamicSmemBytes = a->smem;
+        cfg.stream = a->st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_fused, *a->job, a->G);
+    }, &a);
 }
 
 int fused_occupancy(int G, uint32_t max_tok, uint32_t max_lenb, bool lvl) {

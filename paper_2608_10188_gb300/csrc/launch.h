@@ -17,6 +17,10 @@ cudaError_t launch_local(const JobDev& job, int grid, cudaStream_t st);
 // Cooperative launch (every CTA resident); recorded as a cooperative kernel
 // node when the stream is being captured into a graph.
 cudaError_t launch_external(const JobDev& job, int grid, cudaStream_t st);
+// Run launch(arg) (a cooperative launch on st) after the previous cooperative
+// launch of this process on the current device has completed, and make it the
+// one the next waits for (see assemble.cu).
+cudaError_t coop_ordered(cudaStream_t st, cudaError_t (*launch)(void*), void* arg);
 // The level list of a level-ordered job (kJobLevels): a per-level scan over
 // the items, then one warp per item writes its pieces' entries.
 cudaError_t launch_level_list(const JobDev& job, cudaStream_t st);
