@@ -431,46 +431,64 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
         any_rep = grp_or(bid, any_rep && !bad);
         mark(misc[1] != 0, kStageSources);
 
-        // ---- the 4-entry history as a monoid scan (blocks with repeat codes only) ----
-        if (any_rep && !bad) {
-            HMap* hbuf = reinterpret_cast<HMap*>(sout);  // the block buffer is free until literal placement
-            HMap agg = kHIdentity;
-            for (uint32_t i = i0; i < i1; i++) agg = hmap_step(agg, tcmd[i], i);
-            // inclusive scan of the maps: shuffles inside each warp, then the
-            // warps' totals (earlier maps act first)
-            HMap inc = agg;
+        // ---- the four-entry history (blocks with repeat codes only) as a
+        //      warp-level scan of packed maps by warp 0, while the other warps
+        //      place the literals, which need positions only (a parse-only job
+        //      places none) ----
+        const bool place = !bad && !(job.flags & kJobIndex);
+        if (!bad && (any_rep || place)) {
+            if (any_rep && warp == 0) {
+                const uint32_t per = (n + 31) / 32;
+                const uint32_t j0 = min(n, lane * per), j1 = min(n, j0 + per);
+                HMap agg = kHIdentity;
+                for (uint32_t i = j0; i < j1; i++) agg = hmap_step(agg, tcmd[i], i);
+                // inclusive scan of the lanes' maps (earlier maps act first)
+                HMap inc = agg;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const HMap prev = __shfl_up_sync(ACX_FULL, inc, o);
-                if (lane >= o) inc = hmap_compose(prev, inc);
-            }
-            if (lane == 31) hbuf[warp] = inc;
-            grp_sync(bid);
-            HMap pre = kHIdentity;
-            for (int w = 0; w < warp; w++) pre = hmap_compose(pre, hbuf[w]);
-            const HMap ex = __shfl_up_sync(ACX_FULL, inc, 1);
-            if (lane > 0) pre = hmap_compose(pre, ex);
-            // the history before this thread's tokens: the block starts from
-            // (1, 2, 3, 4); a NEW token's entry is its distance
-            uint64_t h[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t x = (uint32_t)(pre >> (16 * k)) & 0xffff;
-                h[k] = (x & kHRef) ? (uint64_t)((x & 3) + 1) : B + tpos[x] + tll[x] - tsrc[x];
-            }
-            for (uint32_t i = i0; i < i1; i++) {
-                const uint8_t c = tcmd[i];
-                const uint64_t dst = B + tpos[i] + tll[i];
-                if (c == kNew) {
-                    h[3] = h[2]; h[2] = h[1]; h[1] = h[0]; h[0] = dst - tsrc[i];
-                } else if (c >= 1 && c <= 4) {
-                    const int j = c - 1;
-                    const uint64_t d = h[j];
-                    if (d < 1 || d > dst) misc[1] = 1;
-                    tsrc[i] = dst - d;
-                    for (int k = j; k > 0; k--) h[k] = h[k - 1];
-                    h[0] = d;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const HMap prev = __shfl_up_sync(ACX_FULL, inc, o);
+                    if (lane >= o) inc = hmap_compose(prev, inc);
                 }
+                const HMap ex = __shfl_up_sync(ACX_FULL, inc, 1);
+                const HMap pre = lane > 0 ? ex : kHIdentity;
+                // the history before this lane's tokens: the block starts from
+                // (1, 2, 3, 4); a NEW token's entry is its distance
+                auto entry = [&](int k) -> uint64_t {
+                    const uint32_t x = (uint32_t)(pre >> (16 * k)) & 0xffff;
+                    return (x & kHRef) ? (uint64_t)((x & 3) + 1) : B + tpos[x] + tll[x] - tsrc[x];
+                };
+                // the lane's history in four registers (selects, no indexed array)
+                uint64_t h0 = entry(0), h1 = entry(1), h2 = entry(2), h3 = entry(3);
+                for (uint32_t i = j0; i < j1; i++) {
+                    const uint8_t c = tcmd[i];
+                    const uint64_t dst = B + tpos[i] + tll[i];
+                    if (c == kNew) {
+                        h3 = h2; h2 = h1; h1 = h0; h0 = dst - tsrc[i];
+                    } else if (c >= 1 && c <= 4) {
+                        const uint32_t j = c - 1u;
+                        const uint64_t d = j == 0 ? h0 : j == 1 ? h1 : j == 2 ? h2 : h3;
+                        if (d < 1 || d > dst) misc[1] = 1;
+                        tsrc[i] = dst - d;
+                        h3 = j >= 3 ? h2 : h3;
+                        h2 = j >= 2 ? h1 : h2;
+                        h1 = j >= 1 ? h0 : h1;
+                        h0 = d;
+                    }
+                }
+            }
+            if (place && (warp > 0 || !any_rep)) {
+                // literal placement: a thread copies a tiny run (<= kLaneBytes)
+                // by itself, all threads at once; eight lanes copy each longer one
+                const int w0 = any_rep ? 1 : 0, nw = kLocWarps - w0;
+                for (uint32_t i = tid - 32 * w0; i < n; i += 32 * nw) {
+                    const uint32_t ll = tll[i];
+                    if (ll <= kLaneBytes) {
+                        const uint32_t la = tlit[i], lb = tpos[i];
+                        for (uint32_t k = 0; k < ll; k++) sout[lb + k] = slit[la + k];
+                    }
+                }
+                for (uint32_t i = (warp - w0) * 4 + (lane >> 3); i < n; i += nw * 4)
+                    if (tll[i] > kLaneBytes) copy_run8(sout, slit, tlit[i], tpos[i], tll[i], lane & 7);
             }
             grp_sync(bid);
             mark(misc[1] != 0, kStageSources);
@@ -513,17 +531,6 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
 
         uint32_t npend = 0, pbytes = 0;
         if (!bad) {
-            // ---- literal placement: a thread copies a tiny run (<= kLaneBytes)
-            //      by itself, all threads at once; eight lanes copy each longer one ----
-            for (uint32_t i = tid; i < n; i += kLocThreads) {
-                const uint32_t ll = tll[i];
-                if (ll <= kLaneBytes) {
-                    const uint32_t la = tlit[i], lb = tpos[i];
-                    for (uint32_t k = 0; k < ll; k++) sout[lb + k] = slit[la + k];
-                }
-            }
-            for (uint32_t i = warp * 4 + (lane >> 3); i < n; i += kLocWarps * 4)
-                if (tll[i] > kLaneBytes) copy_run8(sout, slit, tlit[i], tpos[i], tll[i], lane & 7);
             // ---- every match byte starts unresolved; external sources are pending for good;
             //      the in-block matches are listed (the literal positions are dead now) ----
             uint16_t* act_list = tlit;
