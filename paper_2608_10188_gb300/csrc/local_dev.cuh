@@ -275,7 +275,7 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
         bool prefetched = false;  // its streams are already in flight
         if (pf_item != 0xffffffffu) {
             item = pf_item;
-            prefetched = misc[2] != 0;  // written by thread 0 when it claimed the item
+            prefetched = misc[2] != 0;  // written by the thread that issued the item's copies
             pf_item = 0xffffffffu;
         } else {
             if (cleft == 0) {
@@ -554,7 +554,10 @@ __device__ __forceinline__ void local_worker(const JobDev& job, uint8_t* sm, uin
             settle_claim();
             pf_item = ticket_item(job, cnext++);
             cleft--;
-            if (tid == 0) {
+            // (issued by the last warp, which takes the fewest in-block matches
+            // below, so that its loads of the next block's descriptor delay the
+            // rounds least)
+            if (tid == kLocThreads - 32) {
                 // in a fused decode, only streams that are already published
                 const bool go = pf_item < job.n_items && (!job.ready || ld_acquire_u32(job.ready + pf_item) != 0);
                 if (go) {

@@ -8,6 +8,8 @@ import synth
 from fmt_writer import build_archive
 from golden import worked_examples as W
 
+BLOCK = 16384
+
 pytestmark = pytest.mark.gpu
 
 FAST, PLAIN = 0, 1
@@ -290,3 +292,61 @@ def test_cross_block_policies_depths_and_launch_shapes(acx, dna4m, text4m, kind)
                 assert np.array_equal(out, want[name]), (name, shape)
         finally:
             ctx.close()
+
+
+def _local_pieces(arc, n_blocks):
+    """Pending pieces left by a local pass that resolves every in-block match
+    it can: per block (from the oracle's parse), the matches whose source
+    precedes the block are pending; an in-block match is resolved once every
+    byte of its source window [src, src + min(distance, length)) is final
+    (a literal, or a byte of a resolved match), repeated to a fixed point;
+    the rest leave ceil(length / 32) pieces each."""
+    total = 0
+    for b in range(n_blocks):
+        t = oracle.parse_block(arc, b)
+        B = b * BLOCK
+        ml, dst, src = t["ml"].astype(np.int64), t["dst"].astype(np.int64), t["src"].astype(np.int64)
+        final = np.ones(BLOCK, bool)
+        todo = []
+        for k in range(len(ml)):
+            if ml[k] == 0:
+                continue
+            o = dst[k] - B
+            final[o:o + ml[k]] = False
+            if src[k] < B:
+                total += (ml[k] + 31) // 32
+            else:
+                todo.append(k)
+        while todo:
+            rest = []
+            for k in todo:
+                so, d = src[k] - B, dst[k] - src[k]
+                if final[so:so + min(d, ml[k])].all():
+                    o = dst[k] - B
+                    final[o:o + ml[k]] = True
+                else:
+                    rest.append(k)
+            if len(rest) == len(todo):
+                break
+            todo = rest
+        total += sum((ml[k] + 31) // 32 for k in todo)
+    return total
+
+
+@pytest.mark.parametrize("kind", ["dna", "text"])
+def test_local_pass_resolves_every_in_block_chain(acx, ctx, kind):
+    """The local pass finishes every in-block match whose chain of sources
+    stays in the block (periodic fills in rounds, "What Does: Periods, Not
+    Chains"); only the rest reach the cross-block pass.  The pending-piece
+    count of the decode equals the count from the oracle's parse, on every
+    run (the rounds must not end early)."""
+    from gpu_util import gpu_decode
+    data = synth.corpus(kind, (2 << 20) + 333, 17)
+    arc = acx.encode(data)
+    nb = (data.size + BLOCK - 1) // BLOCK
+    want = _local_pieces(arc, nb)
+    assert want > 0
+    for _ in range(3):
+        rc, out, st = gpu_decode(ctx, arc, stats=True)
+        assert rc == 0 and np.array_equal(out, data)
+        assert st["pending_spans"] == want, (st["pending_spans"], want)
