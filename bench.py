@@ -209,22 +209,33 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Start sampling every 100 ms and wait (up to 3 s) for the first
+        sample, so that sampling runs before the timed region begins."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        """Stop after one more sample (up to 0.5 s): short timed regions fall
+        between two samples, one taken before and one after them."""
         if not self.proc:
             return None
+        n0, t0 = len(self.lines), time.perf_counter()
+        while len(self.lines) == n0 and time.perf_counter() - t0 < 0.5 and self.proc.poll() is None:
+            time.sleep(0.005)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
