@@ -1004,12 +1004,13 @@ def main():
 
 
 def kernel_source_key():
-    """Hash of the files that make up the decode kernels: profiler counters
-    taken on other sources do not describe these kernels."""
+    """Hash of the files that make up the decode kernels and of the encoder
+    that writes the measured archives: profiler counters taken on other
+    kernels, or on other archives, do not describe these."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2608_10188_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")) or f == "internal.h":
+        if f.endswith((".cu", ".cuh")) or f in ("internal.h", "encode.cpp"):
             h.update(f.encode())
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]

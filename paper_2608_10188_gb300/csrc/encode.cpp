@@ -512,6 +512,21 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
     parallel_for(nb, threads, [&](uint32_t b) {
         std::vector<uint8_t>& P = pay[b];
         P.assign(48, 0);
+        // rANS lanes of each stream: powers of two up to max_lanes, at least 64
+        // symbols a lane; the three short streams (cmd, len, off) take 16 symbols a
+        // lane when their lanes then fit one warp together, which the decoder
+        // decodes them on side by side, so that their dependent steps (a lane
+        // decodes its symbols in sequence) stay few
+        auto lanes_for = [&](uint32_t rn, uint32_t per_lane) {
+            uint32_t k = 1;
+            while (2 * k <= max_lanes && per_lane * (2 * k) <= rn) k *= 2;
+            return k;
+        };
+        uint32_t lanes[4], short_sum = 0;
+        for (int s = 0; s < 4; s++) lanes[s] = lanes_for((uint32_t)blocks[b].s[s].size(), 64);
+        for (int s = 0; s < 3; s++) short_sum += lanes_for((uint32_t)blocks[b].s[s].size(), 16);
+        if (short_sum <= 32)
+            for (int s = 0; s < 3; s++) lanes[s] = lanes_for((uint32_t)blocks[b].s[s].size(), 16);
         for (int s = 0; s < 4; s++) {
             const std::vector<uint8_t>& raw = blocks[b].s[s];
             const uint32_t rn = (uint32_t)raw.size();
@@ -524,8 +539,7 @@ int encode_archive(const uint8_t* src, uint64_t n, int no_rep, uint32_t min_matc
                 table = sum == kM;
             }
             if (rn >= 16 && table) {
-                uint32_t k = 1;
-                while (2 * k <= max_lanes && 64 * (2 * k) <= rn) k *= 2;
+                const uint32_t k = lanes[s];
                 std::vector<uint8_t> enc = rans_encode(raw.data(), rn, k, freq[s]);
                 if (enc.size() < rn) {
                     body.swap(enc);
