@@ -358,7 +358,7 @@ bool aceapex_server::form_tick(int li) {
     size_t k = 0;
     for (; k < cand.size(); k++) {
         Req& r = cand[k];
-        const WalkOut& o = outs[k];
+        WalkOut& o = outs[k];
         if (o.bad) {  // a corrupt block: this request fails alone
             complete(r, ACEAPEX_E_CORRUPT, now());
             continue;
@@ -387,7 +387,7 @@ bool aceapex_server::form_tick(int li) {
             if (!T.scheduled(b)) {
                 T.sched_mark[b] = T.epoch;
                 T.sched.push_back(b);
-                T.need[b] = o.need[q];
+                T.need[b].swap(o.need[q]);  // (o is not read again)
                 if (slot_of[b] == kNoSlot) new_blocks.push_back(b);
             } else {
                 for (const auto& iv : o.need[q]) iv_union(T.need[b], iv.first, iv.second);
@@ -439,7 +439,7 @@ bool aceapex_server::form_tick(int li) {
         S.items[i].need_off = (uint32_t)need.size();
         S.items[i].need_n = (uint32_t)iv.size();
         need.insert(need.end(), iv.begin(), iv.end());
-        valid[blocks[i]] = nb;  // kept once this tick has run (later ticks are ordered after it)
+        valid[blocks[i]].swap(nb);  // kept once this tick has run (later ticks are ordered after it)
     }
     cudaError_t e;
     int rc = ACEAPEX_OK;
