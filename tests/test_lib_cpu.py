@@ -432,3 +432,39 @@ def test_randomized_encoder_options_round_trip(acx):
             want = _levels_from_parse(arc, nb, n)
             for b in range(nb):
                 assert oracle.block_levels(arc, b).tolist() == want[b], (it, b, opts)
+
+
+def _lanes_for(rn, per_lane, cap=32):
+    k = 1
+    while 2 * k <= cap and per_lane * 2 * k <= rn:
+        k *= 2
+    return k
+
+
+@pytest.mark.parametrize("kind", ["dna", "text"])
+def test_encoder_lane_counts_follow_the_stream_lengths(acx, kind):
+    """rANS lanes per stream: the most (a power of two up to the cap) that
+    leave 64 symbols a lane; the three short streams take 16 symbols a lane
+    when their lanes then fit one warp together.  Read back from the block
+    descriptors of the archive."""
+    import struct
+    data = synth.corpus(kind, (2 << 20) + 77, 23)
+    arc = acx.encode(data)
+    nb = struct.unpack_from("<I", arc, 24)[0]
+    off_idx = struct.unpack_from("<Q", arc, 40)[0]
+    packed = 0
+    for b in range(nb):
+        poff = struct.unpack_from("<Q", arc, off_idx + 40 * b)[0]
+        desc = [struct.unpack_from("<IIBB", arc, poff + 12 * s) for s in range(4)]
+        raw = [d[0] for d in desc]
+        want = [_lanes_for(r, 64) for r in raw]
+        short = [_lanes_for(r, 16) for r in raw[:3]]
+        if sum(short) <= 32:
+            want[:3] = short
+            packed += 1
+        for s, (sraw, enc, mode, K) in enumerate(desc):
+            if mode == 1:
+                assert K == want[s], (b, s, sraw, K, want[s])
+    # the genome's blocks all take the packed rule; the text's short streams are too long
+    assert packed == nb if kind == "dna" else packed < nb
+    assert oracle.decode_status(arc, verify=False)[0] == 0
