@@ -52,7 +52,9 @@ def parse_args():
     p.add_argument("--corpus", default="dna", choices=["dna", "text"])
     p.add_argument("--size", type=int, default=0)
     p.add_argument("--encoding", default="history", choices=["history", "no_rep"])
-    p.add_argument("--variant", default="fast", choices=["fast", "plain"])
+    p.add_argument("--variant", default="fast", choices=["fast", "plain", "fused"],
+                   help="fast: entropy stage, local pass, cross-block pass; plain: the serial history-bound "
+                        "decoder; fused: entropy stage and local pass in one kernel (single-archive decodes)")
     p.add_argument("--lanes", type=int, default=32)
     p.add_argument("--wait-ns", type=int, default=0,
                    help="decoder: first cross-block round's wait per piece (0: library default)")
@@ -836,7 +838,7 @@ def main():
     extras = (world == 1 and not args.no_extras and args.corpus == "dna" and not args.size
               and args.encoding == "history" and args.variant == "fast" and not args.shard)
     futs = start_extra_encodes(args, acx, data) if extras else None
-    variant = acx.lib.VARIANT_PLAIN if args.variant == "plain" else acx.lib.VARIANT_FAST
+    variant = {"plain": acx.lib.VARIANT_PLAIN, "fused": acx.lib.VARIANT_FUSED}.get(args.variant, acx.lib.VARIANT_FAST)
     ctx = acx.Context(dev, variant=variant, wait_ns=args.wait_ns)
     h_arc = np.frombuffer(arc, dtype=np.uint8).copy()
     d_arc = torch.from_numpy(h_arc).to(f"cuda:{dev}")
@@ -989,7 +991,8 @@ def main():
             "path_roofline": path_roof,
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "gpu_launches": (6 if args.levels and args.variant == "fast" else 4) * args.steps,
+            "gpu_launches": (3 if args.variant == "fused" else 6 if args.levels and args.variant == "fast" else 4)
+            * args.steps,
             "gpu_launches_note": "prologue, entropy stage, local pass, [level scan, level fill,] cross-block pass",
             "clocks": clk,
             "wall_s": round(wall, 3),
@@ -1051,9 +1054,14 @@ def rooflines(stage, pb, size, arc_len, st, n_blocks, variant, ms_step, wname=""
         "k_rans": (stage["ans"], pb["payload"] + pb["decoded"]),
         # decoded streams read + output written
         local: (stage["local"], pb["decoded"] + size),
+    } if variant != "fused" else {
+        # one kernel: payload read + output written (the streams stay on chip)
+        "k_fused": (stage["local"], pb["payload"] + size),
+    }
+    kern.update({
         # source bytes read + destination bytes written + 16 B per piece record + 4 B count per block
         "k_external": (stage["cross"], 2 * pend_b + 16 * pend_n + 4 * n_blocks),
-    }
+    })
     per = {}
     for k, (ms, b) in kern.items():
         per[k] = {"ms": round(ms, 4), "design_bytes": int(b),
