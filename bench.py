@@ -425,7 +425,7 @@ def run_batch(args, dist):
     torch.cuda.set_device(dev)
     device = f"cuda:{dev}"
     variant = acx.lib.VARIANT_PLAIN if args.variant == "plain" else acx.lib.VARIANT_FAST
-    ctx = acx.Context(dev, variant=variant)
+    ctx = acx.Context(dev, variant=variant, wait_ns=args.wait_ns)
     lanes_ms = None
     if args.autotune:
         args.lanes, lanes_ms = tune_lanes(args, acx, torch, ctx, device)
